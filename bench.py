@@ -1,0 +1,365 @@
+"""Benchmark of the PDR sweep (Alg. 1 with the exact edge solver of Alg. 2) on one GB300.
+
+Workload: the planar-like k-nearest-neighbour instance -- n = 2,500 random
+points, each joined both ways to its 3 nearest neighbours (m = 15,000 arcs),
+K = 500 random OD pairs with integer demands in [1, 20], capacities 1.2x the
+load of a seeded random hop-shortest-path routing (seed 0).
+
+One step = one call of pdr_solve from f = 0 that runs exactly S sweeps (the
+stop rules stay armed but do not fire before S) plus the FP64 residual and
+certificate evaluation: every row of the hot path.  The metric is
+edge-commodity updates per second, m * K * S / step time.
+
+Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
+the solver's stream, with a 256 MiB buffer overwritten between steps so every
+step starts with a cold L2.  ``value`` has the inputs resident in HBM; ``e2e``
+times the same step through the C ABI from pinned host buffers (pdr_create,
+which copies the instance in, pdr_solve, and pdr_flows, which copies the
+flows out).  ``roofline`` times the dominant kernel alone (cold L2 per launch)
+and divides its algorithmic bytes by that time.
+
+Multi-GPU: the sweep does not shard (replicas only): under torchrun every rank
+solves its own replica and ``value`` is the sum of the ranks' updates over the
+slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (the paper's algorithms,
+unoptimised) on this host's cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PDR edge·commodity updates/s, time-to-residual 1e-6, % of HBM peak"
+UNIT = "edge·commodity updates/s"
+WORKLOAD = "knn2500_k500: n=2500, m=15000 (3-NN both ways), K=500, d~U{1..20}, u=1.2x routing load, seed 0"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per step")
+    ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
+    ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while active."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_07549_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_digest") != source_digest():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch"])
+
+
+def cpu_baseline(inst, budget_s=12.0):
+    """The FP64 oracle (Alg. 1 + Alg. 2, unoptimised) on all host cores, on a bounded sample."""
+    import oracle
+
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem.from_instance(inst)
+    t0 = time.perf_counter()
+    P.solve_eso(max_sweeps=5, eps_obj=0.0)
+    per = (time.perf_counter() - t0) / 5
+    n_sweeps = max(5, int(budget_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    _, rep = P.solve_eso(max_sweeps=n_sweeps, eps_obj=0.0)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return {"value": inst.m * inst.K * rep["sweeps"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{rep['sweeps']} FP64 sweeps of Alg. 1 (sort-based Alg. 2) from f = 0 on the same instance, "
+                      f"{dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args, inst):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem.from_instance(inst)
+    t0 = time.perf_counter()
+    P.solve_eso(max_sweeps=3, eps_obj=0.0)
+    per = (time.perf_counter() - t0) / 3
+    # each step: a bounded sample of the workload, about 20 s for the whole run
+    total_steps = args.steps + args.warmup
+    sweeps = max(3, int(20.0 / max(per, 1e-6) / max(total_steps, 1)))
+    for _ in range(args.warmup):
+        P.solve_eso(max_sweeps=sweeps, eps_obj=0.0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        P.solve_eso(max_sweeps=sweeps, eps_obj=0.0)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = inst.m * inst.K * sweeps / (ms / 1e3)
+    sample = f"each step {sweeps} FP64 sweeps of Alg. 1 (sort-based Alg. 2) from f = 0"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sweeps_per_step": sweeps, "threads": threads},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    from paper_2108_07549_gb300 import instances
+
+    inst = instances.knn2500_k500(1.2, seed=0)
+    if args.impl == "reference":
+        run_reference(args, inst)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2108_07549_gb300 import build, pdr
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    pdr.load()
+    stream = torch.cuda.Stream()
+    S = args.sweeps
+    opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S)
+    m, K = inst.m, inst.K
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- device-resident steps
+    with torch.cuda.stream(stream):
+        solver = pdr.Solver.from_instance(inst, stream=stream.cuda_stream, **opts)
+        for _ in range(args.warmup):
+            solver.reset()
+            r = solver.solve()
+        assert r["sweeps"] == S, r
+        barrier()
+        times = []
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with ClockSampler(local) as clocks:
+            for q in range(args.steps):
+                flush.fill_(q & 0xFF)
+                ev0[q].record(stream)
+                solver.reset()
+                r = solver.solve()
+                ev1[q].record(stream)
+            torch.cuda.synchronize()
+        times = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        barrier()
+    ms_step = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * m * K * S / (ms_step / 1e3)
+    launches_per_step = 2 * (S + 1) + 3 + 1 + 2  # sweeps, residuals, state init, reset
+
+    # ---------------------------------------------------------------- end to end through the C ABI
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    host = [pin(x) for x in (inst.row_ptr, inst.col, inst.u, inst.s, inst.t, inst.d)]
+    out = torch.empty((m, K), dtype=torch.float64).pin_memory().numpy()
+    h2d = sum(x.nbytes for x in host)
+    d2h = m * K * 4  # the FP32 flows; pdr_flows widens them to double on the host
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for q in range(max(1, args.warmup) + args.steps):
+            flush.fill_(q & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with pdr.Solver(inst.n, *host, stream=stream.cuda_stream, **opts) as sv:
+                sv.solve()
+                sv._check(sv._lib.pdr_flows(sv._h, out.ctypes.data_as(__import__("ctypes").c_void_p)))
+            t1 = time.perf_counter()
+            if q >= max(1, args.warmup):
+                e2e_times.append(t1 - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * m * K * S / e2e_s
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sweeps_per_step": S, "precision": "FP32 flows and edge QP, FP64 stop "
+                   "test and certificate", "l2": "256 MiB buffer overwritten between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+        "step_result": {k: r[k] for k in ("sweeps", "z", "cap_rel", "cons_rel", "verdict_name")},
+    }
+
+    if not args.no_extras and rank == 0:
+        # dominant kernel alone, cold L2 per launch
+        with torch.cuda.stream(stream):
+            solver.reset()
+            solver.sweeps(200)
+            t_qp = solver.time_kernel("qp", 50, FLUSH_BYTES)
+            t_ex = solver.time_kernel("excess", 50, FLUSH_BYTES)
+        n = inst.n
+        bytes_qp = 4 * K * (2 * m + n) + 12 * m  # f in, f out, h once; tail, head, capacity per edge
+        bytes_ex = 4 * K * (m + n) + 4 * 2 * m + 8 * n  # f once, h out; incidence lists
+        share_qp = t_qp / (t_qp + t_ex)
+        dom, t_dom, b_dom = ("edge_qp", t_qp, bytes_qp) if t_qp >= t_ex else ("excess_height", t_ex, bytes_ex)
+        peak, peak_src = load_peaks()
+        achieved = b_dom / (t_dom / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": ncu_traffic(dom), "kernel": dom,
+                            "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                            "kernel_us": {"edge_qp": t_qp * 1e3, "excess_height": t_ex * 1e3},
+                            "algorithmic_bytes": {"edge_qp": bytes_qp, "excess_height": bytes_ex},
+                            "share_edge_qp": share_qp}
+        # time to the paper's stop rule (|z^(t) - z^(t-1)| < 1e-6) from f = 0
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
+                                          resid_tol=1e-6, max_sweeps=1000000) as sv:
+                rr = sv.solve()
+        line["time_to_eps"] = {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"],
+                               "ms": rr["ms_total"], "z": rr["z"], "cap_rel": rr["cap_rel"],
+                               "cons_rel": rr["cons_rel"], "verdict": rr["verdict_name"]}
+        line["cpu_baseline"] = cpu_baseline(inst)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

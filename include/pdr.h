@@ -1,0 +1,218 @@
+/*
+ * pdr.h -- C ABI of libpdr, a GB300 (sm_103a) implementation of Potential
+ * Difference Reduction (PDR) for the multicommodity-flow feasibility problem.
+ *
+ * Paper: P. Liu, "A Localized Method for Multicommodity Flow Problem",
+ * arXiv 2108.07549.  Section numbers, equations and algorithms below refer
+ * to it.
+ *
+ * Problem (eq. (1)): a directed graph G(V, E) with n vertices and m edges,
+ * capacities u_e >= 0, and K commodities (s_k, t_k, d_k) with s_k != t_k and
+ * d_k > 0.  A flow f_e,k >= 0 is feasible when sum_k f_e,k <= u_e on every
+ * edge and every commodity is conserved with supply d_k at s_k and demand
+ * d_k at t_k.
+ *
+ * Method (Section 4, Alg. 1 with the edge solver of Alg. 2): starting from
+ * f = 0, every sweep computes the excess Delta_ik (eq. (3), (3h)), the
+ * heights h_ik = Delta_ik / delta_i (eq. (2)), the congestion
+ * psi_e = max(0, sum_k f_e,k - u_e) (eq. (41)) and the objective
+ * z = 1/2 sum psi^2 + 1/2 sum delta_i h^2; it stops when a stop rule fires,
+ * and otherwise replaces every edge's flows by the exact minimiser of its
+ * quadratic subproblem (eq. (10)).
+ *
+ * Conventions shared by every entry point:
+ *  - Edge e is CSR position e: its tail is the vertex i with
+ *    row_ptr[i] <= e < row_ptr[i+1], its head is col[e].
+ *  - Flow arrays are edge-major and commodity-contiguous: f[e*K + k].
+ *    Height arrays are vertex-major: h[i*K + k].
+ *  - Host pointers are read or written only during the call; the caller
+ *    keeps ownership of every array it passes.  A context owns all device
+ *    memory it allocates and frees it in pdr_destroy.
+ *  - Device work is enqueued on the CUDA stream given to pdr_create (NULL =
+ *    the legacy default stream); calls that return host data synchronise
+ *    that stream before returning.
+ *  - Every function returns a pdr_status.  The library never aborts, traps
+ *    or prints; the message of the last failure on a context is returned by
+ *    pdr_last_error.  A context is not thread-safe: calls on one context
+ *    must not overlap.
+ */
+#ifndef PDR_H
+#define PDR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdr_ctx pdr_ctx; /* opaque solver context */
+
+typedef enum {
+    PDR_OK = 0,
+    PDR_ERR_INVALID_ARG = 1, /* an argument violates the stated domain */
+    PDR_ERR_OOM = 2,         /* device or host allocation failed */
+    PDR_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    PDR_ERR_NUMERIC = 4,     /* a non-finite objective appeared */
+    PDR_ERR_NOT_SOLVED = 5,  /* reserved */
+    PDR_ERR_UNSUPPORTED = 6  /* option or size outside what this build supports */
+} pdr_status;
+
+typedef enum {
+    PDR_VERDICT_UNKNOWN = 0,   /* neither test below is met yet */
+    PDR_VERDICT_FEASIBLE = 1,  /* eq. (1) residuals are within the tolerance */
+    PDR_VERDICT_INFEASIBLE = 2 /* a Farkas certificate proves eq. (1) empty */
+} pdr_verdict;
+
+typedef enum {
+    PDR_PREC_FP32 = 0,         /* flows, heights and the edge QP in FP32 */
+    PDR_PREC_FP64 = 1,         /* everything in FP64 */
+    PDR_PREC_FP32_FP64TAIL = 2 /* FP32 until its stop rules fire, then FP64 */
+} pdr_precision;
+
+typedef enum {
+    PDR_STOP_MAX_SWEEPS = 0, /* t reached max_sweeps */
+    PDR_STOP_OBJECTIVE = 1,  /* |z^(t) - z^(t-1)| < eps_obj (Alg. 1) */
+    PDR_STOP_RESIDUAL = 2,   /* cap_rel <= resid_tol and cons_rel <= resid_tol */
+    PDR_STOP_RELATIVE = 3,   /* |z^(t) - z^(t-1)| <= eps_rel * z^(t) */
+    PDR_STOP_NUMERIC = 4,    /* z is not finite */
+    PDR_STOP_STALL = 5       /* FP32 phase of PDR_PREC_FP32_FP64TAIL: z^(t) >= z^(t-1) */
+} pdr_stop_reason;
+
+typedef struct {
+    int32_t precision;  /* pdr_precision (default PDR_PREC_FP32) */
+    int32_t reserved0;
+    double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
+    double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
+    double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */
+    int64_t max_sweeps; /* upper bound on QP updates per solve (default 1,000,000) */
+    int32_t trace_len;  /* number of z^(t) values kept for pdr_trace (default 0) */
+    int32_t reserved1;
+} pdr_options;
+
+typedef struct {
+    int64_t sweeps;      /* QP updates applied by the last solve (both phases) */
+    int64_t sweeps_fp64; /* of which in FP64 */
+    double z;            /* objective of the returned flows (FP64 reduction) */
+    double dz;           /* z^(t) - z^(t-1) at the stop */
+    double cap_abs;      /* max_e max(0, sum_k f_e,k - u_e) */
+    double cap_rel;      /* max_e of the same / max(u_e, mean positive u) */
+    double cons_abs;     /* max_{i,k} |Delta_ik| (conservation residual) */
+    double cons_rel;     /* max_{i,k} |Delta_ik| / d_k */
+    double f_min;        /* min_{e,k} f_e,k */
+    double margin;       /* Farkas margin; > 0 proves infeasibility */
+    double margin_scale; /* sum of the margin's absolute terms */
+    double ms_total;     /* wall time of the solve in milliseconds */
+    int32_t verdict;     /* pdr_verdict */
+    int32_t stop_reason; /* pdr_stop_reason */
+} pdr_result;
+
+/* Fills *opt with the defaults listed in pdr_options.  Returns PDR_OK, or
+ * PDR_ERR_INVALID_ARG if opt is NULL. */
+pdr_status pdr_default_options(pdr_options *opt);
+
+/* Creates a solver for one instance of eq. (1) and builds its adjacency on
+ * the device (Table "Notation": delta+(i), delta-(i), delta_i = out-degree +
+ * in-degree).
+ *   n        number of vertices, n >= 1
+ *   m        number of edges, 0 <= m < 2^31
+ *   row_ptr  host int64 [n+1]: row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      host int32 [m]: head of each edge, 0 <= col[e] < n, no self-loops
+ *   u        host double [m]: capacities, finite and >= 0
+ *   K        number of commodities, 1 <= K
+ *   s, t     host int32 [K]: origin and destination, in range, s_k != t_k
+ *   d        host double [K]: demands, finite and > 0
+ *   opt      options, or NULL for the defaults
+ *   stream   a cudaStream_t (NULL = legacy default stream)
+ *   out      receives the context (NULL on failure)
+ * Copies every input; flows start at 0.  Parallel edges are allowed.
+ * Errors: PDR_ERR_INVALID_ARG (domain violation, message names the first
+ * offending index), PDR_ERR_OOM, PDR_ERR_CUDA. */
+pdr_status pdr_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, const double *u,
+                      int32_t K, const int32_t *s, const int32_t *t, const double *d, const pdr_options *opt,
+                      void *stream, pdr_ctx **out);
+
+/* Replaces the options of ctx (the instance is kept).  NULL restores the
+ * defaults.  Errors: PDR_ERR_INVALID_ARG. */
+pdr_status pdr_set_options(pdr_ctx *ctx, const pdr_options *opt);
+
+/* Runs Alg. 1 from the current flows until a stop rule fires (the sweep
+ * loop runs on the device as one CUDA graph), then evaluates the eq. (1)
+ * residuals and the certificate in FP64 (as pdr_residuals).  Leaves f^(t),
+ * the flows whose objective triggered the stop, as the current flows.
+ * out may be NULL.  Errors: PDR_ERR_CUDA, PDR_ERR_NUMERIC. */
+pdr_status pdr_solve(pdr_ctx *ctx, pdr_result *out);
+
+/* Runs exactly `count` sweeps of Alg. 1 (excess/heights, congestion,
+ * objective, edge QP) with every stop rule disabled.  Used to compare single
+ * sweeps with a reference.  Errors: PDR_ERR_INVALID_ARG (count < 0),
+ * PDR_ERR_CUDA. */
+pdr_status pdr_sweeps(pdr_ctx *ctx, int64_t count);
+
+/* Sets every flow to 0 (the start of Alg. 1). */
+pdr_status pdr_reset(pdr_ctx *ctx);
+
+/* Copies host flows f[m*K] (double, edge-major) into the context, rounding
+ * to the working precision.  Errors: PDR_ERR_INVALID_ARG (NULL, negative or
+ * non-finite entries are not checked; the caller supplies f >= 0). */
+pdr_status pdr_set_flows(pdr_ctx *ctx, const double *f);
+
+/* Copies the current flows to host f[m*K] (double, edge-major). */
+pdr_status pdr_flows(pdr_ctx *ctx, double *f);
+
+/* Heights h_ik (eq. (2)) of the current flows, computed in the working
+ * precision by the sweep's excess kernel, into host h[n*K] (double). */
+pdr_status pdr_heights(pdr_ctx *ctx, double *h);
+
+/* Congestion psi_e (eq. (41)) of the current flows into host psi[m]. */
+pdr_status pdr_congestion(pdr_ctx *ctx, double *psi);
+
+/* Objective z of Alg. 1 at the current flows (FP64 reduction of the working
+ * precision heights and congestion) into *z. */
+pdr_status pdr_objective(pdr_ctx *ctx, double *z);
+
+/* The in-adjacency built on the device: in_ptr[n+1] (int64), in_eid[m]
+ * (int32, edge ids entering each vertex in ascending order) and deg[n]
+ * (int32, delta_i).  Any output may be NULL. */
+pdr_status pdr_adjacency(pdr_ctx *ctx, int64_t *in_ptr, int32_t *in_eid, int32_t *deg);
+
+/* eq. (1) residuals, Farkas certificate and verdict of the current flows,
+ * all computed on the device in FP64 from the stored flows.  The
+ * certificate uses potentials h and lengths l_e = max(0, max_k (h_ik - h_jk));
+ * margin = sum_k d_k (h_{s_k,k} - h_{t_k,k}) - sum_e u_e l_e > 0 proves
+ * eq. (1) infeasible (Farkas' lemma; Theorems 1 and 2 of Section 3).
+ * Verdict: INFEASIBLE if margin > 1e-9 * margin_scale or a commodity
+ * endpoint has degree 0; FEASIBLE if cap_rel <= resid_tol and
+ * cons_rel <= resid_tol; UNKNOWN otherwise.  Fills every field of *out
+ * except sweeps, sweeps_fp64, dz, ms_total and stop_reason, which keep the
+ * values of the last solve. */
+pdr_status pdr_residuals(pdr_ctx *ctx, pdr_result *out);
+
+/* Copies up to `len` values of the objective trace z^(0), z^(1), ... of the
+ * last solve (kept when trace_len > 0) into host z; *count receives the
+ * number of values written. */
+pdr_status pdr_trace(pdr_ctx *ctx, double *z, int64_t len, int64_t *count);
+
+/* Instance sizes: n, m, K, and the padded row length Kp used on the device. */
+pdr_status pdr_sizes(const pdr_ctx *ctx, int32_t *n, int64_t *m, int32_t *K, int32_t *Kp);
+
+/* Times `launches` back-to-back launches of one sweep kernel on the current
+ * state, each bracketed by CUDA events on the context's stream, and returns
+ * the mean duration in milliseconds.  which = 0: edge QP (Alg. 2);
+ * which = 1: excess/height (eq. (3), (2)).  If flush_bytes > 0 a buffer of
+ * that size is overwritten before every launch so each starts with a cold
+ * L2.  The QP launches advance the flows (they are real sweeps with fixed
+ * heights).  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
+pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_t flush_bytes, double *ms);
+
+/* Message of the last failure on ctx (or of the last failed pdr_create on
+ * this thread if ctx is NULL).  Never NULL; valid until the next call. */
+const char *pdr_last_error(const pdr_ctx *ctx);
+
+/* Frees every resource of ctx.  NULL is ignored. */
+void pdr_destroy(pdr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDR_H */

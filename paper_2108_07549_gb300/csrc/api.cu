@@ -1,0 +1,930 @@
+// api.cu -- the C ABI declared in include/pdr.h.
+//
+// A context holds one instance of eq. (1) on the device and runs Alg. 1 on
+// it.  pdr_solve launches one CUDA graph whose only node is a conditional
+// "while" loop; its body is one sweep (excess kernel, then edge kernel).  The
+// excess kernel's last block evaluates the stop rules and clears the loop
+// condition, so a whole solve is one launch and one host synchronisation.
+// If the runtime cannot build that graph, the same kernels are launched from
+// a host loop that reads the stop flag back every few hundred sweeps.
+#include "pdr.h"
+#include "pdr_internal.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pdr;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int round_up4(int k) { return (k + 3) / 4 * 4; }
+
+void fill_defaults(pdr_options* o)
+{
+    std::memset(o, 0, sizeof(*o));
+    o->precision = PDR_PREC_FP32;
+    o->eps_obj = 1e-6;
+    o->resid_tol = 1e-6;
+    o->eps_rel = 0.0;
+    o->max_sweeps = 1000000;
+    o->trace_len = 0;
+}
+
+bool options_ok(const pdr_options* o, std::string* why)
+{
+    if (o->precision < PDR_PREC_FP32 || o->precision > PDR_PREC_FP32_FP64TAIL) {
+        *why = "precision must be 0 (FP32), 1 (FP64) or 2 (FP32 with FP64 tail)";
+        return false;
+    }
+    if (!std::isfinite(o->eps_obj) || !std::isfinite(o->resid_tol) || !std::isfinite(o->eps_rel)) {
+        *why = "eps_obj, resid_tol and eps_rel must be finite";
+        return false;
+    }
+    if (o->max_sweeps < 0) {
+        *why = "max_sweeps must be >= 0";
+        return false;
+    }
+    if (o->trace_len < 0) {
+        *why = "trace_len must be >= 0";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+struct pdr_ctx {
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t K = 0, Kp = 0;
+    pdr_options opt{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int num_sms = 0;
+    bool isolated = false;
+
+    // instance
+    int64_t *row_ptr = nullptr, *in_ptr = nullptr, *inc_ptr = nullptr, *work = nullptr;
+    int32_t *col = nullptr, *src = nullptr, *in_eid = nullptr, *inc = nullptr, *deg = nullptr, *s = nullptr,
+            *t = nullptr;
+    double *u_d = nullptr, *dem_d = nullptr, *inv_scale = nullptr;
+    float *u_f = nullptr, *dem_f = nullptr, *inv_dem_f = nullptr;
+    double* inv_dem_d = nullptr;
+    // state
+    float *f32 = nullptr, *h32 = nullptr;
+    double *f64 = nullptr, *h64 = nullptr;
+    int cur_prec = 0;  // precision of the current flows: 0 FP32, 1 FP64
+    double *part_h = nullptr, *part_cons = nullptr, *part_psi = nullptr, *part_cap = nullptr;
+    int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
+    DevState* st = nullptr;
+    DevState* hst = nullptr;  // pinned mirror
+    double* trace = nullptr;
+    int64_t trace_cap = 0;
+    // residuals
+    double *r_h64 = nullptr, *r_part = nullptr;
+    ResidOut* r_out = nullptr;
+    ResidOut* hr_out = nullptr;  // pinned
+    int r_grid_v = 1, r_grid_e = 1;
+    void* psi_tmp = nullptr;
+    // graphs
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraphConditionalHandle cond[2] = {0, 0};
+    bool graph_tried[2] = {false, false};
+    bool graph_ok[2] = {false, false};
+
+    pdr_result last{};
+    std::string err;
+
+    pdr_status fail(pdr_status code, const std::string& msg)
+    {
+        err = msg;
+        return code;
+    }
+    pdr_status cuda_fail(const char* what, cudaError_t e)
+    {
+        err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+        return PDR_ERR_CUDA;
+    }
+};
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return ctx->cuda_fail(#call, _e); \
+    } while (0)
+
+namespace {
+
+template <typename T>
+T* dalloc(pdr_ctx* ctx, size_t count, pdr_status* st)
+{
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *st = (e == cudaErrorMemoryAllocation) ? PDR_ERR_OOM : PDR_ERR_CUDA;
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return nullptr;
+    }
+    return static_cast<T*>(p);
+}
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static constexpr int id = 0;
+    static float* f(pdr_ctx* c) { return c->f32; }
+    static float* h(pdr_ctx* c) { return c->h32; }
+    static const float* u(pdr_ctx* c) { return c->u_f; }
+    static const float* dem(pdr_ctx* c) { return c->dem_f; }
+    static const float* inv_dem(pdr_ctx* c) { return c->inv_dem_f; }
+};
+template <>
+struct Prec<double> {
+    static constexpr int id = 1;
+    static double* f(pdr_ctx* c) { return c->f64; }
+    static double* h(pdr_ctx* c) { return c->h64; }
+    static const double* u(pdr_ctx* c) { return c->u_d; }
+    static const double* dem(pdr_ctx* c) { return c->dem_d; }
+    static const double* inv_dem(pdr_ctx* c) { return c->inv_dem_d; }
+};
+
+template <typename T>
+SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphConditionalHandle cond = 0)
+{
+    SweepArgs<T> a{};
+    const int p = Prec<T>::id;
+    a.n = ctx->n;
+    a.m = ctx->m;
+    a.K = ctx->K;
+    a.Kp = ctx->Kp;
+    a.row_ptr = ctx->row_ptr;
+    a.col = ctx->col;
+    a.src = ctx->src;
+    a.in_ptr = ctx->in_ptr;
+    a.in_eid = ctx->in_eid;
+    a.inc_ptr = ctx->inc_ptr;
+    a.inc = ctx->inc;
+    a.deg = ctx->deg;
+    a.s = ctx->s;
+    a.t = ctx->t;
+    a.dem = Prec<T>::dem(ctx);
+    a.inv_dem = Prec<T>::inv_dem(ctx);
+    a.u = Prec<T>::u(ctx);
+    a.inv_scale = ctx->inv_scale;
+    a.f = Prec<T>::f(ctx);
+    a.h = Prec<T>::h(ctx);
+    a.part_h = ctx->part_h;
+    a.part_cons = ctx->part_cons;
+    a.part_psi = ctx->part_psi;
+    a.part_cap = ctx->part_cap;
+    a.grid_v = ctx->grid_v[p];
+    a.grid_e = ctx->grid_e[p];
+    a.psi_out = nullptr;
+    a.st = ctx->st;
+    a.trace = ctx->trace;
+    a.cond = cond;
+    a.use_cond = use_cond;
+    a.mode = mode;
+    return a;
+}
+
+// Allocates the FP64 state on first use.
+pdr_status ensure_fp64(pdr_ctx* ctx)
+{
+    if (ctx->f64) return PDR_OK;
+    pdr_status st = PDR_OK;
+    const size_t fm = (size_t)ctx->m * ctx->Kp, hn = (size_t)ctx->n * ctx->Kp;
+    ctx->f64 = dalloc<double>(ctx, fm, &st);
+    if (!ctx->f64) return st;
+    ctx->h64 = dalloc<double>(ctx, hn, &st);
+    if (!ctx->h64) return st;
+    CK(cudaMemsetAsync(ctx->f64, 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
+    CK(cudaMemsetAsync(ctx->h64, 0, sizeof(double) * (hn ? hn : 1), ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status ensure_fp32(pdr_ctx* ctx)
+{
+    if (ctx->f32) return PDR_OK;
+    pdr_status st = PDR_OK;
+    const size_t fm = (size_t)ctx->m * ctx->Kp, hn = (size_t)ctx->n * ctx->Kp;
+    ctx->f32 = dalloc<float>(ctx, fm, &st);
+    if (!ctx->f32) return st;
+    ctx->h32 = dalloc<float>(ctx, hn, &st);
+    if (!ctx->h32) return st;
+    CK(cudaMemsetAsync(ctx->f32, 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+    CK(cudaMemsetAsync(ctx->h32, 0, sizeof(float) * (hn ? hn : 1), ctx->stream));
+    return PDR_OK;
+}
+
+int start_prec(const pdr_options& o) { return o.precision == PDR_PREC_FP64 ? 1 : 0; }
+
+// Recomputes the congestion partials of the current flows.
+template <typename T>
+pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr)
+{
+    SweepArgs<T> a = make_args<T>(ctx, MODE_PSI);
+    a.psi_out = psi_out;
+    if (ctx->m > 0) {
+        CK(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
+    } else {
+        CK(cudaMemsetAsync(ctx->part_psi, 0, sizeof(double) * ctx->grid_e[Prec<T>::id], ctx->stream));
+        CK(cudaMemsetAsync(ctx->part_cap, 0, sizeof(double) * ctx->grid_e[Prec<T>::id], ctx->stream));
+    }
+    return PDR_OK;
+}
+
+pdr_status refresh_psi_current(pdr_ctx* ctx)
+{
+    return ctx->cur_prec ? refresh_psi<double>(ctx) : refresh_psi<float>(ctx);
+}
+
+__global__ void set_state_kernel(DevState* st, DevState v) { *st = v; }
+
+pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise)
+{
+    DevState v{};
+    v.z = 0.0;
+    v.z_prev = INFINITY;
+    v.dz = 0.0;
+    v.eps_obj = ctx->opt.eps_obj;
+    v.resid_tol = ctx->opt.resid_tol;
+    v.eps_rel = ctx->opt.eps_rel;
+    v.t = fresh ? 0 : ctx->hst->t;
+    v.max_sweeps = ctx->opt.max_sweeps;
+    v.trace_len = ctx->trace_cap;
+    v.evals = fresh ? 0 : ctx->hst->evals;
+    v.stop = 0;
+    v.reason = 0;
+    v.ticket = 0;
+    v.stop_on_rise = stop_on_rise;
+    set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, v);
+    CK(cudaGetLastError());
+    return PDR_OK;
+}
+
+pdr_status read_state(pdr_ctx* ctx)
+{
+    CK(cudaMemcpyAsync(ctx->hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+template <typename T>
+pdr_status build_graph(pdr_ctx* ctx)
+{
+    const int p = Prec<T>::id;
+    ctx->graph_tried[p] = true;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t node;
+    cudaGraphNodeParams np{};
+    cudaGraph_t body, captured;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) goto fail;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto fail;
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) goto fail;
+    body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        goto fail;
+    {
+        SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 1, h);
+        cudaError_t e1 = launch_excess<T>(a, ctx->cap_stream);
+        cudaError_t e2 = ctx->m > 0 ? launch_edge<T>(a, ctx->cfg[p], ctx->cap_stream) : cudaSuccess;
+        cudaError_t e3 = cudaStreamEndCapture(ctx->cap_stream, &captured);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) goto fail;
+    }
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) goto fail;
+    ctx->graph[p] = g;
+    ctx->exec[p] = exec;
+    ctx->cond[p] = h;
+    ctx->graph_ok[p] = true;
+    return PDR_OK;
+fail:
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    ctx->graph_ok[p] = false;
+    return PDR_OK;  // the host loop takes over
+}
+
+// One phase of Alg. 1 in precision T, from the state set by init_state.
+template <typename T>
+pdr_status run_phase(pdr_ctx* ctx)
+{
+    const int p = Prec<T>::id;
+    if (!ctx->graph_tried[p]) {
+        pdr_status s = build_graph<T>(ctx);
+        if (s != PDR_OK) return s;
+    }
+    if (ctx->graph_ok[p]) {
+        CK(cudaGraphLaunch(ctx->exec[p], ctx->stream));
+        return read_state(ctx);
+    }
+    // host loop fallback: chunks of sweeps, then a look at the stop flag
+    const int chunk = 256;
+    SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0);
+    for (;;) {
+        for (int q = 0; q < chunk; ++q) {
+            CK(launch_excess<T>(a, ctx->stream));
+            if (ctx->m > 0) CK(launch_edge<T>(a, ctx->cfg[p], ctx->stream));
+        }
+        pdr_status s = read_state(ctx);
+        if (s != PDR_OK) return s;
+        if (ctx->hst->stop) return PDR_OK;
+    }
+}
+
+template <typename T>
+pdr_status residuals_T(pdr_ctx* ctx)
+{
+    SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
+    CK(launch_residuals<T>(a, ctx->u_d, ctx->dem_d, ctx->r_h64, ctx->r_part, ctx->r_grid_v, ctx->r_grid_e, ctx->r_out,
+                           ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hr_out, ctx->r_out, sizeof(ResidOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status residuals_into(pdr_ctx* ctx, pdr_result* r)
+{
+    pdr_status s = ctx->cur_prec ? residuals_T<double>(ctx) : residuals_T<float>(ctx);
+    if (s != PDR_OK) return s;
+    const ResidOut& o = *ctx->hr_out;
+    r->z = o.z;
+    r->cap_abs = o.cap_abs;
+    r->cap_rel = o.cap_rel;
+    r->cons_abs = o.cons_abs;
+    r->cons_rel = o.cons_rel;
+    r->f_min = o.f_min;
+    r->margin = o.margin;
+    r->margin_scale = o.margin_scale;
+    const double tol = ctx->opt.resid_tol > 0.0 ? ctx->opt.resid_tol : 1e-6;
+    if (ctx->isolated || o.margin > 1e-9 * o.margin_scale) r->verdict = PDR_VERDICT_INFEASIBLE;
+    else if (o.cap_rel <= tol && o.cons_rel <= tol) r->verdict = PDR_VERDICT_FEASIBLE;
+    else r->verdict = PDR_VERDICT_UNKNOWN;
+    return PDR_OK;
+}
+
+// Copies a padded device array [rows x Kp] of T into host double [rows x K].
+template <typename T>
+pdr_status copy_rows_out(pdr_ctx* ctx, const T* dsrc, int64_t rows, double* out)
+{
+    if (rows == 0) return PDR_OK;
+    std::vector<T> tmp((size_t)rows * ctx->K);
+    CK(cudaMemcpy2DAsync(tmp.data(), sizeof(T) * ctx->K, dsrc, sizeof(T) * ctx->Kp, sizeof(T) * ctx->K, (size_t)rows,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t q = 0; q < tmp.size(); ++q) out[q] = (double)tmp[q];
+    return PDR_OK;
+}
+
+template <typename T>
+pdr_status copy_rows_in(pdr_ctx* ctx, const double* in, int64_t rows, T* ddst)
+{
+    if (rows == 0) return PDR_OK;
+    std::vector<T> tmp((size_t)rows * ctx->K);
+    for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = (T)in[q];
+    CK(cudaMemcpy2DAsync(ddst, sizeof(T) * ctx->Kp, tmp.data(), sizeof(T) * ctx->K, sizeof(T) * ctx->K, (size_t)rows,
+                         cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status destroy_graphs(pdr_ctx* ctx)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (ctx->exec[p]) cudaGraphExecDestroy(ctx->exec[p]);
+        if (ctx->graph[p]) cudaGraphDestroy(ctx->graph[p]);
+        ctx->exec[p] = nullptr;
+        ctx->graph[p] = nullptr;
+        ctx->graph_tried[p] = false;
+        ctx->graph_ok[p] = false;
+    }
+    return PDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pdr_status pdr_default_options(pdr_options* opt)
+{
+    if (!opt) return PDR_ERR_INVALID_ARG;
+    fill_defaults(opt);
+    return PDR_OK;
+}
+
+const char* pdr_last_error(const pdr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void pdr_destroy(pdr_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    destroy_graphs(ctx);
+    void* dev[] = {ctx->row_ptr, ctx->in_ptr, ctx->inc_ptr, ctx->inc, ctx->work, ctx->col, ctx->src, ctx->in_eid,
+                   ctx->deg, ctx->s, ctx->t,
+                   ctx->u_d, ctx->dem_d, ctx->inv_scale, ctx->u_f, ctx->dem_f, ctx->inv_dem_f, ctx->inv_dem_d, ctx->f32, ctx->h32, ctx->f64,
+                   ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_psi, ctx->part_cap, ctx->st, ctx->trace,
+                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (ctx->hst) cudaFreeHost(ctx->hst);
+    if (ctx->hr_out) cudaFreeHost(ctx->hr_out);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, const double* u, int32_t K,
+                      const int32_t* s, const int32_t* t, const double* d, const pdr_options* opt, void* stream,
+                      pdr_ctx** out)
+{
+    g_create_error.clear();
+    auto bad = [](const std::string& msg) {
+        g_create_error = msg;
+        return PDR_ERR_INVALID_ARG;
+    };
+    if (!out) return bad("out is NULL");
+    *out = nullptr;
+    if (n < 1) return bad("n must be >= 1");
+    if (m < 0 || m > (int64_t)INT32_MAX) return bad("m must satisfy 0 <= m < 2^31");
+    if (K < 1) return bad("K must be >= 1");
+    if (!row_ptr || (m > 0 && (!col || !u)) || !s || !t || !d) return bad("NULL input array");
+    if (row_ptr[0] != 0) return bad("row_ptr[0] must be 0");
+    if (row_ptr[n] != m) return bad("row_ptr[n] must equal m");
+    for (int32_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return bad("row_ptr must be non-decreasing (vertex " + std::to_string(i) + ")");
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col[e] < 0 || col[e] >= n) return bad("col out of range at edge " + std::to_string(e));
+            if (col[e] == i) return bad("self-loop at edge " + std::to_string(e));
+        }
+    }
+    for (int64_t e = 0; e < m; ++e)
+        if (!std::isfinite(u[e]) || u[e] < 0.0) return bad("capacity must be finite and >= 0 at edge " + std::to_string(e));
+    for (int32_t k = 0; k < K; ++k) {
+        if (s[k] < 0 || s[k] >= n || t[k] < 0 || t[k] >= n)
+            return bad("commodity endpoint out of range at k = " + std::to_string(k));
+        if (s[k] == t[k]) return bad("s_k == t_k at k = " + std::to_string(k));
+        if (!std::isfinite(d[k]) || !(d[k] > 0.0)) return bad("demand must be finite and > 0 at k = " + std::to_string(k));
+    }
+    pdr_options o;
+    fill_defaults(&o);
+    if (opt) o = *opt;
+    std::string why;
+    if (!options_ok(&o, &why)) return bad(why);
+
+    pdr_ctx* ctx = new pdr_ctx();
+    ctx->n = n;
+    ctx->m = m;
+    ctx->K = K;
+    ctx->Kp = round_up4(K);
+    ctx->opt = o;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    auto give_up = [&](pdr_status code) {
+        g_create_error = ctx->err;
+        pdr_destroy(ctx);
+        return code;
+    };
+#define CKC(call)                                                    \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return give_up(ctx->cuda_fail(#call, _e)); \
+    } while (0)
+    int dev = 0;
+    CKC(cudaGetDevice(&dev));
+    CKC(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CKC(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+
+    const int Kp = ctx->Kp;
+    const int cfg32 = edge_config<float>(Kp), cfg64 = edge_config<double>(Kp);
+    if (cfg32 < 0 || (o.precision != PDR_PREC_FP32 && cfg64 < 0)) {
+        ctx->err = "K = " + std::to_string(K) + " exceeds the largest edge-kernel row supported by this build";
+        return give_up(PDR_ERR_UNSUPPORTED);
+    }
+    ctx->cfg[0] = cfg32;
+    ctx->cfg[1] = cfg64;
+    ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms);
+    ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms);
+    ctx->grid_e[0] = edge_grid<float>(cfg32, m, ctx->num_sms);
+    ctx->grid_e[1] = cfg64 >= 0 ? edge_grid<double>(cfg64, m, ctx->num_sms) : 1;
+    ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms);
+    {
+        int64_t we = (m * 32 + 255) / 256;
+        int64_t cap = (int64_t)ctx->num_sms * 8;
+        ctx->r_grid_e = (int)(we < 1 ? 1 : (we < cap ? we : cap));
+    }
+
+    pdr_status st = PDR_OK;
+#define ALLOC(ptr, T, count)                            \
+    do {                                                \
+        ptr = dalloc<T>(ctx, (size_t)(count), &st);     \
+        if (!ptr) return give_up(st);                   \
+    } while (0)
+    ALLOC(ctx->row_ptr, int64_t, n + 1);
+    ALLOC(ctx->in_ptr, int64_t, n + 1);
+    ALLOC(ctx->work, int64_t, 2 * (int64_t)n + 1);
+    ALLOC(ctx->col, int32_t, m);
+    ALLOC(ctx->src, int32_t, m);
+    ALLOC(ctx->in_eid, int32_t, m);
+    ALLOC(ctx->inc_ptr, int64_t, n + 1);
+    ALLOC(ctx->inc, int32_t, 2 * m);
+    ALLOC(ctx->deg, int32_t, n);
+    ALLOC(ctx->s, int32_t, Kp);
+    ALLOC(ctx->t, int32_t, Kp);
+    ALLOC(ctx->u_d, double, m);
+    ALLOC(ctx->u_f, float, m);
+    ALLOC(ctx->inv_scale, double, m);
+    ALLOC(ctx->dem_d, double, Kp);
+    ALLOC(ctx->dem_f, float, Kp);
+    ALLOC(ctx->inv_dem_d, double, Kp);
+    ALLOC(ctx->inv_dem_f, float, Kp);
+    const int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
+    const int ge = ctx->grid_e[0] > ctx->grid_e[1] ? ctx->grid_e[0] : ctx->grid_e[1];
+    ALLOC(ctx->part_h, double, gv);
+    ALLOC(ctx->part_cons, double, gv);
+    ALLOC(ctx->part_psi, double, ge);
+    ALLOC(ctx->part_cap, double, ge);
+    ALLOC(ctx->st, DevState, 1);
+    ctx->trace_cap = o.trace_len;
+    ALLOC(ctx->trace, double, ctx->trace_cap > 0 ? ctx->trace_cap : 1);
+    ALLOC(ctx->r_h64, double, (size_t)n * Kp);
+    ALLOC(ctx->r_part, double, resid_part_count(ctx->r_grid_v, ctx->r_grid_e));
+    ALLOC(ctx->r_out, ResidOut, 1);
+    ALLOC(ctx->psi_tmp, double, m);
+    CKC(cudaMallocHost(&ctx->hst, sizeof(DevState)));
+    CKC(cudaMallocHost(&ctx->hr_out, sizeof(ResidOut)));
+    std::memset(ctx->hst, 0, sizeof(DevState));
+
+    // host-side staging of the instance
+    std::vector<int32_t> sp(Kp, -1), tp(Kp, -1);
+    std::vector<double> dp(Kp, 0.0);
+    std::vector<float> dpf(Kp, 0.0f), idf(Kp, 0.0f);
+    std::vector<double> idd(Kp, 0.0);
+    for (int k = 0; k < K; ++k) {
+        sp[k] = s[k];
+        tp[k] = t[k];
+        dp[k] = d[k];
+        dpf[k] = (float)d[k];
+        idd[k] = 1.0 / d[k];
+        idf[k] = (float)(1.0 / d[k]);
+    }
+    double usum = 0.0;
+    int64_t upos = 0;
+    for (int64_t e = 0; e < m; ++e)
+        if (u[e] > 0.0) {
+            usum += u[e];
+            ++upos;
+        }
+    const double ubar = upos ? usum / (double)upos : 1.0;
+    std::vector<double> inv(m > 0 ? m : 1);
+    std::vector<float> uf(m > 0 ? m : 1);
+    for (int64_t e = 0; e < m; ++e) {
+        inv[e] = 1.0 / (u[e] > ubar ? u[e] : ubar);
+        uf[e] = (float)u[e];
+    }
+    CKC(cudaMemcpyAsync(ctx->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (m > 0) {
+        CKC(cudaMemcpyAsync(ctx->col, col, sizeof(int32_t) * m, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaMemcpyAsync(ctx->u_d, u, sizeof(double) * m, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaMemcpyAsync(ctx->u_f, uf.data(), sizeof(float) * m, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaMemcpyAsync(ctx->inv_scale, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CKC(cudaMemcpyAsync(ctx->s, sp.data(), sizeof(int32_t) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemcpyAsync(ctx->t, tp.data(), sizeof(int32_t) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemcpyAsync(ctx->dem_d, dp.data(), sizeof(double) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemcpyAsync(ctx->dem_f, dpf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemcpyAsync(ctx->inv_dem_d, idd.data(), sizeof(double) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemcpyAsync(ctx->inv_dem_f, idf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(build_adjacency(n, m, ctx->row_ptr, ctx->col, ctx->src, ctx->in_ptr, ctx->in_eid, ctx->inc_ptr, ctx->inc,
+                        ctx->deg, ctx->work, ctx->stream));
+    // degree-0 commodity endpoints make the instance infeasible outright
+    {
+        std::vector<int32_t> hdeg(n);
+        CKC(cudaMemcpyAsync(hdeg.data(), ctx->deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CKC(cudaStreamSynchronize(ctx->stream));
+        for (int k = 0; k < K; ++k)
+            if (hdeg[s[k]] == 0 || hdeg[t[k]] == 0) ctx->isolated = true;
+    }
+    ctx->cur_prec = start_prec(o);
+    st = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
+    if (st != PDR_OK) return give_up(st);
+    st = refresh_psi_current(ctx);
+    if (st != PDR_OK) return give_up(st);
+    st = init_state(ctx, true, 0);
+    if (st != PDR_OK) return give_up(st);
+    CKC(cudaStreamSynchronize(ctx->stream));
+#undef ALLOC
+#undef CKC
+    *out = ctx;
+    return PDR_OK;
+}
+
+pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    pdr_options o;
+    fill_defaults(&o);
+    if (opt) o = *opt;
+    std::string why;
+    if (!options_ok(&o, &why)) return ctx->fail(PDR_ERR_INVALID_ARG, why);
+    if (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0)
+        return ctx->fail(PDR_ERR_UNSUPPORTED, "K exceeds the largest FP64 edge-kernel row supported by this build");
+    if (o.trace_len != ctx->trace_cap) {
+        if (ctx->trace) cudaFree(ctx->trace);
+        pdr_status st = PDR_OK;
+        ctx->trace = dalloc<double>(ctx, o.trace_len > 0 ? o.trace_len : 1, &st);
+        if (!ctx->trace) return st;
+        ctx->trace_cap = o.trace_len;
+        destroy_graphs(ctx);  // the graphs captured the old trace pointer
+    }
+    const int want = start_prec(o);
+    if (want != ctx->cur_prec && o.precision != PDR_PREC_FP32_FP64TAIL) {
+        // move the current flows into the new working precision
+        std::vector<double> f((size_t)ctx->m * ctx->K);
+        pdr_status s = pdr_flows(ctx, f.data());
+        if (s != PDR_OK) return s;
+        ctx->opt = o;
+        s = want ? ensure_fp64(ctx) : ensure_fp32(ctx);
+        if (s != PDR_OK) return s;
+        ctx->cur_prec = want;
+        return pdr_set_flows(ctx, f.data());
+    }
+    ctx->opt = o;
+    return PDR_OK;
+}
+
+pdr_status pdr_reset(pdr_ctx* ctx)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    ctx->cur_prec = start_prec(ctx->opt);
+    pdr_status s = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
+    if (s != PDR_OK) return s;
+    const size_t fm = (size_t)ctx->m * ctx->Kp;
+    if (ctx->cur_prec) CK(cudaMemsetAsync(ctx->f64, 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
+    else CK(cudaMemsetAsync(ctx->f32, 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+    s = refresh_psi_current(ctx);
+    if (s != PDR_OK) return s;
+    s = init_state(ctx, true, 0);
+    if (s != PDR_OK) return s;
+    return read_state(ctx);
+}
+
+pdr_status pdr_set_flows(pdr_ctx* ctx, const double* f)
+{
+    if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->opt.precision != PDR_PREC_FP32_FP64TAIL) ctx->cur_prec = start_prec(ctx->opt);
+    pdr_status s = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
+    if (s != PDR_OK) return s;
+    s = ctx->cur_prec ? copy_rows_in<double>(ctx, f, ctx->m, ctx->f64) : copy_rows_in<float>(ctx, f, ctx->m, ctx->f32);
+    if (s != PDR_OK) return s;
+    s = refresh_psi_current(ctx);
+    if (s != PDR_OK) return s;
+    s = init_state(ctx, true, 0);
+    if (s != PDR_OK) return s;
+    return read_state(ctx);
+}
+
+pdr_status pdr_flows(pdr_ctx* ctx, double* f)
+{
+    if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
+    return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64, ctx->m, f)
+                         : copy_rows_out<float>(ctx, ctx->f32, ctx->m, f);
+}
+
+pdr_status pdr_heights(pdr_ctx* ctx, double* h)
+{
+    if (!ctx || !h) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "h is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->cur_prec) {
+        CK(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+        return copy_rows_out<double>(ctx, ctx->h64, ctx->n, h);
+    }
+    CK(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+    return copy_rows_out<float>(ctx, ctx->h32, ctx->n, h);
+}
+
+pdr_status pdr_congestion(pdr_ctx* ctx, double* psi)
+{
+    if (!ctx || (!psi && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "psi is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->m == 0) return PDR_OK;
+    pdr_status s;
+    if (ctx->cur_prec) {
+        double* tmp = static_cast<double*>(ctx->psi_tmp);
+        s = refresh_psi<double>(ctx, tmp);
+        if (s != PDR_OK) return s;
+        CK(cudaMemcpyAsync(psi, tmp, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return PDR_OK;
+    }
+    float* tmp = static_cast<float*>(ctx->psi_tmp);
+    s = refresh_psi<float>(ctx, tmp);
+    if (s != PDR_OK) return s;
+    std::vector<float> hv(ctx->m);
+    CK(cudaMemcpyAsync(hv.data(), tmp, sizeof(float) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t e = 0; e < ctx->m; ++e) psi[e] = (double)hv[e];
+    return PDR_OK;
+}
+
+pdr_status pdr_objective(pdr_ctx* ctx, double* z)
+{
+    if (!ctx || !z) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "z is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->cur_prec) CK(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+    else CK(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    *z = ctx->hst->z;
+    return PDR_OK;
+}
+
+pdr_status pdr_adjacency(pdr_ctx* ctx, int64_t* in_ptr, int32_t* in_eid, int32_t* deg)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (in_ptr) CK(cudaMemcpyAsync(in_ptr, ctx->in_ptr, sizeof(int64_t) * (ctx->n + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (in_eid && ctx->m > 0)
+        CK(cudaMemcpyAsync(in_eid, ctx->in_eid, sizeof(int32_t) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    if (deg) CK(cudaMemcpyAsync(deg, ctx->deg, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status pdr_sweeps(pdr_ctx* ctx, int64_t count)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (count < 0) return ctx->fail(PDR_ERR_INVALID_ARG, "count must be >= 0");
+    pdr_status s = init_state(ctx, true, 0);
+    if (s != PDR_OK) return s;
+    for (int64_t q = 0; q < count; ++q) {
+        if (ctx->cur_prec) {
+            SweepArgs<double> a = make_args<double>(ctx, MODE_FORCED);
+            CK(launch_excess<double>(a, ctx->stream));
+            if (ctx->m > 0) CK(launch_edge<double>(a, ctx->cfg[1], ctx->stream));
+        } else {
+            SweepArgs<float> a = make_args<float>(ctx, MODE_FORCED);
+            CK(launch_excess<float>(a, ctx->stream));
+            if (ctx->m > 0) CK(launch_edge<float>(a, ctx->cfg[0], ctx->stream));
+        }
+    }
+    return read_state(ctx);
+}
+
+pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool tail = ctx->opt.precision == PDR_PREC_FP32_FP64TAIL;
+    pdr_status s = init_state(ctx, true, (tail && ctx->cur_prec == 0) ? 1 : 0);
+    if (s != PDR_OK) return s;
+    int64_t sweeps32 = 0;
+    s = ctx->cur_prec ? run_phase<double>(ctx) : run_phase<float>(ctx);
+    if (s != PDR_OK) return s;
+    if (ctx->cur_prec == 0) sweeps32 = ctx->hst->t;
+    const int r = ctx->hst->reason;
+    if (tail && ctx->cur_prec == 0 && (r == STOP_OBJECTIVE || r == STOP_RELATIVE || r == STOP_STALL)) {
+        // FP64 tail from the FP32 flows
+        s = ensure_fp64(ctx);
+        if (s != PDR_OK) return s;
+        CK(launch_convert_f32_to_f64(ctx->f32, ctx->f64, (int64_t)ctx->m * ctx->Kp, ctx->stream));
+        ctx->cur_prec = 1;
+        s = refresh_psi<double>(ctx);
+        if (s != PDR_OK) return s;
+        s = init_state(ctx, false, 0);
+        if (s != PDR_OK) return s;
+        s = run_phase<double>(ctx);
+        if (s != PDR_OK) return s;
+    }
+    pdr_result res{};
+    res.sweeps = ctx->hst->t;
+    res.sweeps_fp64 = ctx->cur_prec ? ctx->hst->t - sweeps32 : 0;
+    res.dz = ctx->hst->dz;
+    res.stop_reason = ctx->hst->reason;
+    s = residuals_into(ctx, &res);
+    if (s != PDR_OK) return s;
+    res.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ctx->last = res;
+    if (out) *out = res;
+    if (res.stop_reason == STOP_NUMERIC) return ctx->fail(PDR_ERR_NUMERIC, "the objective became non-finite");
+    return PDR_OK;
+}
+
+pdr_status pdr_residuals(pdr_ctx* ctx, pdr_result* out)
+{
+    if (!ctx || !out) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "out is NULL") : PDR_ERR_INVALID_ARG;
+    pdr_result res = ctx->last;
+    pdr_status s = residuals_into(ctx, &res);
+    if (s != PDR_OK) return s;
+    *out = res;
+    return PDR_OK;
+}
+
+pdr_status pdr_trace(pdr_ctx* ctx, double* z, int64_t len, int64_t* count)
+{
+    if (!ctx || !count || (len > 0 && !z)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "bad trace arguments")
+                                                      : PDR_ERR_INVALID_ARG;
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    int64_t have = ctx->hst->evals < ctx->trace_cap ? ctx->hst->evals : ctx->trace_cap;
+    if (have > len) have = len;
+    if (have > 0) {
+        CK(cudaMemcpyAsync(z, ctx->trace, sizeof(double) * have, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    *count = have;
+    return PDR_OK;
+}
+
+pdr_status pdr_sizes(const pdr_ctx* ctx, int32_t* n, int64_t* m, int32_t* K, int32_t* Kp)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (n) *n = ctx->n;
+    if (m) *m = ctx->m;
+    if (K) *K = ctx->K;
+    if (Kp) *Kp = ctx->Kp;
+    return PDR_OK;
+}
+
+pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_t flush_bytes, double* ms)
+{
+    if (!ctx || !ms) return PDR_ERR_INVALID_ARG;
+    if ((which != 0 && which != 1) || launches < 1 || flush_bytes < 0)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "which must be 0 or 1, launches >= 1, flush_bytes >= 0");
+    if (which == 0 && ctx->m == 0) return ctx->fail(PDR_ERR_INVALID_ARG, "no edges");
+    const bool f64 = ctx->cur_prec == 1;
+    const size_t fbytes = (size_t)ctx->m * ctx->Kp * (f64 ? sizeof(double) : sizeof(float));
+    void* backup = nullptr;
+    void* flush = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double total = 0.0;
+    pdr_status status = PDR_OK;
+    auto cleanup = [&]() {
+        if (backup) cudaFree(backup);
+        if (flush) cudaFree(flush);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+#define CKT(call)                                     \
+    do {                                              \
+        cudaError_t _e = (call);                      \
+        if (_e != cudaSuccess) {                      \
+            status = ctx->cuda_fail(#call, _e);       \
+            cleanup();                                \
+            return status;                            \
+        }                                             \
+    } while (0)
+    CKT(cudaEventCreate(&e0));
+    CKT(cudaEventCreate(&e1));
+    void* fcur = f64 ? (void*)ctx->f64 : (void*)ctx->f32;
+    if (which == 0) {
+        CKT(cudaMalloc(&backup, fbytes ? fbytes : 1));
+        CKT(cudaMemcpyAsync(backup, fcur, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (flush_bytes > 0) CKT(cudaMalloc(&flush, (size_t)flush_bytes));
+    // heights of the current flows for the QP launches
+    if (f64) CKT(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+    else CKT(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+    for (int q = 0; q < launches; ++q) {
+        if (flush) CKT(cudaMemsetAsync(flush, q & 0xff, (size_t)flush_bytes, ctx->stream));
+        CKT(cudaEventRecord(e0, ctx->stream));
+        if (which == 0) {
+            if (f64) CKT(launch_edge<double>(make_args<double>(ctx, MODE_FORCED), ctx->cfg[1], ctx->stream));
+            else CKT(launch_edge<float>(make_args<float>(ctx, MODE_FORCED), ctx->cfg[0], ctx->stream));
+        } else {
+            if (f64) CKT(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+            else CKT(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+        }
+        CKT(cudaEventRecord(e1, ctx->stream));
+        CKT(cudaEventSynchronize(e1));
+        float el = 0.f;
+        CKT(cudaEventElapsedTime(&el, e0, e1));
+        total += el;
+    }
+    if (which == 0) {
+        CKT(cudaMemcpyAsync(fcur, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        pdr_status s = refresh_psi_current(ctx);
+        if (s != PDR_OK) {
+            cleanup();
+            return s;
+        }
+    }
+    CKT(cudaStreamSynchronize(ctx->stream));
+#undef CKT
+    cleanup();
+    *ms = total / launches;
+    return PDR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// pdr_internal.cuh -- shared declarations of libpdr's CUDA translation units.
+//
+// Device layout (all arrays owned by one pdr_ctx):
+//   f[e*Kp + k]   flows, edge-major, rows padded to Kp = round_up(K, 4) so
+//                 every row starts on a 16-byte boundary; pad entries stay 0
+//   h[i*Kp + k]   heights, vertex-major, same padding
+//   s, t [Kp]     commodity endpoints, padded with -1 (never a vertex)
+//   dem [Kp]      demands, padded with 0
+//   row_ptr/col   out-adjacency (edge id = CSR position), src = edge tails
+//   in_ptr/in_eid in-adjacency, edge ids ascending within each vertex
+//   inc_ptr/inc   incidence list of each vertex: its in-edges e (ascending),
+//                 then its out-edges stored as ~e (ascending); delta_i is
+//                 inc_ptr[i+1] - inc_ptr[i]
+//   deg           delta_i = out-degree + in-degree
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdr {
+
+constexpr int kThreads = 256;  // block size of every sweep kernel
+
+// Kernel modes.
+enum : int {
+    MODE_SOLVE = 0,   // honour and apply the stop rules
+    MODE_EVAL = 1,    // compute h and z only; no stop decision, no counter change
+    MODE_FORCED = 2,  // one sweep with the stop rules disabled
+    MODE_PSI = 3      // edge kernel: congestion of the stored flows only (no QP)
+};
+
+enum : int {
+    STOP_MAX_SWEEPS = 0,
+    STOP_OBJECTIVE = 1,
+    STOP_RESIDUAL = 2,
+    STOP_RELATIVE = 3,
+    STOP_NUMERIC = 4,
+    STOP_STALL = 5
+};
+
+// Solver state that lives on the device and is updated by the last block of
+// the excess kernel, so the sweep loop never returns to the host.
+struct DevState {
+    double z;          // objective z^(t) of the current flows
+    double z_prev;     // objective of the previous sweep (+inf at the start)
+    double dz;         // z - z_prev at the last evaluation
+    double cap_rel;    // max_e psi_e / max(u_e, mean positive u) at the last evaluation
+    double cons_rel;   // max_{i,k} |Delta_ik| / d_k at the last evaluation
+    double eps_obj;    // |dz| < eps_obj stops (<= 0: off)
+    double resid_tol;  // cap_rel, cons_rel <= resid_tol stops (<= 0: off)
+    double eps_rel;    // |dz| <= eps_rel * z stops (<= 0: off)
+    long long t;          // QP updates applied
+    long long max_sweeps; // t >= max_sweeps stops
+    long long trace_len;  // capacity of the z trace
+    long long evals;      // objective evaluations written to the trace
+    int stop;             // 1 once a stop rule fired
+    int reason;           // STOP_* code
+    unsigned int ticket;  // last-block counter of the excess kernel
+    int stop_on_rise;     // 1: z^(t) >= z^(t-1) stops (the FP32 rounding floor)
+};
+
+template <typename T>
+struct SweepArgs {
+    int32_t n;
+    int64_t m;
+    int32_t K, Kp;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* src;
+    const int64_t* in_ptr;
+    const int32_t* in_eid;
+    const int64_t* inc_ptr;
+    const int32_t* inc;
+    const int32_t* deg;
+    const int32_t* s;
+    const int32_t* t;
+    const T* dem;
+    const T* inv_dem;  // [Kp] 1/d_k, 0 in the padding
+    const T* u;
+    const double* inv_scale;  // [m] 1 / max(u_e, mean positive u)
+    T* f;
+    T* h;
+    double* part_h;     // [grid_v] sum delta h^2 per excess block
+    double* part_cons;  // [grid_v] max |Delta|/d per excess block
+    double* part_psi;   // [grid_e] sum psi^2 per edge block
+    double* part_cap;   // [grid_e] max psi/scale per edge block
+    int32_t grid_v, grid_e;
+    T* psi_out;         // optional [m] congestion output of the edge kernel
+    DevState* st;
+    double* trace;
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+    int mode;
+};
+
+// Launchers (sweep.cu).  Each returns the launch error.
+template <typename T>
+cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream);
+template <typename T>
+cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream);
+template <typename T>
+int edge_config(int Kp);  // picks the edge-kernel variant for a row length
+template <typename T>
+int edge_grid(int cfg, int64_t m, int num_sms);  // grid size of that variant
+int excess_grid(int32_t n, int Kp, int vec, int num_sms);
+cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream);
+
+// Adjacency builder (adjacency.cu): in-adjacency, incidence lists, edge
+// tails and degrees.  work must hold 2*n + 1 int64 entries.
+cudaError_t build_adjacency(int32_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, int32_t* src,
+                            int64_t* in_ptr, int32_t* in_eid, int64_t* inc_ptr, int32_t* inc, int32_t* deg,
+                            int64_t* work, cudaStream_t stream);
+
+// Residuals and certificate (residuals.cu).
+struct ResidOut {
+    double z, cap_abs, cap_rel, cons_abs, cons_rel, f_min, margin, margin_scale;
+};
+template <typename T>
+cudaError_t launch_residuals(const SweepArgs<T>& a, const double* u_d, const double* dem_d, double* h64,
+                             double* part, int32_t grid_v, int32_t grid_e, ResidOut* out, cudaStream_t stream);
+int resid_part_count(int32_t grid_v, int32_t grid_e);
+
+}  // namespace pdr

@@ -1,0 +1,629 @@
+// sweep.cu -- the two kernels of one PDR sweep (Alg. 1 loop body).
+//
+//  excess_kernel  eq. (3) + eq. (3h): Delta_ik = sum_in f - sum_out f + hat-Delta_ik,
+//                 eq. (2): h_ik = Delta_ik / delta_i, then the objective of
+//                 Alg. 1 and the stop test, decided on the device by the last
+//                 block to finish (deterministic fixed-order FP64 reduction of
+//                 per-block partials, no floating-point atomics).
+//  edge_kernel    Alg. 2 on every edge: the exact minimiser of eq. (10),
+//                 f' = max(0, c - psi'/2) with c_k = f_k + (h_ik - h_jk)/2,
+//                 followed by the congestion psi = max(0, sum_k f' - u)
+//                 (eq. (41)) of the stored new flows.
+//
+// Alg. 2 sorts the positive potentials to find the congested root.  Here the
+// same root is found without a sort: with theta = psi'/2 and the active set
+// A = {k : c_k > theta}, the root satisfies theta = (sum_A c - u)/(2 + |A|)
+// (Section 4.4.3, Case 2).  Starting from A = {c > 0}, theta(A) never exceeds
+// the root, so every element with c_k <= theta(A) is inactive at the root;
+// dropping them and recomputing theta increases theta monotonically and
+// stops, after at most |A| rounds, at the active set of the root (the
+// active-set iteration of Michelot 1986 for projections onto a simplex,
+// applied to this problem).  Each round is one group-wide sum and count held
+// in registers, so no row is sorted or re-read.
+#include "pdr_internal.cuh"
+
+#include <math.h>
+
+namespace pdr {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using type = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct VecOf<double> {
+    using type = double2;
+    static constexpr int N = 2;
+};
+
+__device__ __forceinline__ void unpack(const float4& v, float* x)
+{
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+}
+__device__ __forceinline__ void unpack(const double2& v, double* x)
+{
+    x[0] = v.x;
+    x[1] = v.y;
+}
+__device__ __forceinline__ float4 pack4(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
+__device__ __forceinline__ double2 pack4(const double* x) { return make_double2(x[0], x[1]); }
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
+    return x;
+}
+
+// Block-wide (sum, max) of non-negative maxima; the result is valid in thread 0.
+__device__ void block_sum_max(double& s, double& mx, double* smem)
+{
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        smem[w] = s;
+        smem[32 + w] = mx;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        s = l < nw ? smem[l] : 0.0;
+        mx = l < nw ? smem[32 + l] : 0.0;
+        s = warp_sum(s);
+        mx = warp_max(mx);
+    }
+    __syncthreads();
+}
+
+// Sum over the G lanes of an aligned lane group (xor offsets below G stay
+// inside the group).  Every lane of the warp must call it.
+template <int G, typename X>
+__device__ __forceinline__ X group_sum(X x)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// Block-wide sum of a value and a count, broadcast to every thread.
+template <typename T>
+__device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    T ta = 0;
+    int tb = 0;
+    for (int q = 0; q < nw; ++q) {  // same order in every thread
+        ta += sa[q];
+        tb += sb[q];
+    }
+    a = ta;
+    b = tb;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ objective and stop rules
+
+// Alg. 1: z = 1/2 sum psi^2 + 1/2 sum delta h^2 and the stop test, run by one
+// thread after every partial of this sweep is final.
+template <typename T>
+__device__ void finalize(const SweepArgs<T>& a, double zh, double zp, double cons, double cap)
+{
+    DevState* st = a.st;
+    const double z = 0.5 * (zp + zh);
+    st->z = z;
+    st->cap_rel = cap;
+    st->cons_rel = cons;
+    st->ticket = 0;
+    if (a.mode == MODE_EVAL) return;
+    const double dz = z - st->z_prev;
+    st->dz = dz;
+    if (a.trace && st->evals < st->trace_len) a.trace[st->evals] = z;
+    st->evals += 1;
+    int stop = 0, reason = STOP_MAX_SWEEPS;
+    if (a.mode == MODE_SOLVE) {
+        if (!isfinite(z)) {
+            stop = 1;
+            reason = STOP_NUMERIC;
+        } else if (st->t >= st->max_sweeps) {
+            stop = 1;
+            reason = STOP_MAX_SWEEPS;
+        } else if (st->eps_obj > 0.0 && fabs(dz) < st->eps_obj) {
+            stop = 1;
+            reason = STOP_OBJECTIVE;
+        } else if (st->resid_tol > 0.0 && cap <= st->resid_tol && cons <= st->resid_tol) {
+            stop = 1;
+            reason = STOP_RESIDUAL;
+        } else if (st->eps_rel > 0.0 && fabs(dz) <= st->eps_rel * z) {
+            stop = 1;
+            reason = STOP_RELATIVE;
+        } else if (st->stop_on_rise && dz >= 0.0) {
+            // the Section 4 theorem makes z non-increasing in exact arithmetic,
+            // so a rise means rounding now dominates the progress
+            stop = 1;
+            reason = STOP_STALL;
+        }
+    }
+    if (stop) {
+        st->stop = 1;
+        st->reason = reason;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    } else {
+        st->z_prev = z;
+        st->t += 1;
+    }
+}
+
+// ------------------------------------------------------------------ excess and heights
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
+{
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    __shared__ double smem[64];
+    __shared__ int s_last;
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) {
+        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+        return;
+    }
+    const uint32_t vpr = (uint32_t)(a.Kp / N);
+    const uint64_t total = (uint64_t)a.n * vpr;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    double zacc = 0.0, cons = 0.0;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const uint32_t i = (uint32_t)(idx / vpr);
+        const uint32_t v = (uint32_t)(idx - (uint64_t)i * vpr);
+        T acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = T(0);
+        // incidence list: in-edges e (added), then out-edges ~e (subtracted),
+        // four rows in flight at a time; the additions keep list order
+        const int64_t q0 = a.inc_ptr[i], q1 = a.inc_ptr[i + 1];
+        int64_t q = q0;
+        for (; q + 4 <= q1; q += 4) {
+            int32_t ev[4];
+            T x[4][N];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ev[u] = a.inc[q + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = ev[u] >= 0 ? ev[u] : ~ev[u];
+                unpack(reinterpret_cast<const VT*>(a.f + e * a.Kp)[v], x[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] = ev[u] >= 0 ? acc[j] + x[u][j] : acc[j] - x[u][j];
+        }
+        for (; q < q1; ++q) {
+            const int32_t ev = a.inc[q];
+            const int64_t e = ev >= 0 ? ev : ~ev;
+            T x[N];
+            unpack(reinterpret_cast<const VT*>(a.f + e * a.Kp)[v], x);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = ev >= 0 ? acc[j] + x[j] : acc[j] - x[j];
+        }
+        const int k0 = (int)v * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int k = k0 + j;
+            if (a.s[k] == (int)i) acc[j] += a.dem[k];
+            else if (a.t[k] == (int)i) acc[j] -= a.dem[k];
+        }
+        const int dg = (int)(q1 - q0);
+        const T dgt = T(dg);
+        T hv[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) hv[j] = dg > 0 ? acc[j] / dgt : T(0);
+        reinterpret_cast<VT*>(a.h + (int64_t)i * a.Kp)[v] = pack4(hv);
+        // delta_i h^2 is formed in the working precision and accumulated in
+        // FP64; the pad entries have h = 0 and 1/d = 0, so they add nothing
+        T cmax = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            zacc += (double)(dgt * hv[j] * hv[j]);
+            const T r = fabs(acc[j]) * a.inv_dem[k0 + j];
+            cmax = r > cmax ? r : cmax;
+        }
+        cons = fmax(cons, (double)cmax);
+    }
+    block_sum_max(zacc, cons, smem);
+    if (threadIdx.x == 0) {
+        a.part_h[blockIdx.x] = zacc;
+        a.part_cons[blockIdx.x] = cons;
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.st->ticket, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double zh = 0.0, cmax = 0.0, zp = 0.0, capmax = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        zh += __ldcg(a.part_h + b);
+        cmax = fmax(cmax, __ldcg(a.part_cons + b));
+    }
+    for (int b = threadIdx.x; b < a.grid_e; b += blockDim.x) {
+        zp += __ldcg(a.part_psi + b);
+        capmax = fmax(capmax, __ldcg(a.part_cap + b));
+    }
+    block_sum_max(zh, cmax, smem);
+    block_sum_max(zp, capmax, smem);
+    if (threadIdx.x == 0) finalize(a, zh, zp, cmax, capmax);
+}
+
+// ------------------------------------------------------------------ edge QP, lane-group form
+
+// One aligned group of G lanes per edge; each lane keeps V vectors of the
+// edge's row in registers (vector q of lane l is row vector l + q*G, so a
+// group reads contiguous memory).  K <= G * V * N.
+template <typename T, int G, int V>
+__global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
+{
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    constexpr int GPW = 32 / G;  // groups per warp
+    __shared__ double smem[64];
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) return;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gw = lane / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int vpr = a.Kp / N;
+    const bool psi_only = (a.mode == MODE_PSI);
+    double zpsi = 0.0, capmax = 0.0;
+    for (int64_t base = warp * GPW; base < a.m; base += nwarps * GPW) {
+        const int64_t e = base + gw;
+        const bool valid = e < a.m;
+        const T ue = valid ? a.u[e] : T(0);
+        T c[V][N];
+        T* frow = a.f + (valid ? e : 0) * a.Kp;
+        if (psi_only) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = gl + q * G;
+                if (valid && v < vpr) unpack(reinterpret_cast<const VT*>(frow)[v], c[q]);
+                else
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = T(0);
+            }
+        } else {
+            const int i = valid ? a.src[e] : 0;
+            const int jv = valid ? a.col[e] : 0;
+            const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)i * a.Kp);
+            const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)jv * a.Kp);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = gl + q * G;
+                if (valid && v < vpr) {
+                    T fx[N], ax[N], bx[N];
+                    unpack(reinterpret_cast<const VT*>(frow)[v], fx);
+                    unpack(__ldg(hi + v), ax);
+                    unpack(__ldg(hj + v), bx);
+                    // c_k = 1/2 ((h_ik + f_k) - (h_jk - f_k)) = f_k + (h_ik - h_jk)/2
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = fma(T(0.5), ax[j] - bx[j], fx[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = T(0);
+                }
+            }
+        }
+        T theta = T(0);
+        if (!psi_only) {
+            // s = sum_k max(0, c_k) and |{c_k > 0}|
+            T sp = T(0);
+            int np = 0;
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (c[q][j] > T(0)) {
+                        sp += c[q][j];
+                        ++np;
+                    }
+            const T s = group_sum<G>(sp);
+            int nA = group_sum<G>(np);
+            const bool congested = valid && s > ue;  // Case 2 of Alg. 2 (s <= u is Case 1)
+            bool done = !congested;
+            if (congested) theta = (s - ue) / T(2 + nA);
+            for (int it = 0; __any_sync(kFull, !done); ++it) {
+                T sa = T(0);
+                int na = 0;
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+#pragma unroll
+                    for (int j = 0; j < N; ++j)
+                        if (c[q][j] > theta) {
+                            sa += c[q][j];
+                            ++na;
+                        }
+                const T S2 = group_sum<G>(sa);
+                const int n2 = group_sum<G>(na);
+                if (!done) {
+                    if (n2 >= nA) done = true;
+                    else {
+                        nA = n2;
+                        theta = (S2 - ue) / T(2 + n2);
+                    }
+                }
+                if (it > a.Kp + 2) break;  // unreachable: nA drops every round
+            }
+        }
+        // f' = max(0, c - psi'/2); psi of the stored flows
+        T rs = T(0);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = gl + q * G;
+            T o[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T x = c[q][j] - theta;
+                o[j] = x > T(0) ? x : T(0);
+                rs += o[j];
+            }
+            if (!psi_only && valid && v < vpr) reinterpret_cast<VT*>(frow)[v] = pack4(o);
+        }
+        rs = group_sum<G>(rs);
+        if (valid && gl == 0) {
+            const T over = rs - ue;
+            const T psi = over > T(0) ? over : T(0);
+            const double pd = (double)psi;
+            zpsi += pd * pd;
+            capmax = fmax(capmax, pd * a.inv_scale[e]);
+            if (a.psi_out) a.psi_out[e] = psi;
+        }
+    }
+    block_sum_max(zpsi, capmax, smem);
+    if (threadIdx.x == 0) {
+        a.part_psi[blockIdx.x] = zpsi;
+        a.part_cap[blockIdx.x] = capmax;
+    }
+}
+
+// ------------------------------------------------------------------ edge QP, block form (large K)
+
+// One block of B threads per edge; thread l keeps row vectors l + q*B.
+template <typename T, int B, int V>
+__global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
+{
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    __shared__ double smem[64];
+    __shared__ T sa_buf[32];
+    __shared__ int sb_buf[32];
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) return;
+    const int vpr = a.Kp / N;
+    const bool psi_only = (a.mode == MODE_PSI);
+    double zpsi = 0.0, capmax = 0.0;
+    for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x) {
+        const T ue = a.u[e];
+        T c[V][N];
+        T* frow = a.f + e * a.Kp;
+        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
+        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = threadIdx.x + q * B;
+            if (v < vpr) {
+                T fx[N];
+                unpack(reinterpret_cast<const VT*>(frow)[v], fx);
+                if (psi_only) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = fx[j];
+                } else {
+                    T ax[N], bx[N];
+                    unpack(__ldg(hi + v), ax);
+                    unpack(__ldg(hj + v), bx);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = fma(T(0.5), ax[j] - bx[j], fx[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) c[q][j] = T(0);
+            }
+        }
+        T theta = T(0);
+        if (!psi_only) {
+            T s = T(0);
+            int nA = 0;
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (c[q][j] > T(0)) {
+                        s += c[q][j];
+                        ++nA;
+                    }
+            block_sum2(s, nA, sa_buf, sb_buf);
+            if (s > ue) {  // block-uniform
+                theta = (s - ue) / T(2 + nA);
+                for (int it = 0; it <= a.Kp + 2; ++it) {
+                    T S2 = T(0);
+                    int n2 = 0;
+#pragma unroll
+                    for (int q = 0; q < V; ++q)
+#pragma unroll
+                        for (int j = 0; j < N; ++j)
+                            if (c[q][j] > theta) {
+                                S2 += c[q][j];
+                                ++n2;
+                            }
+                    block_sum2(S2, n2, sa_buf, sb_buf);
+                    if (n2 >= nA) break;
+                    nA = n2;
+                    theta = (S2 - ue) / T(2 + n2);
+                }
+            }
+        }
+        T rs = T(0);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = threadIdx.x + q * B;
+            T o[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T x = c[q][j] - theta;
+                o[j] = x > T(0) ? x : T(0);
+                rs += o[j];
+            }
+            if (!psi_only && v < vpr) reinterpret_cast<VT*>(frow)[v] = pack4(o);
+        }
+        int dummy = 0;
+        block_sum2(rs, dummy, sa_buf, sb_buf);
+        if (threadIdx.x == 0) {
+            const T over = rs - ue;
+            const T psi = over > T(0) ? over : T(0);
+            const double pd = (double)psi;
+            zpsi += pd * pd;
+            capmax = fmax(capmax, pd * a.inv_scale[e]);
+            if (a.psi_out) a.psi_out[e] = psi;
+        }
+    }
+    block_sum_max(zpsi, capmax, smem);
+    if (threadIdx.x == 0) {
+        a.part_psi[blockIdx.x] = zpsi;
+        a.part_cap[blockIdx.x] = capmax;
+    }
+}
+
+__global__ void convert_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t count)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+// Variant table: capacity (elements per row) of each configuration.
+struct EdgeCfg {
+    int G;        // lanes per edge (0 = block form)
+    int B;        // block size of the block form
+    int V;        // vectors per lane
+};
+constexpr EdgeCfg kCfg[] = {
+    {4, 0, 1}, {8, 0, 1}, {16, 0, 1}, {32, 0, 1}, {32, 0, 2}, {32, 0, 4}, {32, 0, 8}, {32, 0, 16},
+    {0, 256, 4}, {0, 256, 8}, {0, 256, 16}, {0, 512, 16},
+};
+constexpr int kNumCfg = sizeof(kCfg) / sizeof(kCfg[0]);
+
+template <typename T>
+int capacity(int cfg)
+{
+    const EdgeCfg& c = kCfg[cfg];
+    return (c.G ? c.G : c.B) * c.V * VecOf<T>::N;
+}
+
+}  // namespace
+
+template <typename T>
+int edge_config(int Kp)
+{
+    for (int i = 0; i < kNumCfg; ++i)
+        if (capacity<T>(i) >= Kp) return i;
+    return -1;
+}
+
+template <typename T>
+int edge_grid(int cfg, int64_t m, int num_sms)
+{
+    const EdgeCfg& c = kCfg[cfg];
+    int64_t want, cap;
+    (void)num_sms;
+    if (c.G) {
+        const int64_t per_block = kThreads / c.G;
+        want = (m + per_block - 1) / per_block;
+    } else {
+        want = m;
+    }
+    cap = 1 << 20;  // beyond this the kernels loop over edges
+    int64_t g = want < cap ? want : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int excess_grid(int32_t n, int Kp, int vec, int num_sms)
+{
+    const int64_t total = (int64_t)n * (Kp / vec);
+    int64_t want = (total + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)num_sms * 32;
+    int64_t g = want < cap ? want : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream)
+{
+    excess_kernel<T><<<a.grid_v, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
+{
+    const int g = a.grid_e;
+    switch (cfg) {
+    case 0: edge_group_kernel<T, 4, 1><<<g, kThreads, 0, stream>>>(a); break;
+    case 1: edge_group_kernel<T, 8, 1><<<g, kThreads, 0, stream>>>(a); break;
+    case 2: edge_group_kernel<T, 16, 1><<<g, kThreads, 0, stream>>>(a); break;
+    case 3: edge_group_kernel<T, 32, 1><<<g, kThreads, 0, stream>>>(a); break;
+    case 4: edge_group_kernel<T, 32, 2><<<g, kThreads, 0, stream>>>(a); break;
+    case 5: edge_group_kernel<T, 32, 4><<<g, kThreads, 0, stream>>>(a); break;
+    case 6: edge_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
+    case 7: edge_group_kernel<T, 32, 16><<<g, kThreads, 0, stream>>>(a); break;
+    case 8: edge_block_kernel<T, 256, 4><<<g, 256, 0, stream>>>(a); break;
+    case 9: edge_block_kernel<T, 256, 8><<<g, 256, 0, stream>>>(a); break;
+    case 10: edge_block_kernel<T, 256, 16><<<g, 256, 0, stream>>>(a); break;
+    case 11: edge_block_kernel<T, 512, 16><<<g, 512, 0, stream>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    convert_kernel<<<(int)blocks, kThreads, 0, stream>>>(a, b, count);
+    return cudaGetLastError();
+}
+
+template int edge_config<float>(int);
+template int edge_config<double>(int);
+template int edge_grid<float>(int, int64_t, int);
+template int edge_grid<double>(int, int64_t, int);
+template cudaError_t launch_excess<float>(const SweepArgs<float>&, cudaStream_t);
+template cudaError_t launch_excess<double>(const SweepArgs<double>&, cudaStream_t);
+template cudaError_t launch_edge<float>(const SweepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_edge<double>(const SweepArgs<double>&, int, cudaStream_t);
+
+}  // namespace pdr

@@ -165,9 +165,15 @@ def _hop_dist_to(n, row_ptr, col, targets):
 
 def _sample_pairs(n, K, rng, row_ptr, col, chunk=512):
     """K distinct (s, t) pairs, s != t, t reachable from s; with hop distances."""
+    if K > n * (n - 1):
+        raise ValueError(f"{K} distinct pairs do not exist on {n} vertices")
     seen = set()
+    rounds = 0
     s_out, t_out, h_out = [], [], []
     while len(s_out) < K:
+        rounds += 1
+        if rounds > 10000:
+            raise ValueError(f"could not draw {K} distinct reachable pairs")
         need = K - len(s_out)
         cand_s = rng.integers(0, n, size=max(need, 8))
         cand_t = rng.integers(0, n, size=max(need, 8))

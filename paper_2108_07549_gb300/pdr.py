@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libpdr (the C ABI declared in include/pdr.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The library must have been built for sm_103a
+(``__graft_entry__.build()`` or ``python -m paper_2108_07549_gb300.build``);
+there is no CPU fallback, and loading fails loudly if ``libpdr.so`` is
+missing.
+
+``Solver`` wraps one ``pdr_ctx``: an instance of eq. (1) held on the GPU and
+solved by Alg. 1 (Potential Difference Reduction with the exact edge solver of
+Alg. 2) of arXiv 2108.07549.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdr.so")
+
+PREC_FP32, PREC_FP64, PREC_FP32_FP64TAIL = 0, 1, 2
+VERDICT_UNKNOWN, VERDICT_FEASIBLE, VERDICT_INFEASIBLE = 0, 1, 2
+STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall"}
+VERDICT_NAMES = {0: "unknown", 1: "feasible", 2: "infeasible"}
+
+#: every entry point declared in include/pdr.h
+EXPORTS = (
+    "pdr_default_options", "pdr_create", "pdr_set_options", "pdr_solve", "pdr_sweeps", "pdr_reset",
+    "pdr_set_flows", "pdr_flows", "pdr_heights", "pdr_congestion", "pdr_objective", "pdr_adjacency",
+    "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
+)
+
+
+class PdrError(RuntimeError):
+    """A libpdr call returned a status other than PDR_OK."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libpdr status {status}: {message}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("reserved0", C.c_int32), ("eps_obj", C.c_double), ("resid_tol", C.c_double),
+        ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("reserved1", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("sweeps", C.c_int64), ("sweeps_fp64", C.c_int64), ("z", C.c_double), ("dz", C.c_double),
+        ("cap_abs", C.c_double), ("cap_rel", C.c_double), ("cons_abs", C.c_double), ("cons_rel", C.c_double),
+        ("f_min", C.c_double), ("margin", C.c_double), ("margin_scale", C.c_double), ("ms_total", C.c_double),
+        ("verdict", C.c_int32), ("stop_reason", C.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {k: getattr(self, k) for k, _ in self._fields_}
+        out["verdict_name"] = VERDICT_NAMES.get(self.verdict, "?")
+        out["stop_name"] = STOP_NAMES.get(self.stop_reason, "?")
+        return out
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Opens libpdr.so and declares every entry point's signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "pdr_default_options": ([P(Options)], i32),
+        "pdr_create": ([i32, i64, vp, vp, vp, i32, vp, vp, vp, P(Options), vp, P(vp)], i32),
+        "pdr_set_options": ([vp, P(Options)], i32),
+        "pdr_solve": ([vp, P(Result)], i32),
+        "pdr_sweeps": ([vp, i64], i32),
+        "pdr_reset": ([vp], i32),
+        "pdr_set_flows": ([vp, vp], i32),
+        "pdr_flows": ([vp, vp], i32),
+        "pdr_heights": ([vp, vp], i32),
+        "pdr_congestion": ([vp, vp], i32),
+        "pdr_objective": ([vp, P(dbl)], i32),
+        "pdr_adjacency": ([vp, vp, vp, vp], i32),
+        "pdr_residuals": ([vp, P(Result)], i32),
+        "pdr_trace": ([vp, vp, i64, P(i64)], i32),
+        "pdr_sizes": ([vp, P(i32), P(i64), P(i32), P(i32)], i32),
+        "pdr_time_kernel": ([vp, i32, i32, i64, P(dbl)], i32),
+        "pdr_last_error": ([vp], C.c_char_p),
+        "pdr_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    load().pdr_default_options(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _current_stream():
+    """The CUDA stream torch is using on the current device (None if torch has no CUDA)."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Solver:
+    """One instance of eq. (1) on the GPU, solved by Alg. 1 / Alg. 2.
+
+    ``row_ptr, col`` are the out-adjacency (edge id = CSR position), ``u`` the
+    capacities, ``(s, t, d)`` the commodities.  Keyword options are the fields
+    of ``pdr_options``.  ``stream`` is a ``cudaStream_t`` value (default: the
+    current torch stream).
+    """
+
+    def __init__(self, n, row_ptr, col, u, s, t, d, stream=None, **options):
+        lib = load()
+        self._lib = lib
+        self.n = int(n)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.int32)
+        t = np.ascontiguousarray(t, dtype=np.int32)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        self.m = int(col.shape[0])
+        self.K = int(s.shape[0])
+        if t.shape[0] != self.K or d.shape[0] != self.K or u.shape[0] != self.m or row_ptr.shape[0] != self.n + 1:
+            raise ValueError("array lengths do not match n, m, K")
+        self.options = default_options(**options)
+        if stream is None:
+            stream = _current_stream()
+        elif not isinstance(stream, C.c_void_p):
+            stream = C.c_void_p(int(stream))
+        self._stream = stream
+        h = C.c_void_p()
+        st = lib.pdr_create(self.n, self.m, _ptr(row_ptr), _ptr(col), _ptr(u), self.K, _ptr(s), _ptr(t), _ptr(d),
+                            C.byref(self.options), stream, C.byref(h))
+        if st != 0:
+            raise PdrError(st, lib.pdr_last_error(None).decode())
+        self._h = h
+        self.Kp = self.sizes()[3]
+
+    @classmethod
+    def from_instance(cls, inst, stream=None, **options):
+        return cls(inst.n, inst.row_ptr, inst.col, inst.u, inst.s, inst.t, inst.d, stream=stream, **options)
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, status):
+        if status != 0:
+            raise PdrError(status, self._lib.pdr_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pdr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ API
+    def set_options(self, **options):
+        o = default_options()
+        for k, _ in Options._fields_:
+            setattr(o, k, getattr(self.options, k))
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise KeyError(f"unknown option {k!r}")
+            setattr(o, k, v)
+        self._check(self._lib.pdr_set_options(self._h, C.byref(o)))
+        self.options = o
+
+    def solve(self) -> dict:
+        r = Result()
+        self._check(self._lib.pdr_solve(self._h, C.byref(r)))
+        return r.as_dict()
+
+    def sweeps(self, count: int):
+        self._check(self._lib.pdr_sweeps(self._h, int(count)))
+
+    def reset(self):
+        self._check(self._lib.pdr_reset(self._h))
+
+    def set_flows(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (self.m, self.K):
+            raise ValueError(f"flows must have shape {(self.m, self.K)}")
+        self._check(self._lib.pdr_set_flows(self._h, _ptr(f)))
+
+    def flows(self) -> np.ndarray:
+        f = np.empty((self.m, self.K), dtype=np.float64)
+        self._check(self._lib.pdr_flows(self._h, _ptr(f)))
+        return f
+
+    def heights(self) -> np.ndarray:
+        h = np.empty((self.n, self.K), dtype=np.float64)
+        self._check(self._lib.pdr_heights(self._h, _ptr(h)))
+        return h
+
+    def congestion(self) -> np.ndarray:
+        psi = np.empty(self.m, dtype=np.float64)
+        self._check(self._lib.pdr_congestion(self._h, _ptr(psi)))
+        return psi
+
+    def objective(self) -> float:
+        z = C.c_double()
+        self._check(self._lib.pdr_objective(self._h, C.byref(z)))
+        return z.value
+
+    def adjacency(self):
+        in_ptr = np.empty(self.n + 1, dtype=np.int64)
+        in_eid = np.empty(self.m, dtype=np.int32)
+        deg = np.empty(self.n, dtype=np.int32)
+        self._check(self._lib.pdr_adjacency(self._h, _ptr(in_ptr), _ptr(in_eid), _ptr(deg)))
+        return in_ptr, in_eid, deg
+
+    def residuals(self) -> dict:
+        r = Result()
+        self._check(self._lib.pdr_residuals(self._h, C.byref(r)))
+        return r.as_dict()
+
+    def trace(self) -> np.ndarray:
+        cap = int(self.options.trace_len)
+        z = np.empty(max(cap, 1), dtype=np.float64)
+        cnt = C.c_int64()
+        self._check(self._lib.pdr_trace(self._h, _ptr(z), cap, C.byref(cnt)))
+        return z[: cnt.value].copy()
+
+    def sizes(self):
+        n, m, K, Kp = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
+        self._check(self._lib.pdr_sizes(self._h, C.byref(n), C.byref(m), C.byref(K), C.byref(Kp)))
+        return n.value, m.value, K.value, Kp.value
+
+    def time_kernel(self, which: str = "qp", launches: int = 20, flush_bytes: int = 0) -> float:
+        """Mean duration (ms) of one launch of the edge QP ("qp") or excess ("excess") kernel."""
+        ms = C.c_double()
+        w = {"qp": 0, "excess": 1}[which]
+        self._check(self._lib.pdr_time_kernel(self._h, w, int(launches), int(flush_bytes), C.byref(ms)))
+        return ms.value
