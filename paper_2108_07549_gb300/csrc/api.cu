@@ -1,12 +1,15 @@
 // api.cu -- the C ABI declared in include/pdr.h.
 //
 // A context holds one instance of eq. (1) on the device and runs Alg. 1 on
-// it.  pdr_solve launches one CUDA graph whose only node is a conditional
-// "while" loop; its body is one sweep (excess kernel, then edge kernel).  The
-// excess kernel's last block evaluates the stop rules and clears the loop
-// condition, so a whole solve is one launch and one host synchronisation.
-// If the runtime cannot build that graph, the same kernels are launched from
-// a host loop that reads the stop flag back every few hundred sweeps.
+// it.  Flows live in two buffers: a sweep reads f^(t) from one and the edge
+// QP writes f^(t+1) to the other, so the stop decision (taken by an extra
+// block of the edge kernel, concurrently with the QPs) can still return
+// f^(t).  pdr_solve launches one CUDA graph whose only node is a conditional
+// "while" loop over a body of kUnroll sweeps; the decision block clears the
+// loop condition, so a whole solve is one launch and one host
+// synchronisation.  If the runtime cannot build that graph, the same kernels
+// are launched from a host loop that reads the stop flag back between
+// chunks of sweeps.
 #include "pdr.h"
 #include "pdr_internal.cuh"
 
@@ -24,6 +27,8 @@ namespace {
 thread_local std::string g_create_error;
 
 int round_up4(int k) { return (k + 3) / 4 * 4; }
+
+constexpr int kUnroll = 8;  // sweeps per iteration of the graph's while loop (even)
 
 void fill_defaults(pdr_options* o)
 {
@@ -74,14 +79,19 @@ struct pdr_ctx {
     int32_t *col = nullptr, *src = nullptr, *in_eid = nullptr, *inc = nullptr, *deg = nullptr, *s = nullptr,
             *t = nullptr;
     double *u_d = nullptr, *dem_d = nullptr, *inv_scale = nullptr;
-    float *u_f = nullptr, *dem_f = nullptr, *inv_dem_f = nullptr;
+    float *u_f = nullptr, *dem_f = nullptr, *inv_dem_f = nullptr, *inv_scale_f = nullptr;
     double* inv_dem_d = nullptr;
     // state
-    float *f32 = nullptr, *h32 = nullptr;
-    double *f64 = nullptr, *h64 = nullptr;
+    float *f32[2] = {nullptr, nullptr}, *h32 = nullptr, *inv_deg_f = nullptr;
+    double *f64[2] = {nullptr, nullptr}, *h64 = nullptr, *inv_deg_d = nullptr;
+    int cur = 0;  // buffer holding the current flows
+    double* theta = nullptr;  // [m] warm starts, 8 bytes per edge covers both precisions
     int cur_prec = 0;  // precision of the current flows: 0 FP32, 1 FP64
-    double *part_h = nullptr, *part_cons = nullptr, *part_psi = nullptr, *part_cap = nullptr;
+    double* part_h = nullptr;
+    // partials typed by the working precision: 8 bytes per entry covers both
+    double *part_cons = nullptr, *part_capb = nullptr, *part_psi = nullptr, *part_cap = nullptr;
     int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
+    int64_t n_psi[2] = {1, 1};
     DevState* st = nullptr;
     DevState* hst = nullptr;  // pinned mirror
     double* trace = nullptr;
@@ -142,24 +152,31 @@ struct Prec;
 template <>
 struct Prec<float> {
     static constexpr int id = 0;
-    static float* f(pdr_ctx* c) { return c->f32; }
+    static float* f(pdr_ctx* c, int b) { return c->f32[b]; }
     static float* h(pdr_ctx* c) { return c->h32; }
     static const float* u(pdr_ctx* c) { return c->u_f; }
     static const float* dem(pdr_ctx* c) { return c->dem_f; }
     static const float* inv_dem(pdr_ctx* c) { return c->inv_dem_f; }
+    static const float* inv_scale(pdr_ctx* c) { return c->inv_scale_f; }
+    static const float* inv_deg(pdr_ctx* c) { return c->inv_deg_f; }
 };
 template <>
 struct Prec<double> {
     static constexpr int id = 1;
-    static double* f(pdr_ctx* c) { return c->f64; }
+    static double* f(pdr_ctx* c, int b) { return c->f64[b]; }
     static double* h(pdr_ctx* c) { return c->h64; }
     static const double* u(pdr_ctx* c) { return c->u_d; }
     static const double* dem(pdr_ctx* c) { return c->dem_d; }
     static const double* inv_dem(pdr_ctx* c) { return c->inv_dem_d; }
+    static const double* inv_scale(pdr_ctx* c) { return c->inv_scale; }
+    static const double* inv_deg(pdr_ctx* c) { return c->inv_deg_d; }
 };
 
+// Kernel arguments for a sweep that reads buffer (base ^ par) and writes the
+// other one.  base defaults to the buffer of the current flows.
 template <typename T>
-SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphConditionalHandle cond = 0)
+SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphConditionalHandle cond = 0, int par = 0,
+                       int base = -1)
 {
     SweepArgs<T> a{};
     const int p = Prec<T>::id;
@@ -181,14 +198,21 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.inv_dem = Prec<T>::inv_dem(ctx);
     a.u = Prec<T>::u(ctx);
     a.inv_scale = ctx->inv_scale;
-    a.f = Prec<T>::f(ctx);
+    a.inv_scale_t = Prec<T>::inv_scale(ctx);
+    a.inv_deg = Prec<T>::inv_deg(ctx);
+    a.theta = reinterpret_cast<T*>(ctx->theta);
+    const int b = ((base < 0 ? ctx->cur : base) ^ par) & 1;
+    a.f = Prec<T>::f(ctx, b);
+    a.f_out = Prec<T>::f(ctx, b ^ 1);
     a.h = Prec<T>::h(ctx);
     a.part_h = ctx->part_h;
-    a.part_cons = ctx->part_cons;
+    a.part_cons = reinterpret_cast<T*>(ctx->part_cons);
+    a.part_capb = reinterpret_cast<T*>(ctx->part_capb);
     a.part_psi = ctx->part_psi;
-    a.part_cap = ctx->part_cap;
+    a.part_cap = reinterpret_cast<T*>(ctx->part_cap);
     a.grid_v = ctx->grid_v[p];
     a.grid_e = ctx->grid_e[p];
+    a.n_psi = ctx->n_psi[p];
     a.psi_out = nullptr;
     a.st = ctx->st;
     a.trace = ctx->trace;
@@ -201,29 +225,44 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
 // Allocates the FP64 state on first use.
 pdr_status ensure_fp64(pdr_ctx* ctx)
 {
-    if (ctx->f64) return PDR_OK;
+    if (ctx->f64[0]) return PDR_OK;
     pdr_status st = PDR_OK;
     const size_t fm = (size_t)ctx->m * ctx->Kp, hn = (size_t)ctx->n * ctx->Kp;
-    ctx->f64 = dalloc<double>(ctx, fm, &st);
-    if (!ctx->f64) return st;
+    for (int b = 0; b < 2; ++b) {
+        ctx->f64[b] = dalloc<double>(ctx, fm, &st);
+        if (!ctx->f64[b]) return st;
+        CK(cudaMemsetAsync(ctx->f64[b], 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
+    }
     ctx->h64 = dalloc<double>(ctx, hn, &st);
     if (!ctx->h64) return st;
-    CK(cudaMemsetAsync(ctx->f64, 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
     CK(cudaMemsetAsync(ctx->h64, 0, sizeof(double) * (hn ? hn : 1), ctx->stream));
     return PDR_OK;
 }
 
 pdr_status ensure_fp32(pdr_ctx* ctx)
 {
-    if (ctx->f32) return PDR_OK;
+    if (ctx->f32[0]) return PDR_OK;
     pdr_status st = PDR_OK;
     const size_t fm = (size_t)ctx->m * ctx->Kp, hn = (size_t)ctx->n * ctx->Kp;
-    ctx->f32 = dalloc<float>(ctx, fm, &st);
-    if (!ctx->f32) return st;
+    for (int b = 0; b < 2; ++b) {
+        ctx->f32[b] = dalloc<float>(ctx, fm, &st);
+        if (!ctx->f32[b]) return st;
+        CK(cudaMemsetAsync(ctx->f32[b], 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+    }
     ctx->h32 = dalloc<float>(ctx, hn, &st);
     if (!ctx->h32) return st;
-    CK(cudaMemsetAsync(ctx->f32, 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
     CK(cudaMemsetAsync(ctx->h32, 0, sizeof(float) * (hn ? hn : 1), ctx->stream));
+    return PDR_OK;
+}
+
+// Moves the current flows into buffer 0 (the graphs are captured for it).
+template <typename T>
+pdr_status flows_to_buffer0(pdr_ctx* ctx)
+{
+    if (ctx->cur == 0) return PDR_OK;
+    const size_t bytes = sizeof(T) * (size_t)ctx->m * ctx->Kp;
+    if (bytes) CK(cudaMemcpyAsync(Prec<T>::f(ctx, 0), Prec<T>::f(ctx, 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->cur = 0;
     return PDR_OK;
 }
 
@@ -233,13 +272,17 @@ int start_prec(const pdr_options& o) { return o.precision == PDR_PREC_FP64 ? 1 :
 template <typename T>
 pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr)
 {
+    if (!psi_out) {
+        // new flows: the edge QPs start their root search cold
+        CK(cudaMemsetAsync(ctx->theta, 0, sizeof(double) * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
+    }
     SweepArgs<T> a = make_args<T>(ctx, MODE_PSI);
     a.psi_out = psi_out;
     if (ctx->m > 0) {
         CK(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
     } else {
-        CK(cudaMemsetAsync(ctx->part_psi, 0, sizeof(double) * ctx->grid_e[Prec<T>::id], ctx->stream));
-        CK(cudaMemsetAsync(ctx->part_cap, 0, sizeof(double) * ctx->grid_e[Prec<T>::id], ctx->stream));
+        CK(cudaMemsetAsync(ctx->part_psi, 0, sizeof(double) * ctx->n_psi[Prec<T>::id], ctx->stream));
+        CK(cudaMemsetAsync(ctx->part_cap, 0, sizeof(double) * ctx->n_psi[Prec<T>::id], ctx->stream));
     }
     return PDR_OK;
 }
@@ -266,7 +309,6 @@ pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise)
     v.evals = fresh ? 0 : ctx->hst->evals;
     v.stop = 0;
     v.reason = 0;
-    v.ticket = 0;
     v.stop_on_rise = stop_on_rise;
     set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, v);
     CK(cudaGetLastError());
@@ -303,11 +345,14 @@ pdr_status build_graph(pdr_ctx* ctx)
         cudaSuccess)
         goto fail;
     {
-        SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 1, h);
-        cudaError_t e1 = launch_excess<T>(a, ctx->cap_stream);
-        cudaError_t e2 = ctx->m > 0 ? launch_edge<T>(a, ctx->cfg[p], ctx->cap_stream) : cudaSuccess;
+        cudaError_t e1 = cudaSuccess;
+        for (int q = 0; q < kUnroll && e1 == cudaSuccess; ++q) {
+            SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 1, h, q & 1, 0);
+            e1 = launch_excess<T>(a, ctx->cap_stream);
+            if (e1 == cudaSuccess) e1 = launch_edge<T>(a, ctx->cfg[p], ctx->cap_stream);
+        }
         cudaError_t e3 = cudaStreamEndCapture(ctx->cap_stream, &captured);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) goto fail;
+        if (e1 != cudaSuccess || e3 != cudaSuccess) goto fail;
     }
     if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) goto fail;
     ctx->graph[p] = g;
@@ -322,31 +367,38 @@ fail:
     return PDR_OK;  // the host loop takes over
 }
 
-// One phase of Alg. 1 in precision T, from the state set by init_state.
+// One phase of Alg. 1 in precision T, from the state set by init_state
+// (whose t is t_start).  Afterwards the current flows f^(t) sit in buffer
+// (t - t_start) mod 2: every sweep that does not stop swaps the buffers.
 template <typename T>
-pdr_status run_phase(pdr_ctx* ctx)
+pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
 {
     const int p = Prec<T>::id;
+    pdr_status s = flows_to_buffer0<T>(ctx);
+    if (s != PDR_OK) return s;
     if (!ctx->graph_tried[p]) {
-        pdr_status s = build_graph<T>(ctx);
+        s = build_graph<T>(ctx);
         if (s != PDR_OK) return s;
     }
     if (ctx->graph_ok[p]) {
         CK(cudaGraphLaunch(ctx->exec[p], ctx->stream));
-        return read_state(ctx);
-    }
-    // host loop fallback: chunks of sweeps, then a look at the stop flag
-    const int chunk = 256;
-    SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0);
-    for (;;) {
-        for (int q = 0; q < chunk; ++q) {
-            CK(launch_excess<T>(a, ctx->stream));
-            if (ctx->m > 0) CK(launch_edge<T>(a, ctx->cfg[p], ctx->stream));
+        s = read_state(ctx);
+    } else {
+        // host loop fallback: chunks of an even number of sweeps, then a look
+        // at the stop flag (a chunk that does not stop leaves f in buffer 0)
+        for (;;) {
+            for (int q = 0; q < 32 * kUnroll; ++q) {
+                SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, q & 1, 0);
+                CK(launch_excess<T>(a, ctx->stream));
+                CK(launch_edge<T>(a, ctx->cfg[p], ctx->stream));
+            }
+            s = read_state(ctx);
+            if (s != PDR_OK || ctx->hst->stop) break;
         }
-        pdr_status s = read_state(ctx);
-        if (s != PDR_OK) return s;
-        if (ctx->hst->stop) return PDR_OK;
     }
+    if (s != PDR_OK) return s;
+    ctx->cur = (int)((ctx->hst->t - t_start) & 1);
+    return PDR_OK;
 }
 
 template <typename T>
@@ -438,8 +490,9 @@ void pdr_destroy(pdr_ctx* ctx)
     destroy_graphs(ctx);
     void* dev[] = {ctx->row_ptr, ctx->in_ptr, ctx->inc_ptr, ctx->inc, ctx->work, ctx->col, ctx->src, ctx->in_eid,
                    ctx->deg, ctx->s, ctx->t,
-                   ctx->u_d, ctx->dem_d, ctx->inv_scale, ctx->u_f, ctx->dem_f, ctx->inv_dem_f, ctx->inv_dem_d, ctx->f32, ctx->h32, ctx->f64,
-                   ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_psi, ctx->part_cap, ctx->st, ctx->trace,
+                   ctx->u_d, ctx->dem_d, ctx->inv_scale, ctx->u_f, ctx->dem_f, ctx->inv_dem_f, ctx->inv_dem_d,
+                   ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
+                   ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta,
                    ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -518,11 +571,13 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     }
     ctx->cfg[0] = cfg32;
     ctx->cfg[1] = cfg64;
-    ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms);
-    ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms);
+    ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms, excess_resident_blocks<float>());
+    ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms, excess_resident_blocks<double>());
     ctx->grid_e[0] = edge_grid<float>(cfg32, m, ctx->num_sms);
     ctx->grid_e[1] = cfg64 >= 0 ? edge_grid<double>(cfg64, m, ctx->num_sms) : 1;
-    ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms);
+    ctx->n_psi[0] = edge_parts<float>(cfg32, ctx->grid_e[0]);
+    ctx->n_psi[1] = cfg64 >= 0 ? edge_parts<double>(cfg64, ctx->grid_e[1]) : 1;
+    ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms, 8);
     {
         int64_t we = (m * 32 + 255) / 256;
         int64_t cap = (int64_t)ctx->num_sms * 8;
@@ -549,16 +604,21 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->u_d, double, m);
     ALLOC(ctx->u_f, float, m);
     ALLOC(ctx->inv_scale, double, m);
+    ALLOC(ctx->inv_scale_f, float, m);
+    ALLOC(ctx->inv_deg_f, float, n);
+    ALLOC(ctx->inv_deg_d, double, n);
+    ALLOC(ctx->theta, double, m);
     ALLOC(ctx->dem_d, double, Kp);
     ALLOC(ctx->dem_f, float, Kp);
     ALLOC(ctx->inv_dem_d, double, Kp);
     ALLOC(ctx->inv_dem_f, float, Kp);
     const int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
-    const int ge = ctx->grid_e[0] > ctx->grid_e[1] ? ctx->grid_e[0] : ctx->grid_e[1];
+    const int64_t np = ctx->n_psi[0] > ctx->n_psi[1] ? ctx->n_psi[0] : ctx->n_psi[1];
     ALLOC(ctx->part_h, double, gv);
     ALLOC(ctx->part_cons, double, gv);
-    ALLOC(ctx->part_psi, double, ge);
-    ALLOC(ctx->part_cap, double, ge);
+    ALLOC(ctx->part_capb, double, gv);
+    ALLOC(ctx->part_psi, double, np);
+    ALLOC(ctx->part_cap, double, np);
     ALLOC(ctx->st, DevState, 1);
     ctx->trace_cap = o.trace_len;
     ALLOC(ctx->trace, double, ctx->trace_cap > 0 ? ctx->trace_cap : 1);
@@ -592,9 +652,10 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
         }
     const double ubar = upos ? usum / (double)upos : 1.0;
     std::vector<double> inv(m > 0 ? m : 1);
-    std::vector<float> uf(m > 0 ? m : 1);
+    std::vector<float> uf(m > 0 ? m : 1), invf(m > 0 ? m : 1);
     for (int64_t e = 0; e < m; ++e) {
         inv[e] = 1.0 / (u[e] > ubar ? u[e] : ubar);
+        invf[e] = (float)inv[e];
         uf[e] = (float)u[e];
     }
     CKC(cudaMemcpyAsync(ctx->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, ctx->stream));
@@ -603,6 +664,7 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
         CKC(cudaMemcpyAsync(ctx->u_d, u, sizeof(double) * m, cudaMemcpyHostToDevice, ctx->stream));
         CKC(cudaMemcpyAsync(ctx->u_f, uf.data(), sizeof(float) * m, cudaMemcpyHostToDevice, ctx->stream));
         CKC(cudaMemcpyAsync(ctx->inv_scale, inv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaMemcpyAsync(ctx->inv_scale_f, invf.data(), sizeof(float) * m, cudaMemcpyHostToDevice, ctx->stream));
     }
     CKC(cudaMemcpyAsync(ctx->s, sp.data(), sizeof(int32_t) * Kp, cudaMemcpyHostToDevice, ctx->stream));
     CKC(cudaMemcpyAsync(ctx->t, tp.data(), sizeof(int32_t) * Kp, cudaMemcpyHostToDevice, ctx->stream));
@@ -619,6 +681,15 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
         CKC(cudaStreamSynchronize(ctx->stream));
         for (int k = 0; k < K; ++k)
             if (hdeg[s[k]] == 0 || hdeg[t[k]] == 0) ctx->isolated = true;
+        std::vector<double> idd_v(n);
+        std::vector<float> idf_v(n);
+        for (int32_t i = 0; i < n; ++i) {
+            idd_v[i] = hdeg[i] > 0 ? 1.0 / (double)hdeg[i] : 0.0;
+            idf_v[i] = hdeg[i] > 0 ? 1.0f / (float)hdeg[i] : 0.0f;
+        }
+        CKC(cudaMemcpyAsync(ctx->inv_deg_d, idd_v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaMemcpyAsync(ctx->inv_deg_f, idf_v.data(), sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CKC(cudaStreamSynchronize(ctx->stream));
     }
     ctx->cur_prec = start_prec(o);
     st = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
@@ -675,8 +746,9 @@ pdr_status pdr_reset(pdr_ctx* ctx)
     pdr_status s = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
     if (s != PDR_OK) return s;
     const size_t fm = (size_t)ctx->m * ctx->Kp;
-    if (ctx->cur_prec) CK(cudaMemsetAsync(ctx->f64, 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
-    else CK(cudaMemsetAsync(ctx->f32, 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+    ctx->cur = 0;
+    if (ctx->cur_prec) CK(cudaMemsetAsync(ctx->f64[0], 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
+    else CK(cudaMemsetAsync(ctx->f32[0], 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
     s = refresh_psi_current(ctx);
     if (s != PDR_OK) return s;
     s = init_state(ctx, true, 0);
@@ -690,7 +762,9 @@ pdr_status pdr_set_flows(pdr_ctx* ctx, const double* f)
     if (ctx->opt.precision != PDR_PREC_FP32_FP64TAIL) ctx->cur_prec = start_prec(ctx->opt);
     pdr_status s = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
     if (s != PDR_OK) return s;
-    s = ctx->cur_prec ? copy_rows_in<double>(ctx, f, ctx->m, ctx->f64) : copy_rows_in<float>(ctx, f, ctx->m, ctx->f32);
+    ctx->cur = 0;
+    s = ctx->cur_prec ? copy_rows_in<double>(ctx, f, ctx->m, ctx->f64[0])
+                      : copy_rows_in<float>(ctx, f, ctx->m, ctx->f32[0]);
     if (s != PDR_OK) return s;
     s = refresh_psi_current(ctx);
     if (s != PDR_OK) return s;
@@ -702,8 +776,8 @@ pdr_status pdr_set_flows(pdr_ctx* ctx, const double* f)
 pdr_status pdr_flows(pdr_ctx* ctx, double* f)
 {
     if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
-    return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64, ctx->m, f)
-                         : copy_rows_out<float>(ctx, ctx->f32, ctx->m, f);
+    return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64[ctx->cur], ctx->m, f)
+                         : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
 }
 
 pdr_status pdr_heights(pdr_ctx* ctx, double* h)
@@ -743,8 +817,13 @@ pdr_status pdr_congestion(pdr_ctx* ctx, double* psi)
 pdr_status pdr_objective(pdr_ctx* ctx, double* z)
 {
     if (!ctx || !z) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "z is NULL") : PDR_ERR_INVALID_ARG;
-    if (ctx->cur_prec) CK(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
-    else CK(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+    if (ctx->cur_prec) {
+        CK(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+        CK(launch_finalize<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
+    } else {
+        CK(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+        CK(launch_finalize<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
+    }
     pdr_status s = read_state(ctx);
     if (s != PDR_OK) return s;
     *z = ctx->hst->z;
@@ -769,16 +848,18 @@ pdr_status pdr_sweeps(pdr_ctx* ctx, int64_t count)
     pdr_status s = init_state(ctx, true, 0);
     if (s != PDR_OK) return s;
     for (int64_t q = 0; q < count; ++q) {
+        const int par = (int)(q & 1);
         if (ctx->cur_prec) {
-            SweepArgs<double> a = make_args<double>(ctx, MODE_FORCED);
+            SweepArgs<double> a = make_args<double>(ctx, MODE_FORCED, 0, 0, par);
             CK(launch_excess<double>(a, ctx->stream));
-            if (ctx->m > 0) CK(launch_edge<double>(a, ctx->cfg[1], ctx->stream));
+            CK(launch_edge<double>(a, ctx->cfg[1], ctx->stream));
         } else {
-            SweepArgs<float> a = make_args<float>(ctx, MODE_FORCED);
+            SweepArgs<float> a = make_args<float>(ctx, MODE_FORCED, 0, 0, par);
             CK(launch_excess<float>(a, ctx->stream));
-            if (ctx->m > 0) CK(launch_edge<float>(a, ctx->cfg[0], ctx->stream));
+            CK(launch_edge<float>(a, ctx->cfg[0], ctx->stream));
         }
     }
+    ctx->cur ^= (int)(count & 1);
     return read_state(ctx);
 }
 
@@ -790,7 +871,7 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     pdr_status s = init_state(ctx, true, (tail && ctx->cur_prec == 0) ? 1 : 0);
     if (s != PDR_OK) return s;
     int64_t sweeps32 = 0;
-    s = ctx->cur_prec ? run_phase<double>(ctx) : run_phase<float>(ctx);
+    s = ctx->cur_prec ? run_phase<double>(ctx, 0) : run_phase<float>(ctx, 0);
     if (s != PDR_OK) return s;
     if (ctx->cur_prec == 0) sweeps32 = ctx->hst->t;
     const int r = ctx->hst->reason;
@@ -798,13 +879,14 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
         // FP64 tail from the FP32 flows
         s = ensure_fp64(ctx);
         if (s != PDR_OK) return s;
-        CK(launch_convert_f32_to_f64(ctx->f32, ctx->f64, (int64_t)ctx->m * ctx->Kp, ctx->stream));
+        CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
+        ctx->cur = 0;
         ctx->cur_prec = 1;
         s = refresh_psi<double>(ctx);
         if (s != PDR_OK) return s;
         s = init_state(ctx, false, 0);
         if (s != PDR_OK) return s;
-        s = run_phase<double>(ctx);
+        s = run_phase<double>(ctx, ctx->hst->t);
         if (s != PDR_OK) return s;
     }
     pdr_result res{};
@@ -864,14 +946,11 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         return ctx->fail(PDR_ERR_INVALID_ARG, "which must be 0 or 1, launches >= 1, flush_bytes >= 0");
     if (which == 0 && ctx->m == 0) return ctx->fail(PDR_ERR_INVALID_ARG, "no edges");
     const bool f64 = ctx->cur_prec == 1;
-    const size_t fbytes = (size_t)ctx->m * ctx->Kp * (f64 ? sizeof(double) : sizeof(float));
-    void* backup = nullptr;
     void* flush = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double total = 0.0;
     pdr_status status = PDR_OK;
     auto cleanup = [&]() {
-        if (backup) cudaFree(backup);
         if (flush) cudaFree(flush);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -887,11 +966,6 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
     } while (0)
     CKT(cudaEventCreate(&e0));
     CKT(cudaEventCreate(&e1));
-    void* fcur = f64 ? (void*)ctx->f64 : (void*)ctx->f32;
-    if (which == 0) {
-        CKT(cudaMalloc(&backup, fbytes ? fbytes : 1));
-        CKT(cudaMemcpyAsync(backup, fcur, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
     if (flush_bytes > 0) CKT(cudaMalloc(&flush, (size_t)flush_bytes));
     // heights of the current flows for the QP launches
     if (f64) CKT(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
@@ -900,6 +974,8 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         if (flush) CKT(cudaMemsetAsync(flush, q & 0xff, (size_t)flush_bytes, ctx->stream));
         CKT(cudaEventRecord(e0, ctx->stream));
         if (which == 0) {
+            // reads the current flows, writes the other buffer: every launch
+            // repeats the same sweep
             if (f64) CKT(launch_edge<double>(make_args<double>(ctx, MODE_FORCED), ctx->cfg[1], ctx->stream));
             else CKT(launch_edge<float>(make_args<float>(ctx, MODE_FORCED), ctx->cfg[0], ctx->stream));
         } else {
@@ -912,8 +988,7 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         CKT(cudaEventElapsedTime(&el, e0, e1));
         total += el;
     }
-    if (which == 0) {
-        CKT(cudaMemcpyAsync(fcur, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    {
         pdr_status s = refresh_psi_current(ctx);
         if (s != PDR_OK) {
             cleanup();

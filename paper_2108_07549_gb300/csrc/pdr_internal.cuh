@@ -38,8 +38,8 @@ enum : int {
     STOP_STALL = 5
 };
 
-// Solver state that lives on the device and is updated by the last block of
-// the excess kernel, so the sweep loop never returns to the host.
+// Solver state that lives on the device and is updated by the decision block
+// of the edge kernel, so the sweep loop never returns to the host.
 struct DevState {
     double z;          // objective z^(t) of the current flows
     double z_prev;     // objective of the previous sweep (+inf at the start)
@@ -55,8 +55,8 @@ struct DevState {
     long long evals;      // objective evaluations written to the trace
     int stop;             // 1 once a stop rule fired
     int reason;           // STOP_* code
-    unsigned int ticket;  // last-block counter of the excess kernel
     int stop_on_rise;     // 1: z^(t) >= z^(t-1) stops (the FP32 rounding floor)
+    int pad;
 };
 
 template <typename T>
@@ -78,13 +78,24 @@ struct SweepArgs {
     const T* inv_dem;  // [Kp] 1/d_k, 0 in the padding
     const T* u;
     const double* inv_scale;  // [m] 1 / max(u_e, mean positive u)
-    T* f;
+    const T* inv_scale_t;     // the same in the working precision
+    const T* inv_deg;   // [n] 1/delta_i (0 for isolated vertices)
+    T* f;               // flows read by this sweep, f^(t)
+    T* f_out;           // flows written by the edge QP, f^(t+1) (the other buffer)
     T* h;
-    double* part_h;     // [grid_v] sum delta h^2 per excess block
-    double* part_cons;  // [grid_v] max |Delta|/d per excess block
-    double* part_psi;   // [grid_e] sum psi^2 per edge block
-    double* part_cap;   // [grid_e] max psi/scale per edge block
+    T* theta;           // [m] last root psi'/2 of each edge QP (0 = none); warm start
+    // Objective partials.  Edge kernels write one partial per warp (lane-group
+    // form) or per block (block form): the sum of psi^2 as an accumulator
+    // pair and the largest psi/scale.  Each excess block adds a fixed slice
+    // of those to its own sum of delta h^2 and writes one FP64 value; the
+    // last excess block reduces those in FP64.
+    double* part_h;     // [grid_v] per excess block: slice of psi^2 + delta h^2
+    T* part_cons;       // [grid_v] per excess block: max |Delta|/d
+    T* part_capb;       // [grid_v] per excess block: max psi/scale of its slice
+    void* part_psi;     // [n_psi] per edge warp/block: sum psi^2 (float2 pair or double)
+    T* part_cap;        // [n_psi] per edge warp/block: max psi/scale
     int32_t grid_v, grid_e;
+    int64_t n_psi;      // number of edge partials
     T* psi_out;         // optional [m] congestion output of the edge kernel
     DevState* st;
     double* trace;
@@ -96,13 +107,21 @@ struct SweepArgs {
 // Launchers (sweep.cu).  Each returns the launch error.
 template <typename T>
 cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream);
+// Objective reduction and stop decision on their own (one block); the edge
+// kernel does the same work in its extra block during a sweep.
+template <typename T>
+cudaError_t launch_finalize(const SweepArgs<T>& a, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream);
 template <typename T>
 int edge_config(int Kp);  // picks the edge-kernel variant for a row length
 template <typename T>
 int edge_grid(int cfg, int64_t m, int num_sms);  // grid size of that variant
-int excess_grid(int32_t n, int Kp, int vec, int num_sms);
+template <typename T>
+int64_t edge_parts(int cfg, int grid);  // number of partials that grid writes
+int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
+template <typename T>
+int excess_resident_blocks();  // excess blocks resident per SM (occupancy)
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream);
 
 // Adjacency builder (adjacency.cu): in-adjacency, incidence lists, edge

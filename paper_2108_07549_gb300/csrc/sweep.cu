@@ -1,14 +1,18 @@
 // sweep.cu -- the two kernels of one PDR sweep (Alg. 1 loop body).
 //
 //  excess_kernel  eq. (3) + eq. (3h): Delta_ik = sum_in f - sum_out f + hat-Delta_ik,
-//                 eq. (2): h_ik = Delta_ik / delta_i, then the objective of
-//                 Alg. 1 and the stop test, decided on the device by the last
-//                 block to finish (deterministic fixed-order FP64 reduction of
-//                 per-block partials, no floating-point atomics).
+//                 eq. (2): h_ik = Delta_ik / delta_i, and per-block partials
+//                 of the objective of Alg. 1.
 //  edge_kernel    Alg. 2 on every edge: the exact minimiser of eq. (10),
 //                 f' = max(0, c - psi'/2) with c_k = f_k + (h_ik - h_jk)/2,
-//                 followed by the congestion psi = max(0, sum_k f' - u)
-//                 (eq. (41)) of the stored new flows.
+//                 written to the other flow buffer, followed by the
+//                 congestion psi = max(0, sum_k f' - u) (eq. (41)) of the
+//                 stored new flows.  One extra block of the same launch
+//                 reduces the objective partials in FP64 (fixed order, no
+//                 floating-point atomics) and takes the stop decision while
+//                 the other blocks solve the edge QPs; if it stops, f^(t) in
+//                 the input buffer is the result and f^(t+1) is discarded,
+//                 exactly as Alg. 1 returns f^(t).
 //
 // Alg. 2 sorts the positive potentials to find the congested root.  Here the
 // same root is found without a sort: with theta = psi'/2 and the active set
@@ -57,47 +61,25 @@ __device__ __forceinline__ void unpack(const double2& v, double* x)
 __device__ __forceinline__ float4 pack4(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
 __device__ __forceinline__ double2 pack4(const double* x) { return make_double2(x[0], x[1]); }
 
-__device__ __forceinline__ double warp_sum(double x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-__device__ __forceinline__ double warp_max(double x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
-    return x;
-}
-
-// Block-wide (sum, max) of non-negative maxima; the result is valid in thread 0.
-__device__ void block_sum_max(double& s, double& mx, double* smem)
-{
-    s = warp_sum(s);
-    mx = warp_max(mx);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        smem[w] = s;
-        smem[32 + w] = mx;
-    }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = blockDim.x >> 5;
-        s = l < nw ? smem[l] : 0.0;
-        mx = l < nw ? smem[32 + l] : 0.0;
-        s = warp_sum(s);
-        mx = warp_max(mx);
-    }
-    __syncthreads();
-}
-
 // Sum over the G lanes of an aligned lane group (xor offsets below G stay
-// inside the group).  Every lane of the warp must call it.
+// inside the group).  Every lane of the warp must call it.  IEEE addition is
+// commutative, so every lane of the group ends with the same value.
 template <int G, typename X>
 __device__ __forceinline__ X group_sum(X x)
 {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+template <typename X>
+__device__ __forceinline__ X warp_max(X x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const X y = __shfl_xor_sync(kFull, x, o);
+        x = y > x ? y : x;
+    }
     return x;
 }
 
@@ -128,19 +110,104 @@ __device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
     __syncthreads();
 }
 
+// ------------------------------------------------------------------ objective accumulators
+//
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the per-element
+// sums behind the objective stay off the FP64 pipe in FP32 mode: terms are
+// formed in FP32 and summed as an unevaluated pair hi + lo with the
+// error-free TwoSum transformation (Knuth; Dekker 1971), which keeps about 44
+// significant bits.  Only the cross-block reduction and the stop decision
+// run in FP64.  In FP64 mode the accumulator is a plain double.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    struct V {
+        float hi, lo;
+    };
+    using S = float2;  // stored form
+    static __device__ __forceinline__ V zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ V add(V a, V b)
+    {
+        const float s = a.hi + b.hi;
+        const float bb = s - a.hi;
+        const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+        const float hi = s + e;
+        return {hi, e - (hi - s)};
+    }
+    static __device__ __forceinline__ V add(V a, float b) { return add(a, V{b, 0.f}); }
+    static __device__ __forceinline__ V shfl(V a, int o)
+    {
+        return {__shfl_xor_sync(kFull, a.hi, o), __shfl_xor_sync(kFull, a.lo, o)};
+    }
+    static __device__ __forceinline__ S store(V a) { return make_float2(a.hi, a.lo); }
+    static __device__ __forceinline__ V load(const S* p) { const float2 x = __ldcg(p); return {x.x, x.y}; }
+    static __device__ __forceinline__ double to_double(V a) { return (double)a.hi + (double)a.lo; }
+};
+
+template <>
+struct Acc<double> {
+    using V = double;
+    using S = double;
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V shfl(V a, int o) { return __shfl_xor_sync(kFull, a, o); }
+    static __device__ __forceinline__ S store(V a) { return a; }
+    static __device__ __forceinline__ V load(const S* p) { return __ldcg(p); }
+    static __device__ __forceinline__ double to_double(V a) { return a; }
+};
+
+// Warp reduction of (sum, max): the result is valid in lane 0 (lane 0 always
+// combines in the same order, so it is deterministic).
+template <typename T>
+__device__ __forceinline__ void warp_acc_max(typename Acc<T>::V& z, T& mx)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
+    mx = warp_max(mx);
+}
+
+// Block reduction of (sum, max, max); the result is valid in thread 0.
+template <typename T>
+__device__ void block_acc_max2(typename Acc<T>::V& z, T& m1, T& m2)
+{
+    using V = typename Acc<T>::V;
+    __shared__ V sz[32];
+    __shared__ T s1[32], s2[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
+    m1 = warp_max(m1);
+    m2 = warp_max(m2);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sz[w] = z;
+        s1[w] = m1;
+        s2[w] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int q = 1; q < nw; ++q) {
+            z = Acc<T>::add(z, sz[q]);
+            m1 = s1[q] > m1 ? s1[q] : m1;
+            m2 = s2[q] > m2 ? s2[q] : m2;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ objective and stop rules
 
 // Alg. 1: z = 1/2 sum psi^2 + 1/2 sum delta h^2 and the stop test, run by one
 // thread after every partial of this sweep is final.
 template <typename T>
-__device__ void finalize(const SweepArgs<T>& a, double zh, double zp, double cons, double cap)
+__device__ void finalize(const SweepArgs<T>& a, double zsum, double cons, double cap)
 {
     DevState* st = a.st;
-    const double z = 0.5 * (zp + zh);
+    const double z = 0.5 * zsum;
     st->z = z;
     st->cap_rel = cap;
     st->cons_rel = cons;
-    st->ticket = 0;
     if (a.mode == MODE_EVAL) return;
     const double dz = z - st->z_prev;
     st->dz = dz;
@@ -180,35 +247,97 @@ __device__ void finalize(const SweepArgs<T>& a, double zh, double zp, double con
     }
 }
 
+// FP64 reduction of the excess blocks' partials in a fixed order, then the
+// objective and the stop test.  Run by one whole block.
+template <typename T>
+__device__ void reduce_and_finalize(const SweepArgs<T>& a)
+{
+    __shared__ double sz[32];
+    __shared__ T sm1[32], sm2[32];
+    double zs = 0.0;
+    T cm = T(0), cp = T(0);
+    for (int b = threadIdx.x; b < a.grid_v; b += blockDim.x) {
+        zs += __ldcg(a.part_h + b);
+        const T c1 = __ldcg(a.part_cons + b);
+        const T c2 = __ldcg(a.part_capb + b);
+        cm = c1 > cm ? c1 : cm;
+        cp = c2 > cp ? c2 : cp;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(kFull, zs, o);
+    cm = warp_max(cm);
+    cp = warp_max(cp);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sz[w] = zs;
+        sm1[w] = cm;
+        sm2[w] = cp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int q = 1; q < nw; ++q) {
+            zs += sz[q];
+            cm = sm1[q] > cm ? sm1[q] : cm;
+            cp = sm2[q] > cp ? sm2[q] : cp;
+        }
+        finalize(a, zs, (double)cm, (double)cp);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) finalize_kernel(SweepArgs<T> a)
+{
+    reduce_and_finalize(a);
+}
+
 // ------------------------------------------------------------------ excess and heights
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
+    using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
-    __shared__ double smem[64];
-    __shared__ int s_last;
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) {
-        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
-        return;
-    }
+    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
     const uint32_t vpr = (uint32_t)(a.Kp / N);
     const uint64_t total = (uint64_t)a.n * vpr;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    double zacc = 0.0, cons = 0.0;
+    typename A::V zacc = A::zero();
+    T cons = T(0);
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        const uint32_t i = (uint32_t)(idx / vpr);
-        const uint32_t v = (uint32_t)(idx - (uint64_t)i * vpr);
+        uint32_t i, v;
+        if (total <= 0xffffffffull) {
+            i = (uint32_t)idx / vpr;
+            v = (uint32_t)idx - i * vpr;
+        } else {
+            i = (uint32_t)(idx / vpr);
+            v = (uint32_t)(idx - (uint64_t)i * vpr);
+        }
         T acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = T(0);
         // incidence list: in-edges e (added), then out-edges ~e (subtracted),
-        // four rows in flight at a time; the additions keep list order
+        // up to eight rows in flight; the additions keep list order
         const int64_t q0 = a.inc_ptr[i], q1 = a.inc_ptr[i + 1];
         int64_t q = q0;
-        for (; q + 4 <= q1; q += 4) {
+        for (; q + 8 <= q1; q += 8) {
+            int32_t ev[8];
+            T x[8][N];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ev[u] = a.inc[q + u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t e = ev[u] >= 0 ? ev[u] : ~ev[u];
+                unpack(reinterpret_cast<const VT*>(a.f + e * a.Kp)[v], x[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] = ev[u] >= 0 ? acc[j] + x[u][j] : acc[j] - x[u][j];
+        }
+        if (q + 4 <= q1) {
             int32_t ev[4];
             T x[4][N];
 #pragma unroll
@@ -222,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int j = 0; j < N; ++j) acc[j] = ev[u] >= 0 ? acc[j] + x[u][j] : acc[j] - x[u][j];
+            q += 4;
         }
         for (; q < q1; ++q) {
             const int32_t ev = a.inc[q];
@@ -238,46 +368,40 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
             if (a.s[k] == (int)i) acc[j] += a.dem[k];
             else if (a.t[k] == (int)i) acc[j] -= a.dem[k];
         }
-        const int dg = (int)(q1 - q0);
-        const T dgt = T(dg);
+        const T dgt = T(q1 - q0);
+        const T idg = a.inv_deg[i];
         T hv[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) hv[j] = dg > 0 ? acc[j] / dgt : T(0);
+        for (int j = 0; j < N; ++j) hv[j] = acc[j] * idg;
         reinterpret_cast<VT*>(a.h + (int64_t)i * a.Kp)[v] = pack4(hv);
-        // delta_i h^2 is formed in the working precision and accumulated in
-        // FP64; the pad entries have h = 0 and 1/d = 0, so they add nothing
-        T cmax = T(0);
+        // delta_i h^2 and |Delta|/d; pad entries have h = 0 and 1/d = 0
+        T zt = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            zacc += (double)(dgt * hv[j] * hv[j]);
+            zt += dgt * hv[j] * hv[j];
             const T r = fabs(acc[j]) * a.inv_dem[k0 + j];
-            cmax = r > cmax ? r : cmax;
+            cons = r > cons ? r : cons;
         }
-        cons = fmax(cons, (double)cmax);
+        zacc = A::add(zacc, zt);
     }
-    block_sum_max(zacc, cons, smem);
+    // this block's fixed slice of the edge kernel's psi partials
+    T capb = T(0);
+    {
+        const int64_t lo = (int64_t)blockIdx.x * a.n_psi / gridDim.x;
+        const int64_t hi = (int64_t)(blockIdx.x + 1) * a.n_psi / gridDim.x;
+        const typename A::S* pp = reinterpret_cast<const typename A::S*>(a.part_psi);
+        for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+            zacc = A::add(zacc, A::load(pp + b));
+            const T c = __ldcg(a.part_cap + b);
+            capb = c > capb ? c : capb;
+        }
+    }
+    block_acc_max2<T>(zacc, cons, capb);
     if (threadIdx.x == 0) {
-        a.part_h[blockIdx.x] = zacc;
+        a.part_h[blockIdx.x] = A::to_double(zacc);
         a.part_cons[blockIdx.x] = cons;
-        __threadfence();
-        const unsigned prev = atomicAdd(&a.st->ticket, 1u);
-        s_last = (prev == gridDim.x - 1);
+        a.part_capb[blockIdx.x] = capb;
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double zh = 0.0, cmax = 0.0, zp = 0.0, capmax = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        zh += __ldcg(a.part_h + b);
-        cmax = fmax(cmax, __ldcg(a.part_cons + b));
-    }
-    for (int b = threadIdx.x; b < a.grid_e; b += blockDim.x) {
-        zp += __ldcg(a.part_psi + b);
-        capmax = fmax(capmax, __ldcg(a.part_cap + b));
-    }
-    block_sum_max(zh, cmax, smem);
-    block_sum_max(zp, capmax, smem);
-    if (threadIdx.x == 0) finalize(a, zh, zp, cmax, capmax);
 }
 
 // ------------------------------------------------------------------ edge QP, lane-group form
@@ -291,23 +415,29 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
     constexpr int GPW = 32 / G;  // groups per warp
-    __shared__ double smem[64];
+    using A = Acc<T>;
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;
+    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (blockIdx.x == gridDim.x - 1) {               // the decision block
+        if (a.mode != MODE_PSI) reduce_and_finalize(a);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int gw = lane / G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nwarps = ((int64_t)(gridDim.x - 1) * blockDim.x) >> 5;
     const int vpr = a.Kp / N;
     const bool psi_only = (a.mode == MODE_PSI);
-    double zpsi = 0.0, capmax = 0.0;
+    typename A::V zpsi = A::zero();
+    T capmax = T(0);
     for (int64_t base = warp * GPW; base < a.m; base += nwarps * GPW) {
         const int64_t e = base + gw;
         const bool valid = e < a.m;
         const T ue = valid ? a.u[e] : T(0);
         T c[V][N];
-        T* frow = a.f + (valid ? e : 0) * a.Kp;
+        const T* frow = a.f + (valid ? e : 0) * a.Kp;
+        T* orow = a.f_out + (valid ? e : 0) * a.Kp;
         if (psi_only) {
 #pragma unroll
             for (int q = 0; q < V; ++q) {
@@ -341,22 +471,43 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
         }
         T theta = T(0);
         if (!psi_only) {
-            // s = sum_k max(0, c_k) and |{c_k > 0}|
-            T sp = T(0);
-            int np = 0;
+            // One pass gives s = sum_k max(0, c_k), |{c_k > 0}|, and the same
+            // two sums above a warm start w slightly below the previous
+            // sweep's root.  g(theta) = sum_k max(0, c_k - theta) - u - 2 theta
+            // decreases in theta and vanishes at the root, so g(w) >= 0
+            // certifies w <= root and the active set lies inside {c > w}.
+            const T w = valid ? a.theta[e] * T(0.999) : T(0);
+            T sp = T(0), sw = T(0);
+            int np = 0, nw = 0;
 #pragma unroll
             for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int j = 0; j < N; ++j)
-                    if (c[q][j] > T(0)) {
-                        sp += c[q][j];
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j];
+                    if (x > T(0)) {
+                        sp += x;
                         ++np;
                     }
+                    if (x > w) {
+                        sw += x;
+                        ++nw;
+                    }
+                }
             const T s = group_sum<G>(sp);
-            int nA = group_sum<G>(np);
+            const int n0 = group_sum<G>(np);
+            const T S_w = group_sum<G>(sw);
+            const int n_w = group_sum<G>(nw);
             const bool congested = valid && s > ue;  // Case 2 of Alg. 2 (s <= u is Case 1)
             bool done = !congested;
-            if (congested) theta = (s - ue) / T(2 + nA);
+            int nA = n0;
+            if (congested) {
+                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
+                    nA = n_w;
+                    theta = (S_w - ue) / T(2 + n_w);
+                } else {
+                    theta = (s - ue) / T(2 + n0);
+                }
+            }
             for (int it = 0; __any_sync(kFull, !done); ++it) {
                 T sa = T(0);
                 int na = 0;
@@ -379,6 +530,7 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
                 }
                 if (it > a.Kp + 2) break;  // unreachable: nA drops every round
             }
+            if (valid && gl == 0) a.theta[e] = theta;
         }
         // f' = max(0, c - psi'/2); psi of the stored flows
         T rs = T(0);
@@ -392,22 +544,23 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
                 o[j] = x > T(0) ? x : T(0);
                 rs += o[j];
             }
-            if (!psi_only && valid && v < vpr) reinterpret_cast<VT*>(frow)[v] = pack4(o);
+            if (!psi_only && valid && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
         }
         rs = group_sum<G>(rs);
         if (valid && gl == 0) {
             const T over = rs - ue;
             const T psi = over > T(0) ? over : T(0);
-            const double pd = (double)psi;
-            zpsi += pd * pd;
-            capmax = fmax(capmax, pd * a.inv_scale[e]);
+            zpsi = A::add(zpsi, psi * psi);
+            const T c = psi * a.inv_scale_t[e];
+            capmax = c > capmax ? c : capmax;
             if (a.psi_out) a.psi_out[e] = psi;
         }
     }
-    block_sum_max(zpsi, capmax, smem);
-    if (threadIdx.x == 0) {
-        a.part_psi[blockIdx.x] = zpsi;
-        a.part_cap[blockIdx.x] = capmax;
+    // one partial per warp, no block barrier
+    warp_acc_max<T>(zpsi, capmax);
+    if (lane == 0) {
+        reinterpret_cast<typename A::S*>(a.part_psi)[warp] = A::store(zpsi);
+        a.part_cap[warp] = capmax;
     }
 }
 
@@ -419,18 +572,24 @@ __global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
-    __shared__ double smem[64];
+    using A = Acc<T>;
     __shared__ T sa_buf[32];
     __shared__ int sb_buf[32];
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;
+    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (blockIdx.x == gridDim.x - 1) {               // the decision block
+        if (a.mode != MODE_PSI) reduce_and_finalize(a);
+        return;
+    }
     const int vpr = a.Kp / N;
     const bool psi_only = (a.mode == MODE_PSI);
-    double zpsi = 0.0, capmax = 0.0;
-    for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x) {
+    typename A::V zpsi = A::zero();
+    T capmax = T(0);
+    for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x - 1) {
         const T ue = a.u[e];
         T c[V][N];
-        T* frow = a.f + e * a.Kp;
+        const T* frow = a.f + e * a.Kp;
+        T* orow = a.f_out + e * a.Kp;
         const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
         const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
 #pragma unroll
@@ -456,19 +615,34 @@ __global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
         }
         T theta = T(0);
         if (!psi_only) {
-            T s = T(0);
-            int nA = 0;
+            // same warm-started active-set search as the lane-group form
+            const T w = a.theta[e] * T(0.999);
+            T s = T(0), S_w = T(0);
+            int n0 = 0, n_w = 0;
 #pragma unroll
             for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int j = 0; j < N; ++j)
-                    if (c[q][j] > T(0)) {
-                        s += c[q][j];
-                        ++nA;
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j];
+                    if (x > T(0)) {
+                        s += x;
+                        ++n0;
                     }
-            block_sum2(s, nA, sa_buf, sb_buf);
+                    if (x > w) {
+                        S_w += x;
+                        ++n_w;
+                    }
+                }
+            block_sum2(s, n0, sa_buf, sb_buf);
+            block_sum2(S_w, n_w, sa_buf, sb_buf);
             if (s > ue) {  // block-uniform
-                theta = (s - ue) / T(2 + nA);
+                int nA = n0;
+                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
+                    nA = n_w;
+                    theta = (S_w - ue) / T(2 + n_w);
+                } else {
+                    theta = (s - ue) / T(2 + n0);
+                }
                 for (int it = 0; it <= a.Kp + 2; ++it) {
                     T S2 = T(0);
                     int n2 = 0;
@@ -486,6 +660,7 @@ __global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
                     theta = (S2 - ue) / T(2 + n2);
                 }
             }
+            if (threadIdx.x == 0) a.theta[e] = theta;
         }
         T rs = T(0);
 #pragma unroll
@@ -498,22 +673,22 @@ __global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
                 o[j] = x > T(0) ? x : T(0);
                 rs += o[j];
             }
-            if (!psi_only && v < vpr) reinterpret_cast<VT*>(frow)[v] = pack4(o);
+            if (!psi_only && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
         }
         int dummy = 0;
         block_sum2(rs, dummy, sa_buf, sb_buf);
         if (threadIdx.x == 0) {
             const T over = rs - ue;
             const T psi = over > T(0) ? over : T(0);
-            const double pd = (double)psi;
-            zpsi += pd * pd;
-            capmax = fmax(capmax, pd * a.inv_scale[e]);
+            zpsi = A::add(zpsi, psi * psi);
+            const T c = psi * a.inv_scale_t[e];
+            capmax = c > capmax ? c : capmax;
             if (a.psi_out) a.psi_out[e] = psi;
         }
     }
-    block_sum_max(zpsi, capmax, smem);
+    // one partial per block, held by thread 0
     if (threadIdx.x == 0) {
-        a.part_psi[blockIdx.x] = zpsi;
+        reinterpret_cast<typename A::S*>(a.part_psi)[blockIdx.x] = A::store(zpsi);
         a.part_cap[blockIdx.x] = capmax;
     }
 }
@@ -570,14 +745,35 @@ int edge_grid(int cfg, int64_t m, int num_sms)
     return (int)(g < 1 ? 1 : g);
 }
 
-int excess_grid(int32_t n, int Kp, int vec, int num_sms)
+template <typename T>
+int64_t edge_parts(int cfg, int grid)
+{
+    return kCfg[cfg].G ? (int64_t)grid * (kThreads / 32) : (int64_t)grid;
+}
+
+// One wave of resident blocks (or fewer if the rows are fewer): the grid-
+// stride loop then spreads the rows evenly and leaves no partial last wave.
+int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks)
 {
     const int64_t total = (int64_t)n * (Kp / vec);
     int64_t want = (total + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)num_sms * 32;
+    const int64_t cap = (int64_t)num_sms * (resident_blocks > 0 ? resident_blocks : 4);
     int64_t g = want < cap ? want : cap;
     return (int)(g < 1 ? 1 : g);
 }
+
+template <typename T>
+int excess_resident_blocks()
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, excess_kernel<T>, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 4;
+    }
+    return blocks;
+}
+template int excess_resident_blocks<float>();
+template int excess_resident_blocks<double>();
 
 template <typename T>
 cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream)
@@ -587,9 +783,16 @@ cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream)
 }
 
 template <typename T>
+cudaError_t launch_finalize(const SweepArgs<T>& a, cudaStream_t stream)
+{
+    finalize_kernel<T><<<1, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
 {
-    const int g = a.grid_e;
+    const int g = a.grid_e + 1;  // edge blocks plus the decision block
     switch (cfg) {
     case 0: edge_group_kernel<T, 4, 1><<<g, kThreads, 0, stream>>>(a); break;
     case 1: edge_group_kernel<T, 8, 1><<<g, kThreads, 0, stream>>>(a); break;
@@ -620,10 +823,14 @@ cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, 
 template int edge_config<float>(int);
 template int edge_config<double>(int);
 template int edge_grid<float>(int, int64_t, int);
+template int64_t edge_parts<float>(int, int);
+template int64_t edge_parts<double>(int, int);
 template int edge_grid<double>(int, int64_t, int);
 template cudaError_t launch_excess<float>(const SweepArgs<float>&, cudaStream_t);
 template cudaError_t launch_excess<double>(const SweepArgs<double>&, cudaStream_t);
 template cudaError_t launch_edge<float>(const SweepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_finalize<float>(const SweepArgs<float>&, cudaStream_t);
+template cudaError_t launch_finalize<double>(const SweepArgs<double>&, cudaStream_t);
 template cudaError_t launch_edge<double>(const SweepArgs<double>&, int, cudaStream_t);
 
 }  // namespace pdr
