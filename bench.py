@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per step")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="profiler driver: run this many host-launched sweeps from f = 0 on the workload and exit")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the sweep kernels from a host loop instead of the device-side graph loop "
+                         "(same kernels; used for profiler runs)")
     return ap.parse_args()
 
 
@@ -138,13 +143,13 @@ def load_peaks():
 
 
 def source_digest():
+    """Digest of the sweep kernels' sources (the files the ncu counters depend on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_07549_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode())
-                h.update(fh.read())
+    for name in ("sweep.cu", "pdr_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -248,8 +253,15 @@ def main():
         dist.barrier()
     pdr.load()
     stream = torch.cuda.Stream()
+    if args.profile_sweeps > 0:
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
+                sv.sweeps(args.profile_sweeps)
+        torch.cuda.synchronize()
+        return
     S = args.sweeps
-    opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S)
+    opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
+                use_graph=0 if args.host_loop else 1)
     m, K = inst.m, inst.K
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -285,7 +297,11 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     value = world * m * K * S / (ms_step / 1e3)
-    launches_per_step = 2 * (S + 1) + 3 + 1 + 2  # sweeps, residuals, state init, reset
+    # S + 1 objective evaluations (the last one stops); the graph body holds 8
+    # sweeps (two kernels each), the host loop launches chunks of 256 sweeps;
+    # plus residuals (3), solve state init (1), reset (psi refresh + state init)
+    chunk = 256 if args.host_loop else 8
+    launches_per_step = 2 * chunk * (-(-(S + 1) // chunk)) + 3 + 1 + 2
 
     # ---------------------------------------------------------------- end to end through the C ABI
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731

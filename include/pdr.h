@@ -80,7 +80,9 @@ typedef enum {
 
 typedef struct {
     int32_t precision;  /* pdr_precision (default PDR_PREC_FP32) */
-    int32_t reserved0;
+    int32_t use_graph;  /* 1: the sweep loop runs on the device as one CUDA graph with a conditional
+                           while node; 0: the same kernels are launched from a host loop that reads
+                           the stop flag between chunks of sweeps (default 1) */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */

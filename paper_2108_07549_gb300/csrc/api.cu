@@ -34,6 +34,7 @@ void fill_defaults(pdr_options* o)
 {
     std::memset(o, 0, sizeof(*o));
     o->precision = PDR_PREC_FP32;
+    o->use_graph = 1;
     o->eps_obj = 1e-6;
     o->resid_tol = 1e-6;
     o->eps_rel = 0.0;
@@ -376,11 +377,11 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     const int p = Prec<T>::id;
     pdr_status s = flows_to_buffer0<T>(ctx);
     if (s != PDR_OK) return s;
-    if (!ctx->graph_tried[p]) {
+    if (ctx->opt.use_graph && !ctx->graph_tried[p]) {
         s = build_graph<T>(ctx);
         if (s != PDR_OK) return s;
     }
-    if (ctx->graph_ok[p]) {
+    if (ctx->opt.use_graph && ctx->graph_ok[p]) {
         CK(cudaGraphLaunch(ctx->exec[p], ctx->stream));
         s = read_state(ctx);
     } else {

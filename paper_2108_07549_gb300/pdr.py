@@ -44,7 +44,7 @@ class PdrError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [
-        ("precision", C.c_int32), ("reserved0", C.c_int32), ("eps_obj", C.c_double), ("resid_tol", C.c_double),
+        ("precision", C.c_int32), ("use_graph", C.c_int32), ("eps_obj", C.c_double), ("resid_tol", C.c_double),
         ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("reserved1", C.c_int32),
     ]
 

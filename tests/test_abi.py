@@ -39,7 +39,7 @@ def test_default_options(lib):
     from paper_2108_07549_gb300 import pdr
 
     o = pdr.default_options()
-    assert o.precision == pdr.PREC_FP32
+    assert o.precision == pdr.PREC_FP32 and o.use_graph == 1
     assert o.eps_obj == 1e-6 and o.resid_tol == 1e-6 and o.eps_rel == 0.0
     assert o.max_sweeps == 1000000 and o.trace_len == 0
     assert lib.pdr_default_options(None) == 1

@@ -303,3 +303,15 @@ def test_repeat_solves_are_deterministic(pdr, knn2500):
         s.solve()
         b = s.flows()
     np.testing.assert_array_equal(a, b)
+
+
+def test_host_loop_matches_graph_loop(pdr, knn2500):
+    """use_graph = 0 launches the same kernels from a host loop: same sweeps, same flows."""
+    out = []
+    for g in (1, 0):
+        with pdr.Solver.from_instance(knn2500, precision=pdr.PREC_FP32, eps_obj=1e-2, resid_tol=0.0,
+                                      max_sweeps=5000, use_graph=g) as s:
+            r = s.solve()
+            out.append((r["sweeps"], r["stop_name"], s.flows()))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] == "objective"
+    np.testing.assert_array_equal(out[0][2], out[1][2])
