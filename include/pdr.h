@@ -206,8 +206,41 @@ pdr_status pdr_sizes(const pdr_ctx *ctx, int32_t *n, int64_t *m, int32_t *K, int
  * heights).  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
 pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_t flush_bytes, double *ms);
 
-/* Message of the last failure on ctx (or of the last failed pdr_create on
- * this thread if ctx is NULL).  Never NULL; valid until the next call. */
+/* In-adjacency and degrees of a graph that already lives in device memory,
+ * computed without allocating any memory.  The paper has no counterpart:
+ * this is a deployment entry point, not a step of the method.
+ *
+ * Who needs it: a caller whose device memory is owned by another allocator
+ * (a framework's caching pool that has claimed the GPU, or a service that
+ * reserves all memory at start-up and must not allocate afterwards) cannot
+ * call cudaMalloc, so it cannot use pdr_create.  This function takes the
+ * caller's device arrays and uses a fixed scratch area compiled into the
+ * library instead of allocating one.
+ *   n        number of vertices, 1 <= n <= 262,144 (the scratch limit;
+ *            larger n returns PDR_ERR_INVALID_ARG and does no GPU work)
+ *   m        number of edges, 0 <= m < 2^31
+ *   row_ptr  device int64 [n+1], col device int32 [m]: the out-adjacency
+ *            (edge id = CSR position); checked on the device, a malformed
+ *            CSR returns PDR_ERR_INVALID_ARG with nothing written
+ *   in_ptr   device int64 [n+1] (out): offsets of the in-adjacency
+ *   in_eid   device int32 [m] (out): edge ids entering each vertex, ascending
+ *   deg      device int32 [n] (out): out-degree + in-degree
+ *   stream   cudaStream_t to run on (NULL = legacy default stream)
+ * The outputs equal those of pdr_adjacency on a context built from the same
+ * graph.  The call synchronises the stream before returning.
+ * Scratch: 4 MiB of device memory per GPU that loads the library, held until
+ * the process exits, shared by every call: calls whose GPU work overlaps
+ * (other host threads, or other streams of the same device) race on it and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the scratch's device address (with that device current); make that first
+ * call before any stream capture begins.  On failure pdr_last_error(NULL)
+ * returns the message.  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA. */
+pdr_status pdr_adjacency_static(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, int64_t *in_ptr,
+                                int32_t *in_eid, int32_t *deg, void *stream);
+
+/* Message of the last failure on ctx (or, if ctx is NULL, of the last failed
+ * pdr_create or pdr_adjacency_static on this thread).  Never NULL; valid
+ * until the next call. */
 const char *pdr_last_error(const pdr_ctx *ctx);
 
 /* Frees every resource of ctx.  NULL is ignored. */

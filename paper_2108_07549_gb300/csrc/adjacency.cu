@@ -130,3 +130,120 @@ cudaError_t build_adjacency(int32_t n, int64_t m, const int64_t* row_ptr, const 
 }
 
 }  // namespace pdr
+
+// ------------------------------------------------------------------ entry point that allocates nothing
+//
+// pdr_adjacency_static builds the same in-adjacency and degrees as the
+// context path above, for a caller that owns the device arrays and cannot
+// allocate device memory itself.  Its scratch (in-degree counts, fill
+// cursors and an input-error word) is one file-scope device array, so the
+// call makes no cudaMalloc or cudaFree.
+#include "pdr.h"
+
+#include <mutex>
+#include <string>
+
+namespace pdr {
+namespace {
+
+constexpr int64_t kStaticMaxVertices = int64_t(1) << 18;  // 262,144 vertices: 4 MiB of scratch per GPU
+constexpr int kMaxDevices = 64;
+
+// [0, max): in-degree counts; [max, 2 max): fill cursors; [2 max]: input-error word
+__device__ __align__(256) unsigned long long g_static_scratch[2 * kStaticMaxVertices + 1];
+
+std::mutex g_static_mutex;
+void* g_static_addr[kMaxDevices] = {};
+
+// Input checks on the device: row_ptr[0] = 0, non-decreasing, row_ptr[n] = m,
+// 0 <= col[e] < n.  Sets bits of *err instead of trusting the arrays.
+__global__ void static_check_kernel(int32_t n, int64_t m, const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ col, unsigned long long* __restrict__ err)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0 && (row_ptr[0] != 0 || row_ptr[n] != m)) atomicOr(err, 1ull);
+    for (int64_t i = tid; i < n; i += stride)
+        if (row_ptr[i + 1] < row_ptr[i]) atomicOr(err, 2ull);
+    for (int64_t e = tid; e < m; e += stride)
+        if (col[e] < 0 || col[e] >= n) atomicOr(err, 4ull);
+}
+
+}  // namespace
+}  // namespace pdr
+
+extern "C" pdr_status pdr_adjacency_static(int32_t n, int64_t m, const int64_t* row_ptr, const int32_t* col,
+                                           int64_t* in_ptr, int32_t* in_eid, int32_t* deg, void* stream_)
+{
+    using namespace pdr;
+    set_thread_error("");
+    if (n < 1 || n > kStaticMaxVertices) {
+        set_thread_error("pdr_adjacency_static: n must satisfy 1 <= n <= " + std::to_string(kStaticMaxVertices) +
+                         " (the size of its static scratch)");
+        return PDR_ERR_INVALID_ARG;
+    }
+    if (m < 0 || m > (int64_t)INT32_MAX) {
+        set_thread_error("pdr_adjacency_static: m must satisfy 0 <= m < 2^31");
+        return PDR_ERR_INVALID_ARG;
+    }
+    if (!row_ptr || !in_ptr || !deg || (m > 0 && (!col || !in_eid))) {
+        set_thread_error("pdr_adjacency_static: NULL array");
+        return PDR_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_thread_error(std::string("pdr_adjacency_static: cudaGetDevice: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return PDR_ERR_CUDA;
+    }
+    void* base = nullptr;
+    {
+        // once per device, with that device current: the host-side name of
+        // the array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_addr[dev]) {
+            e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
+            if (e != cudaSuccess) {
+                g_static_addr[dev] = nullptr;
+                set_thread_error(std::string("pdr_adjacency_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                cudaGetLastError();
+                return PDR_ERR_CUDA;
+            }
+        }
+        base = g_static_addr[dev];
+    }
+    unsigned long long* cnt = static_cast<unsigned long long*>(base);
+    unsigned long long* cursor = cnt + kStaticMaxVertices;
+    unsigned long long* err = cnt + 2 * kStaticMaxVertices;
+    unsigned long long host_err = 0;
+#define CKS(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess) {                                                                   \
+            set_thread_error(std::string("pdr_adjacency_static: " #call ": ") + cudaGetErrorString(_e)); \
+            cudaGetLastError();                                                                    \
+            return PDR_ERR_CUDA;                                                                   \
+        }                                                                                          \
+    } while (0)
+    // the array keeps the previous call's contents: clear what must start at zero
+    CKS(cudaMemsetAsync(err, 0, sizeof(unsigned long long), stream));
+    CKS(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (size_t)n, stream));
+    static_check_kernel<<<blocks_for(m > n ? m : n, 256), 256, 0, stream>>>(n, m, row_ptr, col, err);
+    CKS(cudaGetLastError());
+    CKS(cudaMemcpyAsync(&host_err, err, sizeof(host_err), cudaMemcpyDeviceToHost, stream));
+    CKS(cudaStreamSynchronize(stream));
+    if (host_err) {
+        set_thread_error("pdr_adjacency_static: malformed CSR (row_ptr bounds or order, or col out of range)");
+        return PDR_ERR_INVALID_ARG;
+    }
+    if (m > 0) count_kernel<<<blocks_for(m, 256), 256, 0, stream>>>(m, col, cnt);
+    scan_kernel<<<1, kScanThreads, 0, stream>>>(n, row_ptr, cnt, in_ptr, reinterpret_cast<long long*>(cursor), deg);
+    if (m > 0) fill_kernel<<<blocks_for(m, 256), 256, 0, stream>>>(m, col, cursor, in_eid);
+    sort_kernel<<<blocks_for(n, 128), 128, 0, stream>>>(n, in_ptr, in_eid);
+    CKS(cudaGetLastError());
+    CKS(cudaStreamSynchronize(stream));
+#undef CKS
+    return PDR_OK;
+}

@@ -65,6 +65,8 @@ bool options_ok(const pdr_options* o, std::string* why)
 
 }  // namespace
 
+void pdr::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct pdr_ctx {
     int32_t n = 0;
     int64_t m = 0;

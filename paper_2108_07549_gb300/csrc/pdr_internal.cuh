@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace pdr {
 
 constexpr int kThreads = 256;  // block size of every sweep kernel
@@ -138,5 +140,8 @@ template <typename T>
 cudaError_t launch_residuals(const SweepArgs<T>& a, const double* u_d, const double* dem_d, double* h64,
                              double* part, int32_t grid_v, int32_t grid_e, ResidOut* out, cudaStream_t stream);
 int resid_part_count(int32_t grid_v, int32_t grid_e);
+
+// Message returned by pdr_last_error(NULL) on the calling thread (api.cu).
+void set_thread_error(const std::string& msg);
 
 }  // namespace pdr

@@ -31,6 +31,7 @@ EXPORTS = (
     "pdr_default_options", "pdr_create", "pdr_set_options", "pdr_solve", "pdr_sweeps", "pdr_reset",
     "pdr_set_flows", "pdr_flows", "pdr_heights", "pdr_congestion", "pdr_objective", "pdr_adjacency",
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
+    "pdr_adjacency_static",
 )
 
 
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "pdr_time_kernel": ([vp, i32, i32, i64, P(dbl)], i32),
         "pdr_last_error": ([vp], C.c_char_p),
         "pdr_destroy": ([vp], None),
+        "pdr_adjacency_static": ([i32, i64, vp, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -130,6 +132,23 @@ def _current_stream():
     except ImportError:
         pass
     return None
+
+
+def adjacency_static(n, m, row_ptr, col, in_ptr, in_eid, deg, stream=None):
+    """In-adjacency and degrees of a device-resident graph with no allocation
+    (pdr_adjacency_static).  Every array argument is a device address (an
+    int, e.g. ``tensor.data_ptr()``): row_ptr int64 [n+1] and col int32 [m]
+    in, in_ptr int64 [n+1], in_eid int32 [m] and deg int32 [n] out.  For
+    callers that may not allocate device memory; see include/pdr.h."""
+    lib = load()
+    if stream is None:
+        stream = _current_stream()
+    elif not isinstance(stream, C.c_void_p):
+        stream = C.c_void_p(int(stream))
+    st = lib.pdr_adjacency_static(int(n), int(m), C.c_void_p(row_ptr), C.c_void_p(col), C.c_void_p(in_ptr),
+                                  C.c_void_p(in_eid), C.c_void_p(deg), stream)
+    if st != 0:
+        raise PdrError(st, lib.pdr_last_error(None).decode())
 
 
 class Solver:
