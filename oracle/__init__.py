@@ -65,6 +65,28 @@ class _Options(C.Structure):
     _fields_ = [("max_sweeps", C.c_int64), ("eps_obj", C.c_double), ("resid_tol", C.c_double)]
 
 
+class _GDParams(C.Structure):
+    _fields_ = [("momentum", C.c_int32), ("pad", C.c_int32), ("beta_init", C.c_double), ("beta_min", C.c_double),
+                ("beta_max", C.c_double), ("alpha_inc", C.c_double), ("alpha_dec", C.c_double),
+                ("gamma", C.c_double)]
+
+
+def gd_params(momentum: bool, K: int, **overrides) -> dict:
+    """Section 7 parameters: AGD (Alg. 3) beta_init .25, beta_max .5; GDM (Alg. 4)
+    beta_init .1, beta_max .2, gamma .9; both beta_min 1/K, alpha_inc 2, alpha_dec .5."""
+    if momentum:
+        p = dict(momentum=1, beta_init=0.1, beta_min=1.0 / K, beta_max=0.2, alpha_inc=2.0, alpha_dec=0.5, gamma=0.9)
+    else:
+        p = dict(momentum=0, beta_init=0.25, beta_min=1.0 / K, beta_max=0.5, alpha_inc=2.0, alpha_dec=0.5, gamma=0.0)
+    p.update(overrides)
+    return p
+
+
+def _gd_struct(p: dict) -> _GDParams:
+    return _GDParams(int(p["momentum"]), 0, p["beta_init"], p["beta_min"], p["beta_max"], p["alpha_inc"],
+                     p["alpha_dec"], p["gamma"])
+
+
 class _Report(C.Structure):
     _fields_ = [("sweeps", C.c_int64), ("z", C.c_double), ("z_prev", C.c_double),
                 ("stop_reason", C.c_int32), ("qp_fallbacks", C.c_int64)]
@@ -96,6 +118,12 @@ def _load():
             lib.orc_residuals_at.restype = None
             lib.orc_solve_eso.argtypes = [P, C.POINTER(_Options), vp, C.POINTER(_Report), vp, C.c_int64]
             lib.orc_solve_eso.restype = C.c_int32
+            G = C.POINTER(_GDParams)
+            lib.orc_gd_edge.argtypes = [G, C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp,
+                                        C.POINTER(C.c_double), C.c_int64, vp, C.POINTER(C.c_double)]
+            lib.orc_gd_edge.restype = C.c_int32
+            lib.orc_solve_gd.argtypes = [P, C.POINTER(_Options), G, vp, vp, vp, C.POINTER(_Report), vp, C.c_int64]
+            lib.orc_solve_gd.restype = C.c_int32
             lib.orc_set_threads.argtypes = [C.c_int32]
             lib.orc_set_threads.restype = None
             lib.orc_max_threads.argtypes = []
@@ -204,6 +232,41 @@ class Problem:
         _load().orc_residuals_at(C.byref(self._c), _ptr(f), float(tol), C.byref(R))
         return {k: getattr(R, k) for k, _ in _Residuals._fields_}
 
+    def solve_gd(self, params: dict, max_sweeps=100000, eps_obj=1e-6, resid_tol=0.0, f0=None, v0=None, beta0=None,
+                 trace=False):
+        """Alg. 3 (params["momentum"] = 0) or Alg. 4 (= 1) from (f0, v0, beta0)
+        (default 0, 0, beta_init).  Returns (f, v, beta, report dict[, ztrace])."""
+        f = np.zeros((self.m, self.K)) if f0 is None else self._f(f0).copy()
+        v = np.zeros((self.m, self.K)) if v0 is None else self._f(v0).copy()
+        beta = (np.full(self.m, float(params["beta_init"])) if beta0 is None
+                else np.ascontiguousarray(beta0, dtype=np.float64).copy())
+        opt = _Options(int(max_sweeps), float(eps_obj), float(resid_tol))
+        rep = _Report()
+        g = _gd_struct(params)
+        zt = np.full(int(max_sweeps) + 1, np.nan) if trace else None
+        rc = _load().orc_solve_gd(C.byref(self._c), C.byref(opt), C.byref(g), _ptr(f), _ptr(v), _ptr(beta),
+                                  C.byref(rep), _ptr(zt) if trace else None, int(max_sweeps) + 1 if trace else 0)
+        if rc != 0:
+            raise MemoryError("oracle solve failed to allocate")
+        out = {k: getattr(rep, k) for k, _ in _Report._fields_}
+        if trace:
+            return f, v, beta, out, zt[: out["sweeps"] + 1]
+        return f, v, beta, out
+
+    def gd_sweep(self, params: dict, f, v, beta, t):
+        """One iteration of Alg. 3 / Alg. 4 without the stop test, at iteration t:
+        returns (f, v, beta) of iteration t + 1."""
+        f = self._f(f).copy()
+        v = self._f(v).copy()
+        beta = np.ascontiguousarray(beta, dtype=np.float64).copy()
+        _, h = self.excess(f)
+        psi = self.congestion(f)
+        for e in range(self.m):
+            fe, ve, be, _, _ = gd_edge(params, h[self.src[e]], h[self.col[e]], psi[e], self.u[e], f[e], v[e],
+                                       beta[e], t)
+            f[e], v[e], beta[e] = fe, ve, be
+        return f, v, beta
+
     def solve_eso(self, max_sweeps=100000, eps_obj=1e-6, resid_tol=0.0, f0=None, trace=False):
         """Alg. 1 with Alg. 2 from f0 (default 0).  Returns (f, report dict[, ztrace])."""
         f = np.zeros((self.m, self.K)) if f0 is None else self._f(f0).copy()
@@ -218,6 +281,23 @@ class Problem:
         if trace:
             return f, out, zt[: out["sweeps"] + 1]
         return f, out
+
+
+def gd_edge(params: dict, hi, hj, psi, u, f, v, beta, t):
+    """One edge step of Alg. 3 / Alg. 4 at iteration t.
+    Returns (f_new, v_new, beta_new, accepted, dz)."""
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    hj = np.ascontiguousarray(hj, dtype=np.float64)
+    f = np.array(f, dtype=np.float64)
+    v = np.array(v if v is not None else np.zeros_like(f), dtype=np.float64)
+    K = int(f.shape[0])
+    b = C.c_double(float(beta))
+    dz = C.c_double()
+    df = np.empty(max(K, 1))
+    g = _gd_struct(params)
+    acc = _load().orc_gd_edge(C.byref(g), K, _ptr(hi), _ptr(hj), float(psi), float(u), _ptr(f), _ptr(v),
+                              C.byref(b), int(t), _ptr(df), C.byref(dz))
+    return f, v, b.value, bool(acc), dz.value
 
 
 def edge_qp(hi, hj, f, u):

@@ -486,3 +486,137 @@ int32_t orc_solve_eso(const orc_problem *P, const orc_options *opt, double *f, o
     free(f_next);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3 (PDR-AGD) and Alg. 4 (PDR-GDM): projected gradient steps          */
+/* ------------------------------------------------------------------------ */
+
+/* Parameters of Section 7: AGD beta_init 0.25, beta_min 1/K, beta_max 0.5,
+ * alpha_inc 2, alpha_dec 0.5; GDM beta_init 0.1, gamma 0.9, beta_min 1/K,
+ * beta_max 0.2, alpha_inc 2, alpha_dec 0.5. */
+typedef struct {
+    int32_t momentum; /* 0: Alg. 3 (AGD), 1: Alg. 4 (GDM) */
+    int32_t pad;
+    double beta_init, beta_min, beta_max, alpha_inc, alpha_dec, gamma;
+} orc_gd_params;
+
+/* One edge of the update loop of Alg. 3 / Alg. 4 at iteration t.
+ *   hi, hj   h_ik, h_jk at iteration t;  psi = psi_ij^(t) (eq. (41))
+ *   f, v     flows (and velocities for Alg. 4) of the edge, updated in place
+ *   beta     the edge's learning rate, updated in place
+ *   df       caller scratch of K doubles
+ * Local objective change of the step (eq. (9) with the optimal slack, minus
+ * its value at Delta f = 0):
+ *   dz = 1/2 (psi'^2 - psi^2) + sum_k (Delta f_k^2 - (h_ik - h_jk) Delta f_k),
+ *   psi' = max(0, sum_k (f_k + Delta f_k) - u).
+ * Returns 1 if the step was accepted. */
+int32_t orc_gd_edge(const orc_gd_params *prm, int32_t K, const double *hi, const double *hj, double psi, double u,
+                    double *f, double *v, double *beta, int64_t t, double *df, double *dz_out)
+{
+    /* potential differences and the projected step */
+    double tot = 0.0;
+    for (int32_t k = 0; k < K; ++k) {
+        double phi = hi[k] - hj[k] - psi;
+        double step = *beta * phi;
+        df[k] = step > -f[k] ? step : -f[k];
+        tot += f[k] + df[k];
+    }
+    double over = tot - u;
+    double psi_new = over > 0.0 ? over : 0.0;
+    double dz = 0.5 * (psi_new * psi_new - psi * psi);
+    for (int32_t k = 0; k < K; ++k) dz += df[k] * df[k] - (hi[k] - hj[k]) * df[k];
+    int32_t accept = dz <= 0.0;
+    if (accept) {
+        if (prm->momentum) {
+            for (int32_t k = 0; k < K; ++k) {
+                v[k] = prm->gamma * v[k] + df[k];
+                double x = f[k] + v[k];
+                f[k] = x > 0.0 ? x : 0.0;
+            }
+        } else {
+            for (int32_t k = 0; k < K; ++k) f[k] = f[k] + df[k];
+        }
+    } else {
+        double b = *beta * prm->alpha_dec;
+        *beta = b > prm->beta_min ? b : prm->beta_min;
+    }
+    if (t % 10 == 0) {
+        double b = *beta * prm->alpha_inc;
+        *beta = b < prm->beta_max ? b : prm->beta_max;
+    }
+    if (dz_out) *dz_out = dz;
+    return accept;
+}
+
+/* Runs Alg. 3 (momentum = 0) or Alg. 4 (momentum = 1) from the flows in f,
+ * velocities v and learning rates beta (the paper starts at f = 0, v = 0,
+ * beta = beta_init); all three are updated in place and hold the state of
+ * iteration t at exit.  Same stop rules and report as orc_solve_eso.
+ * Returns 0, or -1 on allocation failure. */
+int32_t orc_solve_gd(const orc_problem *P, const orc_options *opt, const orc_gd_params *prm, double *f, double *v,
+                     double *beta, orc_report *rep, double *ztrace, int64_t ztrace_len)
+{
+    const int32_t n = P->n, K = P->K;
+    const int64_t m = P->m;
+    double *Delta = (double *)malloc(sizeof(double) * (size_t)n * (size_t)K);
+    double *h = (double *)malloc(sizeof(double) * (size_t)n * (size_t)K);
+    double *psi = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!Delta || !h || !psi) {
+        free(Delta);
+        free(h);
+        free(psi);
+        return -1;
+    }
+    double ubar = capacity_scale(P);
+    double z_prev = INFINITY, z = 0.0;
+    int64_t t = 0;
+    rep->stop_reason = 0;
+    rep->qp_fallbacks = 0;
+    for (;;) {
+        orc_excess(P, f, Delta, h);
+        orc_congestion(P, f, psi);
+        z = orc_objective(P, h, psi);
+        if (ztrace && t < ztrace_len) ztrace[t] = z;
+        if (t >= opt->max_sweeps) break;
+        if (opt->eps_obj > 0.0 && fabs(z - z_prev) < opt->eps_obj) {
+            rep->stop_reason = 1;
+            break;
+        }
+        if (opt->resid_tol > 0.0) {
+            double cap = 0.0, cons = 0.0;
+            for (int64_t e = 0; e < m; ++e) {
+                double scale = P->u[e] > ubar ? P->u[e] : ubar;
+                if (psi[e] / scale > cap) cap = psi[e] / scale;
+            }
+            for (int32_t i = 0; i < n; ++i)
+                for (int32_t k = 0; k < K; ++k) {
+                    double a = fabs(Delta[(int64_t)i * K + k]) / P->d[k];
+                    if (a > cons) cons = a;
+                }
+            if (cap <= opt->resid_tol && cons <= opt->resid_tol) {
+                rep->stop_reason = 2;
+                break;
+            }
+        }
+        z_prev = z;
+        /* every edge steps from the same h^(t), psi^(t) (the edges' rows are
+         * disjoint, so updating them in place is the parallel update) */
+#pragma omp parallel
+        {
+            double *df = (double *)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+#pragma omp for schedule(static)
+            for (int64_t e = 0; e < m; ++e)
+                orc_gd_edge(prm, K, h + (int64_t)P->src[e] * K, h + (int64_t)P->col[e] * K, psi[e], P->u[e],
+                            f + e * K, v ? v + e * K : NULL, beta + e, t, df, NULL);
+            free(df);
+        }
+        ++t;
+    }
+    rep->sweeps = t;
+    rep->z = z;
+    rep->z_prev = z_prev;
+    free(Delta);
+    free(h);
+    free(psi);
+    return 0;
+}
