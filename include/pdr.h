@@ -70,6 +70,12 @@ typedef enum {
 } pdr_precision;
 
 typedef enum {
+    PDR_ALGO_ESO = 0, /* Alg. 1 with the exact edge solver of Alg. 2 (PDR-ESO) */
+    PDR_ALGO_AGD = 1, /* Alg. 3: projected gradient step with adaptive learning rate (PDR-AGD) */
+    PDR_ALGO_GDM = 2  /* Alg. 4: Alg. 3 with momentum (PDR-GDM) */
+} pdr_algo;
+
+typedef enum {
     PDR_STOP_MAX_SWEEPS = 0, /* t reached max_sweeps */
     PDR_STOP_OBJECTIVE = 1,  /* |z^(t) - z^(t-1)| < eps_obj (Alg. 1) */
     PDR_STOP_RESIDUAL = 2,   /* cap_rel <= resid_tol and cons_rel <= resid_tol */
@@ -88,7 +94,12 @@ typedef struct {
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */
     int64_t max_sweeps; /* upper bound on QP updates per solve (default 1,000,000) */
     int32_t trace_len;  /* number of z^(t) values kept for pdr_trace (default 0) */
-    int32_t reserved1;
+    int32_t algo;       /* pdr_algo (default PDR_ALGO_ESO) */
+    /* Alg. 3 / Alg. 4 parameters (Section 7).  A value <= 0 (gamma < 0)
+     * selects the paper's default for the chosen algorithm: AGD beta_init
+     * 0.25, beta_max 0.5; GDM beta_init 0.1, beta_max 0.2, gamma 0.9; both
+     * beta_min 1/K, alpha_inc 2, alpha_dec 0.5.  Ignored by PDR_ALGO_ESO. */
+    double beta_init, beta_min, beta_max, alpha_inc, alpha_dec, gamma;
 } pdr_options;
 
 typedef struct {
@@ -137,29 +148,45 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_
  * defaults.  Errors: PDR_ERR_INVALID_ARG. */
 pdr_status pdr_set_options(pdr_ctx *ctx, const pdr_options *opt);
 
-/* Runs Alg. 1 from the current flows until a stop rule fires (the sweep
- * loop runs on the device as one CUDA graph), then evaluates the eq. (1)
- * residuals and the certificate in FP64 (as pdr_residuals).  Leaves f^(t),
- * the flows whose objective triggered the stop, as the current flows.
- * out may be NULL.  Errors: PDR_ERR_CUDA, PDR_ERR_NUMERIC. */
+/* Runs Alg. 1 (or Alg. 3 / Alg. 4, by opt.algo) from the current state until
+ * a stop rule fires (the sweep loop runs on the device as one CUDA graph),
+ * then evaluates the eq. (1) residuals and the certificate in FP64 (as
+ * pdr_residuals).  Leaves f^(t), the flows whose objective triggered the
+ * stop, as the current flows (with the learning rates and velocities of the
+ * same iteration for Alg. 3 / Alg. 4).  out may be NULL.
+ * Errors: PDR_ERR_CUDA, PDR_ERR_NUMERIC. */
 pdr_status pdr_solve(pdr_ctx *ctx, pdr_result *out);
 
-/* Runs exactly `count` sweeps of Alg. 1 (excess/heights, congestion,
- * objective, edge QP) with every stop rule disabled.  Used to compare single
- * sweeps with a reference.  Errors: PDR_ERR_INVALID_ARG (count < 0),
- * PDR_ERR_CUDA. */
+/* Runs exactly `count` sweeps of the chosen algorithm (excess/heights,
+ * congestion, objective, flow update) with every stop rule disabled; the
+ * iteration counter t continues from the last solve or sweep (it drives the
+ * learning-rate schedule of Alg. 3 / Alg. 4).  Used to compare single sweeps
+ * with a reference.  Errors: PDR_ERR_INVALID_ARG (count < 0), PDR_ERR_CUDA. */
 pdr_status pdr_sweeps(pdr_ctx *ctx, int64_t count);
 
-/* Sets every flow to 0 (the start of Alg. 1). */
+/* Sets every flow to 0, every velocity to 0 and every learning rate to
+ * beta_init, and the iteration counter to 0 (the start of Alg. 1, 3 and 4). */
 pdr_status pdr_reset(pdr_ctx *ctx);
 
 /* Copies host flows f[m*K] (double, edge-major) into the context, rounding
- * to the working precision.  Errors: PDR_ERR_INVALID_ARG (NULL, negative or
- * non-finite entries are not checked; the caller supplies f >= 0). */
+ * to the working precision; velocities restart at 0, learning rates at
+ * beta_init and the iteration counter at 0.  Errors: PDR_ERR_INVALID_ARG
+ * (NULL; negative or non-finite entries are not checked, the caller
+ * supplies f >= 0). */
 pdr_status pdr_set_flows(pdr_ctx *ctx, const double *f);
 
 /* Copies the current flows to host f[m*K] (double, edge-major). */
 pdr_status pdr_flows(pdr_ctx *ctx, double *f);
+
+/* State of Alg. 3 / Alg. 4 of the current iteration: learning rates beta[m]
+ * and (Alg. 4) velocities v[m*K] (edge-major) into host arrays; either may
+ * be NULL.  Errors: PDR_ERR_INVALID_ARG if the context runs Alg. 1. */
+pdr_status pdr_gd_state(pdr_ctx *ctx, double *beta, double *v);
+
+/* Replaces the Alg. 3 / Alg. 4 state: beta[m] (> 0) and, for Alg. 4, v[m*K]
+ * (NULL = zeros).  The flows are kept.  Errors: PDR_ERR_INVALID_ARG. */
+pdr_status pdr_set_gd_state(pdr_ctx *ctx, const double *beta, const double *v);
+
 
 /* Heights h_ik (eq. (2)) of the current flows, computed in the working
  * precision by the sweep's excess kernel, into host h[n*K] (double). */

@@ -40,6 +40,9 @@ void fill_defaults(pdr_options* o)
     o->eps_rel = 0.0;
     o->max_sweeps = 1000000;
     o->trace_len = 0;
+    o->algo = PDR_ALGO_ESO;
+    o->beta_init = o->beta_min = o->beta_max = o->alpha_inc = o->alpha_dec = 0.0;
+    o->gamma = -1.0;
 }
 
 bool options_ok(const pdr_options* o, std::string* why)
@@ -58,6 +61,20 @@ bool options_ok(const pdr_options* o, std::string* why)
     }
     if (o->trace_len < 0) {
         *why = "trace_len must be >= 0";
+        return false;
+    }
+    if (o->algo < PDR_ALGO_ESO || o->algo > PDR_ALGO_GDM) {
+        *why = "algo must be 0 (ESO), 1 (AGD) or 2 (GDM)";
+        return false;
+    }
+    const double g[] = {o->beta_init, o->beta_min, o->beta_max, o->alpha_inc, o->alpha_dec, o->gamma};
+    for (double x : g)
+        if (!std::isfinite(x)) {
+            *why = "learning-rate parameters must be finite";
+            return false;
+        }
+    if (o->gamma >= 1.0) {
+        *why = "gamma must be < 1";
         return false;
     }
     return true;
@@ -89,6 +106,12 @@ struct pdr_ctx {
     double *f64[2] = {nullptr, nullptr}, *h64 = nullptr, *inv_deg_d = nullptr;
     int cur = 0;  // buffer holding the current flows
     double* theta = nullptr;  // [m] warm starts, 8 bytes per edge covers both precisions
+    // Alg. 3 / Alg. 4 state, double-buffered like the flows
+    double* beta_buf[2] = {nullptr, nullptr};  // [m], 8 bytes per edge covers both precisions
+    float* v32[2] = {nullptr, nullptr};
+    double* v64[2] = {nullptr, nullptr};
+    // effective Alg. 3 / Alg. 4 parameters
+    double g_beta_init = 0, g_beta_min = 0, g_beta_max = 0, g_alpha_inc = 0, g_alpha_dec = 0, g_gamma = 0;
     int cur_prec = 0;  // precision of the current flows: 0 FP32, 1 FP64
     double* part_h = nullptr;
     // partials typed by the working precision: 8 bytes per entry covers both
@@ -162,6 +185,7 @@ struct Prec<float> {
     static const float* inv_dem(pdr_ctx* c) { return c->inv_dem_f; }
     static const float* inv_scale(pdr_ctx* c) { return c->inv_scale_f; }
     static const float* inv_deg(pdr_ctx* c) { return c->inv_deg_f; }
+    static float* v(pdr_ctx* c, int b) { return c->v32[b]; }
 };
 template <>
 struct Prec<double> {
@@ -173,6 +197,7 @@ struct Prec<double> {
     static const double* inv_dem(pdr_ctx* c) { return c->inv_dem_d; }
     static const double* inv_scale(pdr_ctx* c) { return c->inv_scale; }
     static const double* inv_deg(pdr_ctx* c) { return c->inv_deg_d; }
+    static double* v(pdr_ctx* c, int b) { return c->v64[b]; }
 };
 
 // Kernel arguments for a sweep that reads buffer (base ^ par) and writes the
@@ -207,6 +232,16 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     const int b = ((base < 0 ? ctx->cur : base) ^ par) & 1;
     a.f = Prec<T>::f(ctx, b);
     a.f_out = Prec<T>::f(ctx, b ^ 1);
+    a.beta_in = reinterpret_cast<const T*>(ctx->beta_buf[b]);
+    a.beta_out = reinterpret_cast<T*>(ctx->beta_buf[b ^ 1]);
+    a.v_in = Prec<T>::v(ctx, b);
+    a.v_out = Prec<T>::v(ctx, b ^ 1);
+    a.momentum = ctx->opt.algo == PDR_ALGO_GDM ? 1 : 0;
+    a.beta_min = (T)ctx->g_beta_min;
+    a.beta_max = (T)ctx->g_beta_max;
+    a.alpha_inc = (T)ctx->g_alpha_inc;
+    a.alpha_dec = (T)ctx->g_alpha_dec;
+    a.gamma = (T)ctx->g_gamma;
     a.h = Prec<T>::h(ctx);
     a.part_h = ctx->part_h;
     a.part_cons = reinterpret_cast<T*>(ctx->part_cons);
@@ -258,6 +293,65 @@ pdr_status ensure_fp32(pdr_ctx* ctx)
     return PDR_OK;
 }
 
+// Effective Alg. 3 / Alg. 4 parameters: the caller's, or Section 7's.
+void resolve_gd_params(pdr_ctx* ctx)
+{
+    const pdr_options& o = ctx->opt;
+    const bool gdm = o.algo == PDR_ALGO_GDM;
+    ctx->g_beta_init = o.beta_init > 0 ? o.beta_init : (gdm ? 0.1 : 0.25);
+    ctx->g_beta_min = o.beta_min > 0 ? o.beta_min : 1.0 / ctx->K;
+    ctx->g_beta_max = o.beta_max > 0 ? o.beta_max : (gdm ? 0.2 : 0.5);
+    ctx->g_alpha_inc = o.alpha_inc > 0 ? o.alpha_inc : 2.0;
+    ctx->g_alpha_dec = o.alpha_dec > 0 ? o.alpha_dec : 0.5;
+    ctx->g_gamma = o.gamma >= 0 ? o.gamma : (gdm ? 0.9 : 0.0);
+}
+
+// The flow update of one sweep: the edge QP (Alg. 2) or the gradient step.
+template <typename T>
+cudaError_t launch_update(pdr_ctx* ctx, const SweepArgs<T>& a, cudaStream_t stream)
+{
+    const int cfg = ctx->cfg[Prec<T>::id];
+    return ctx->opt.algo == PDR_ALGO_ESO ? launch_edge<T>(a, cfg, stream) : launch_gd<T>(a, cfg, stream);
+}
+
+// Velocity buffers of the working precision (Alg. 4 only).
+template <typename T>
+pdr_status ensure_velocity(pdr_ctx* ctx)
+{
+    if (ctx->opt.algo != PDR_ALGO_GDM) return PDR_OK;
+    const size_t fm = (size_t)ctx->m * ctx->Kp;
+    for (int b = 0; b < 2; ++b) {
+        T*& buf = Prec<T>::id ? reinterpret_cast<T*&>(ctx->v64[b]) : reinterpret_cast<T*&>(ctx->v32[b]);
+        if (buf) continue;
+        pdr_status st = PDR_OK;
+        buf = dalloc<T>(ctx, fm, &st);
+        if (!buf) return st;
+        CK(cudaMemsetAsync(buf, 0, sizeof(T) * (fm ? fm : 1), ctx->stream));
+    }
+    return PDR_OK;
+}
+
+// Learning rates = beta_init and velocities = 0 in buffer 0 (precision T).
+template <typename T>
+pdr_status init_gd_state(pdr_ctx* ctx)
+{
+    if (ctx->m == 0) return PDR_OK;
+    std::vector<T> b(ctx->m, (T)ctx->g_beta_init);
+    CK(cudaMemcpyAsync(ctx->beta_buf[0], b.data(), sizeof(T) * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->opt.algo == PDR_ALGO_GDM) {
+        pdr_status s = ensure_velocity<T>(ctx);
+        if (s != PDR_OK) return s;
+        CK(cudaMemsetAsync(Prec<T>::v(ctx, 0), 0, sizeof(T) * (size_t)ctx->m * ctx->Kp, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status init_gd_state_current(pdr_ctx* ctx)
+{
+    return ctx->cur_prec ? init_gd_state<double>(ctx) : init_gd_state<float>(ctx);
+}
+
 // Moves the current flows into buffer 0 (the graphs are captured for it).
 template <typename T>
 pdr_status flows_to_buffer0(pdr_ctx* ctx)
@@ -265,8 +359,18 @@ pdr_status flows_to_buffer0(pdr_ctx* ctx)
     if (ctx->cur == 0) return PDR_OK;
     const size_t bytes = sizeof(T) * (size_t)ctx->m * ctx->Kp;
     if (bytes) CK(cudaMemcpyAsync(Prec<T>::f(ctx, 0), Prec<T>::f(ctx, 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->m > 0)
+        CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->beta_buf[1], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    if (ctx->opt.algo == PDR_ALGO_GDM && bytes && Prec<T>::v(ctx, 1))
+        CK(cudaMemcpyAsync(Prec<T>::v(ctx, 0), Prec<T>::v(ctx, 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->cur = 0;
     return PDR_OK;
+}
+
+pdr_status flows_to_buffer0_current(pdr_ctx* ctx)
+{
+    return ctx->cur_prec ? flows_to_buffer0<double>(ctx) : flows_to_buffer0<float>(ctx);
 }
 
 int start_prec(const pdr_options& o) { return o.precision == PDR_PREC_FP64 ? 1 : 0; }
@@ -352,7 +456,7 @@ pdr_status build_graph(pdr_ctx* ctx)
         for (int q = 0; q < kUnroll && e1 == cudaSuccess; ++q) {
             SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 1, h, q & 1, 0);
             e1 = launch_excess<T>(a, ctx->cap_stream);
-            if (e1 == cudaSuccess) e1 = launch_edge<T>(a, ctx->cfg[p], ctx->cap_stream);
+            if (e1 == cudaSuccess) e1 = launch_update<T>(ctx, a, ctx->cap_stream);
         }
         cudaError_t e3 = cudaStreamEndCapture(ctx->cap_stream, &captured);
         if (e1 != cudaSuccess || e3 != cudaSuccess) goto fail;
@@ -377,7 +481,9 @@ template <typename T>
 pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
 {
     const int p = Prec<T>::id;
-    pdr_status s = flows_to_buffer0<T>(ctx);
+    pdr_status s = ensure_velocity<T>(ctx);
+    if (s != PDR_OK) return s;
+    s = flows_to_buffer0<T>(ctx);
     if (s != PDR_OK) return s;
     if (ctx->opt.use_graph && !ctx->graph_tried[p]) {
         s = build_graph<T>(ctx);
@@ -393,7 +499,7 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
             for (int q = 0; q < 32 * kUnroll; ++q) {
                 SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, q & 1, 0);
                 CK(launch_excess<T>(a, ctx->stream));
-                CK(launch_edge<T>(a, ctx->cfg[p], ctx->stream));
+                CK(launch_update<T>(ctx, a, ctx->stream));
             }
             s = read_state(ctx);
             if (s != PDR_OK || ctx->hst->stop) break;
@@ -496,6 +602,7 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->u_d, ctx->dem_d, ctx->inv_scale, ctx->u_f, ctx->dem_f, ctx->inv_dem_f, ctx->inv_dem_d,
                    ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
                    ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta,
+                   ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
                    ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -611,6 +718,8 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_deg_f, float, n);
     ALLOC(ctx->inv_deg_d, double, n);
     ALLOC(ctx->theta, double, m);
+    ALLOC(ctx->beta_buf[0], double, m);
+    ALLOC(ctx->beta_buf[1], double, m);
     ALLOC(ctx->dem_d, double, Kp);
     ALLOC(ctx->dem_f, float, Kp);
     ALLOC(ctx->inv_dem_d, double, Kp);
@@ -695,7 +804,10 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
         CKC(cudaStreamSynchronize(ctx->stream));
     }
     ctx->cur_prec = start_prec(o);
+    resolve_gd_params(ctx);
     st = ctx->cur_prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
+    if (st != PDR_OK) return give_up(st);
+    st = init_gd_state_current(ctx);
     if (st != PDR_OK) return give_up(st);
     st = refresh_psi_current(ctx);
     if (st != PDR_OK) return give_up(st);
@@ -726,6 +838,11 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
         ctx->trace_cap = o.trace_len;
         destroy_graphs(ctx);  // the graphs captured the old trace pointer
     }
+    const bool gd_changed = o.algo != ctx->opt.algo || o.beta_init != ctx->opt.beta_init ||
+                            o.beta_min != ctx->opt.beta_min || o.beta_max != ctx->opt.beta_max ||
+                            o.alpha_inc != ctx->opt.alpha_inc || o.alpha_dec != ctx->opt.alpha_dec ||
+                            o.gamma != ctx->opt.gamma;
+    if (gd_changed || o.use_graph != ctx->opt.use_graph) destroy_graphs(ctx);  // captured arguments change
     const int want = start_prec(o);
     if (want != ctx->cur_prec && o.precision != PDR_PREC_FP32_FP64TAIL) {
         // move the current flows into the new working precision
@@ -733,12 +850,20 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
         pdr_status s = pdr_flows(ctx, f.data());
         if (s != PDR_OK) return s;
         ctx->opt = o;
+        resolve_gd_params(ctx);
         s = want ? ensure_fp64(ctx) : ensure_fp32(ctx);
         if (s != PDR_OK) return s;
         ctx->cur_prec = want;
         return pdr_set_flows(ctx, f.data());
     }
     ctx->opt = o;
+    resolve_gd_params(ctx);
+    if (gd_changed) {
+        // a new algorithm or new rates: learning rates and velocities restart, the flows stay
+        pdr_status s = flows_to_buffer0_current(ctx);
+        if (s != PDR_OK) return s;
+        return init_gd_state_current(ctx);
+    }
     return PDR_OK;
 }
 
@@ -752,6 +877,8 @@ pdr_status pdr_reset(pdr_ctx* ctx)
     ctx->cur = 0;
     if (ctx->cur_prec) CK(cudaMemsetAsync(ctx->f64[0], 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
     else CK(cudaMemsetAsync(ctx->f32[0], 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+    s = init_gd_state_current(ctx);
+    if (s != PDR_OK) return s;
     s = refresh_psi_current(ctx);
     if (s != PDR_OK) return s;
     s = init_state(ctx, true, 0);
@@ -769,6 +896,8 @@ pdr_status pdr_set_flows(pdr_ctx* ctx, const double* f)
     s = ctx->cur_prec ? copy_rows_in<double>(ctx, f, ctx->m, ctx->f64[0])
                       : copy_rows_in<float>(ctx, f, ctx->m, ctx->f32[0]);
     if (s != PDR_OK) return s;
+    s = init_gd_state_current(ctx);
+    if (s != PDR_OK) return s;
     s = refresh_psi_current(ctx);
     if (s != PDR_OK) return s;
     s = init_state(ctx, true, 0);
@@ -781,6 +910,73 @@ pdr_status pdr_flows(pdr_ctx* ctx, double* f)
     if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
     return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64[ctx->cur], ctx->m, f)
                          : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
+}
+
+pdr_status pdr_gd_state(pdr_ctx* ctx, double* beta, double* v)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (ctx->opt.algo == PDR_ALGO_ESO) return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 (no learning rates)");
+    const int b = ctx->cur;
+    if (beta && ctx->m > 0) {
+        if (ctx->cur_prec) {
+            CK(cudaMemcpyAsync(beta, ctx->beta_buf[b], sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            std::vector<float> tmp(ctx->m);
+            CK(cudaMemcpyAsync(tmp.data(), ctx->beta_buf[b], sizeof(float) * ctx->m, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int64_t e = 0; e < ctx->m; ++e) beta[e] = tmp[e];
+        }
+    }
+    if (v) {
+        if (ctx->opt.algo != PDR_ALGO_GDM) {
+            std::memset(v, 0, sizeof(double) * (size_t)ctx->m * ctx->K);
+        } else {
+            pdr_status s = ctx->cur_prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
+            if (s != PDR_OK) return s;
+            s = ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->v64[b], ctx->m, v)
+                              : copy_rows_out<float>(ctx, ctx->v32[b], ctx->m, v);
+            if (s != PDR_OK) return s;
+        }
+    }
+    return PDR_OK;
+}
+
+pdr_status pdr_set_gd_state(pdr_ctx* ctx, const double* beta, const double* v)
+{
+    if (!ctx || (!beta && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "beta is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->opt.algo == PDR_ALGO_ESO) return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 (no learning rates)");
+    for (int64_t e = 0; e < ctx->m; ++e)
+        if (!(beta[e] > 0.0) || !std::isfinite(beta[e]))
+            return ctx->fail(PDR_ERR_INVALID_ARG, "beta must be finite and > 0 at edge " + std::to_string(e));
+    pdr_status s = flows_to_buffer0_current(ctx);
+    if (s != PDR_OK) return s;
+    if (ctx->m > 0) {
+        if (ctx->cur_prec) {
+            CK(cudaMemcpyAsync(ctx->beta_buf[0], beta, sizeof(double) * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            std::vector<float> tmp(beta, beta + ctx->m);
+            CK(cudaMemcpyAsync(ctx->beta_buf[0], tmp.data(), sizeof(float) * ctx->m, cudaMemcpyHostToDevice,
+                               ctx->stream));
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (ctx->opt.algo == PDR_ALGO_GDM) {
+        s = ctx->cur_prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
+        if (s != PDR_OK) return s;
+        const size_t fm = (size_t)ctx->m * ctx->Kp;
+        if (!v) {
+            if (ctx->cur_prec) CK(cudaMemsetAsync(ctx->v64[0], 0, sizeof(double) * (fm ? fm : 1), ctx->stream));
+            else CK(cudaMemsetAsync(ctx->v32[0], 0, sizeof(float) * (fm ? fm : 1), ctx->stream));
+        } else {
+            s = ctx->cur_prec ? copy_rows_in<double>(ctx, v, ctx->m, ctx->v64[0])
+                              : copy_rows_in<float>(ctx, v, ctx->m, ctx->v32[0]);
+            if (s != PDR_OK) return s;
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
 }
 
 pdr_status pdr_heights(pdr_ctx* ctx, double* h)
@@ -848,18 +1044,22 @@ pdr_status pdr_sweeps(pdr_ctx* ctx, int64_t count)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
     if (count < 0) return ctx->fail(PDR_ERR_INVALID_ARG, "count must be >= 0");
-    pdr_status s = init_state(ctx, true, 0);
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    s = init_state(ctx, false, 0);  // t continues (it drives the Alg. 3 / Alg. 4 schedule)
+    if (s != PDR_OK) return s;
+    s = ctx->cur_prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
     if (s != PDR_OK) return s;
     for (int64_t q = 0; q < count; ++q) {
         const int par = (int)(q & 1);
         if (ctx->cur_prec) {
             SweepArgs<double> a = make_args<double>(ctx, MODE_FORCED, 0, 0, par);
             CK(launch_excess<double>(a, ctx->stream));
-            CK(launch_edge<double>(a, ctx->cfg[1], ctx->stream));
+            CK(launch_update<double>(ctx, a, ctx->stream));
         } else {
             SweepArgs<float> a = make_args<float>(ctx, MODE_FORCED, 0, 0, par);
             CK(launch_excess<float>(a, ctx->stream));
-            CK(launch_edge<float>(a, ctx->cfg[0], ctx->stream));
+            CK(launch_update<float>(ctx, a, ctx->stream));
         }
     }
     ctx->cur ^= (int)(count & 1);
@@ -883,6 +1083,19 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
         s = ensure_fp64(ctx);
         if (s != PDR_OK) return s;
         CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
+        if (ctx->opt.algo != PDR_ALGO_ESO && ctx->m > 0) {
+            // learning rates (and velocities) follow the flows into FP64
+            CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta,
+                                         ctx->m, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->theta, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+            if (ctx->opt.algo == PDR_ALGO_GDM) {
+                s = ensure_velocity<double>(ctx);
+                if (s != PDR_OK) return s;
+                CK(launch_convert_f32_to_f64(ctx->v32[ctx->cur], ctx->v64[0], (int64_t)ctx->m * ctx->Kp,
+                                             ctx->stream));
+            }
+        }
         ctx->cur = 0;
         ctx->cur_prec = 1;
         s = refresh_psi<double>(ctx);
@@ -979,8 +1192,8 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         if (which == 0) {
             // reads the current flows, writes the other buffer: every launch
             // repeats the same sweep
-            if (f64) CKT(launch_edge<double>(make_args<double>(ctx, MODE_FORCED), ctx->cfg[1], ctx->stream));
-            else CKT(launch_edge<float>(make_args<float>(ctx, MODE_FORCED), ctx->cfg[0], ctx->stream));
+            if (f64) CKT(launch_update<double>(ctx, make_args<double>(ctx, MODE_FORCED), ctx->stream));
+            else CKT(launch_update<float>(ctx, make_args<float>(ctx, MODE_FORCED), ctx->stream));
         } else {
             if (f64) CKT(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
             else CKT(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));

@@ -59,6 +59,8 @@ struct DevState {
     int reason;           // STOP_* code
     int stop_on_rise;     // 1: z^(t) >= z^(t-1) stops (the FP32 rounding floor)
     int pad;
+    long long t_sweep;    // t of the sweep in flight (written by the excess kernel, read by
+                          // the gradient-step kernels while the decision block advances t)
 };
 
 template <typename T>
@@ -98,6 +100,13 @@ struct SweepArgs {
     T* part_cap;        // [n_psi] per edge warp/block: max psi/scale
     int32_t grid_v, grid_e;
     int64_t n_psi;      // number of edge partials
+    // Alg. 3 / Alg. 4 state (double-buffered like the flows) and parameters
+    const T* beta_in;   // [m] learning rates beta_ij of iteration t
+    T* beta_out;        // [m] learning rates of iteration t+1
+    const T* v_in;      // [m][Kp] velocities of iteration t (Alg. 4)
+    T* v_out;           // [m][Kp] velocities of iteration t+1 (Alg. 4)
+    int momentum;       // 0: Alg. 3, 1: Alg. 4
+    T beta_min, beta_max, alpha_inc, alpha_dec, gamma;
     T* psi_out;         // optional [m] congestion output of the edge kernel
     DevState* st;
     double* trace;
@@ -125,6 +134,11 @@ int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
 template <typename T>
 int excess_resident_blocks();  // excess blocks resident per SM (occupancy)
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream);
+
+// Gradient-step kernels of Alg. 3 / Alg. 4 (gd.cu); same grid, partials and
+// decision block as launch_edge.
+template <typename T>
+cudaError_t launch_gd(const SweepArgs<T>& a, int cfg, cudaStream_t stream);
 
 // Adjacency builder (adjacency.cu): in-adjacency, incidence lists, edge
 // tails and degrees.  work must hold 2*n + 1 int64 entries.

@@ -24,266 +24,10 @@
 // active-set iteration of Michelot 1986 for projections onto a simplex,
 // applied to this problem).  Each round is one group-wide sum and count held
 // in registers, so no row is sorted or re-read.
-#include "pdr_internal.cuh"
-
-#include <math.h>
+#include "sweep_common.cuh"
 
 namespace pdr {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T>
-struct VecOf;
-template <>
-struct VecOf<float> {
-    using type = float4;
-    static constexpr int N = 4;
-};
-template <>
-struct VecOf<double> {
-    using type = double2;
-    static constexpr int N = 2;
-};
-
-__device__ __forceinline__ void unpack(const float4& v, float* x)
-{
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
-    x[3] = v.w;
-}
-__device__ __forceinline__ void unpack(const double2& v, double* x)
-{
-    x[0] = v.x;
-    x[1] = v.y;
-}
-__device__ __forceinline__ float4 pack4(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
-__device__ __forceinline__ double2 pack4(const double* x) { return make_double2(x[0], x[1]); }
-
-// Sum over the G lanes of an aligned lane group (xor offsets below G stay
-// inside the group).  Every lane of the warp must call it.  IEEE addition is
-// commutative, so every lane of the group ends with the same value.
-template <int G, typename X>
-__device__ __forceinline__ X group_sum(X x)
-{
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
-
-template <typename X>
-__device__ __forceinline__ X warp_max(X x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const X y = __shfl_xor_sync(kFull, x, o);
-        x = y > x ? y : x;
-    }
-    return x;
-}
-
-// Block-wide sum of a value and a count, broadcast to every thread.
-template <typename T>
-__device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sa[w] = a;
-        sb[w] = b;
-    }
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    T ta = 0;
-    int tb = 0;
-    for (int q = 0; q < nw; ++q) {  // same order in every thread
-        ta += sa[q];
-        tb += sb[q];
-    }
-    a = ta;
-    b = tb;
-    __syncthreads();
-}
-
-// ------------------------------------------------------------------ objective accumulators
-//
-// GB300 issues FP64 at a small fraction of its FP32 rate, so the per-element
-// sums behind the objective stay off the FP64 pipe in FP32 mode: terms are
-// formed in FP32 and summed as an unevaluated pair hi + lo with the
-// error-free TwoSum transformation (Knuth; Dekker 1971), which keeps about 44
-// significant bits.  Only the cross-block reduction and the stop decision
-// run in FP64.  In FP64 mode the accumulator is a plain double.
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<float> {
-    struct V {
-        float hi, lo;
-    };
-    using S = float2;  // stored form
-    static __device__ __forceinline__ V zero() { return {0.f, 0.f}; }
-    static __device__ __forceinline__ V add(V a, V b)
-    {
-        const float s = a.hi + b.hi;
-        const float bb = s - a.hi;
-        const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
-        const float hi = s + e;
-        return {hi, e - (hi - s)};
-    }
-    static __device__ __forceinline__ V add(V a, float b) { return add(a, V{b, 0.f}); }
-    static __device__ __forceinline__ V shfl(V a, int o)
-    {
-        return {__shfl_xor_sync(kFull, a.hi, o), __shfl_xor_sync(kFull, a.lo, o)};
-    }
-    static __device__ __forceinline__ S store(V a) { return make_float2(a.hi, a.lo); }
-    static __device__ __forceinline__ V load(const S* p) { const float2 x = __ldcg(p); return {x.x, x.y}; }
-    static __device__ __forceinline__ double to_double(V a) { return (double)a.hi + (double)a.lo; }
-};
-
-template <>
-struct Acc<double> {
-    using V = double;
-    using S = double;
-    static __device__ __forceinline__ V zero() { return 0.0; }
-    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-    static __device__ __forceinline__ V shfl(V a, int o) { return __shfl_xor_sync(kFull, a, o); }
-    static __device__ __forceinline__ S store(V a) { return a; }
-    static __device__ __forceinline__ V load(const S* p) { return __ldcg(p); }
-    static __device__ __forceinline__ double to_double(V a) { return a; }
-};
-
-// Warp reduction of (sum, max): the result is valid in lane 0 (lane 0 always
-// combines in the same order, so it is deterministic).
-template <typename T>
-__device__ __forceinline__ void warp_acc_max(typename Acc<T>::V& z, T& mx)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
-    mx = warp_max(mx);
-}
-
-// Block reduction of (sum, max, max); the result is valid in thread 0.
-template <typename T>
-__device__ void block_acc_max2(typename Acc<T>::V& z, T& m1, T& m2)
-{
-    using V = typename Acc<T>::V;
-    __shared__ V sz[32];
-    __shared__ T s1[32], s2[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
-    m1 = warp_max(m1);
-    m2 = warp_max(m2);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sz[w] = z;
-        s1[w] = m1;
-        s2[w] = m2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int q = 1; q < nw; ++q) {
-            z = Acc<T>::add(z, sz[q]);
-            m1 = s1[q] > m1 ? s1[q] : m1;
-            m2 = s2[q] > m2 ? s2[q] : m2;
-        }
-    }
-}
-
-// ------------------------------------------------------------------ objective and stop rules
-
-// Alg. 1: z = 1/2 sum psi^2 + 1/2 sum delta h^2 and the stop test, run by one
-// thread after every partial of this sweep is final.
-template <typename T>
-__device__ void finalize(const SweepArgs<T>& a, double zsum, double cons, double cap)
-{
-    DevState* st = a.st;
-    const double z = 0.5 * zsum;
-    st->z = z;
-    st->cap_rel = cap;
-    st->cons_rel = cons;
-    if (a.mode == MODE_EVAL) return;
-    const double dz = z - st->z_prev;
-    st->dz = dz;
-    if (a.trace && st->evals < st->trace_len) a.trace[st->evals] = z;
-    st->evals += 1;
-    int stop = 0, reason = STOP_MAX_SWEEPS;
-    if (a.mode == MODE_SOLVE) {
-        if (!isfinite(z)) {
-            stop = 1;
-            reason = STOP_NUMERIC;
-        } else if (st->t >= st->max_sweeps) {
-            stop = 1;
-            reason = STOP_MAX_SWEEPS;
-        } else if (st->eps_obj > 0.0 && fabs(dz) < st->eps_obj) {
-            stop = 1;
-            reason = STOP_OBJECTIVE;
-        } else if (st->resid_tol > 0.0 && cap <= st->resid_tol && cons <= st->resid_tol) {
-            stop = 1;
-            reason = STOP_RESIDUAL;
-        } else if (st->eps_rel > 0.0 && fabs(dz) <= st->eps_rel * z) {
-            stop = 1;
-            reason = STOP_RELATIVE;
-        } else if (st->stop_on_rise && dz >= 0.0) {
-            // the Section 4 theorem makes z non-increasing in exact arithmetic,
-            // so a rise means rounding now dominates the progress
-            stop = 1;
-            reason = STOP_STALL;
-        }
-    }
-    if (stop) {
-        st->stop = 1;
-        st->reason = reason;
-        if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
-    } else {
-        st->z_prev = z;
-        st->t += 1;
-    }
-}
-
-// FP64 reduction of the excess blocks' partials in a fixed order, then the
-// objective and the stop test.  Run by one whole block.
-template <typename T>
-__device__ void reduce_and_finalize(const SweepArgs<T>& a)
-{
-    __shared__ double sz[32];
-    __shared__ T sm1[32], sm2[32];
-    double zs = 0.0;
-    T cm = T(0), cp = T(0);
-    for (int b = threadIdx.x; b < a.grid_v; b += blockDim.x) {
-        zs += __ldcg(a.part_h + b);
-        const T c1 = __ldcg(a.part_cons + b);
-        const T c2 = __ldcg(a.part_capb + b);
-        cm = c1 > cm ? c1 : cm;
-        cp = c2 > cp ? c2 : cp;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) zs += __shfl_xor_sync(kFull, zs, o);
-    cm = warp_max(cm);
-    cp = warp_max(cp);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        sz[w] = zs;
-        sm1[w] = cm;
-        sm2[w] = cp;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int q = 1; q < nw; ++q) {
-            zs += sz[q];
-            cm = sm1[q] > cm ? sm1[q] : cm;
-            cp = sm2[q] > cp ? sm2[q] : cp;
-        }
-        finalize(a, zs, (double)cm, (double)cp);
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finalize_kernel(SweepArgs<T> a)
@@ -301,6 +45,7 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     constexpr int N = VecOf<T>::N;
     volatile DevState* vst = a.st;
     if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
     const uint32_t vpr = (uint32_t)(a.Kp / N);
     const uint64_t total = (uint64_t)a.n * vpr;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -706,8 +451,8 @@ struct EdgeCfg {
     int V;        // vectors per lane
 };
 constexpr EdgeCfg kCfg[] = {
-    {4, 0, 1}, {8, 0, 1}, {16, 0, 1}, {32, 0, 1}, {32, 0, 2}, {32, 0, 4}, {32, 0, 8}, {32, 0, 16},
-    {0, 256, 4}, {0, 256, 8}, {0, 256, 16}, {0, 512, 16},
+    {4, 0, 1},  {8, 0, 1},  {16, 0, 1},   {32, 0, 1},   {32, 0, 2},   {32, 0, 4},
+    {32, 0, 8}, {0, 256, 2}, {0, 512, 2}, {0, 1024, 2}, {0, 1024, 4}, {0, 1024, 8},
 };
 constexpr int kNumCfg = sizeof(kCfg) / sizeof(kCfg[0]);
 
@@ -801,11 +546,11 @@ cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
     case 4: edge_group_kernel<T, 32, 2><<<g, kThreads, 0, stream>>>(a); break;
     case 5: edge_group_kernel<T, 32, 4><<<g, kThreads, 0, stream>>>(a); break;
     case 6: edge_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
-    case 7: edge_group_kernel<T, 32, 16><<<g, kThreads, 0, stream>>>(a); break;
-    case 8: edge_block_kernel<T, 256, 4><<<g, 256, 0, stream>>>(a); break;
-    case 9: edge_block_kernel<T, 256, 8><<<g, 256, 0, stream>>>(a); break;
-    case 10: edge_block_kernel<T, 256, 16><<<g, 256, 0, stream>>>(a); break;
-    case 11: edge_block_kernel<T, 512, 16><<<g, 512, 0, stream>>>(a); break;
+    case 7: edge_block_kernel<T, 256, 2><<<g, 256, 0, stream>>>(a); break;
+    case 8: edge_block_kernel<T, 512, 2><<<g, 512, 0, stream>>>(a); break;
+    case 9: edge_block_kernel<T, 1024, 2><<<g, 1024, 0, stream>>>(a); break;
+    case 10: edge_block_kernel<T, 1024, 4><<<g, 1024, 0, stream>>>(a); break;
+    case 11: edge_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpdr.so")
 
 PREC_FP32, PREC_FP64, PREC_FP32_FP64TAIL = 0, 1, 2
+ALGO_ESO, ALGO_AGD, ALGO_GDM = 0, 1, 2
 VERDICT_UNKNOWN, VERDICT_FEASIBLE, VERDICT_INFEASIBLE = 0, 1, 2
 STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall"}
 VERDICT_NAMES = {0: "unknown", 1: "feasible", 2: "infeasible"}
@@ -31,7 +32,7 @@ EXPORTS = (
     "pdr_default_options", "pdr_create", "pdr_set_options", "pdr_solve", "pdr_sweeps", "pdr_reset",
     "pdr_set_flows", "pdr_flows", "pdr_heights", "pdr_congestion", "pdr_objective", "pdr_adjacency",
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
-    "pdr_adjacency_static",
+    "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state",
 )
 
 
@@ -46,7 +47,9 @@ class PdrError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("use_graph", C.c_int32), ("eps_obj", C.c_double), ("resid_tol", C.c_double),
-        ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("reserved1", C.c_int32),
+        ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("algo", C.c_int32),
+        ("beta_init", C.c_double), ("beta_min", C.c_double), ("beta_max", C.c_double), ("alpha_inc", C.c_double),
+        ("alpha_dec", C.c_double), ("gamma", C.c_double),
     ]
 
 
@@ -99,6 +102,8 @@ def load(path: str = LIB_PATH):
         "pdr_last_error": ([vp], C.c_char_p),
         "pdr_destroy": ([vp], None),
         "pdr_adjacency_static": ([i32, i64, vp, vp, vp, vp, vp, vp], i32),
+        "pdr_gd_state": ([vp, vp, vp], i32),
+        "pdr_set_gd_state": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +252,18 @@ class Solver:
         f = np.empty((self.m, self.K), dtype=np.float64)
         self._check(self._lib.pdr_flows(self._h, _ptr(f)))
         return f
+
+    def gd_state(self):
+        """(beta [m], v [m, K]) of Alg. 3 / Alg. 4 at the current iteration."""
+        beta = np.empty(self.m, dtype=np.float64)
+        v = np.empty((self.m, self.K), dtype=np.float64)
+        self._check(self._lib.pdr_gd_state(self._h, _ptr(beta), _ptr(v)))
+        return beta, v
+
+    def set_gd_state(self, beta, v=None):
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        self._check(self._lib.pdr_set_gd_state(self._h, _ptr(beta), None if vv is None else _ptr(vv)))
 
     def heights(self) -> np.ndarray:
         h = np.empty((self.n, self.K), dtype=np.float64)

@@ -42,6 +42,7 @@ def test_default_options(lib):
     assert o.precision == pdr.PREC_FP32 and o.use_graph == 1
     assert o.eps_obj == 1e-6 and o.resid_tol == 1e-6 and o.eps_rel == 0.0
     assert o.max_sweeps == 1000000 and o.trace_len == 0
+    assert o.algo == pdr.ALGO_ESO and o.beta_init == 0.0 and o.gamma == -1.0
     assert lib.pdr_default_options(None) == 1
 
 
@@ -90,6 +91,12 @@ def test_create_rejects_bad_options(lib):
     o = pdr.default_options(max_sweeps=-1)
     st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
     assert st == 1 and "max_sweeps" in msg
+    o = pdr.default_options(algo=3)
+    st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
+    assert st == 1 and "algo" in msg
+    o = pdr.default_options(algo=2, gamma=1.5)
+    st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
+    assert st == 1 and "gamma" in msg
 
 
 def test_null_context_calls_fail_cleanly(lib):

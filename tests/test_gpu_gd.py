@@ -1,0 +1,167 @@
+"""GPU parity for Alg. 3 (PDR-AGD) and Alg. 4 (PDR-GDM) against the FP64 oracle.
+
+The accept/reject decision of an edge step (dz <= 0) is a discrete choice
+taken from floating-point sums.  Where the oracle's |dz| is within the FP32
+rounding bound of its terms, both choices are correct and either outcome is
+accepted; every other edge must take the oracle's decision and match its
+outcome to the usual tolerances (FP32: 1e-5 of the row scale plus a 1e-36
+denormal floor; FP64: 1e-12).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_07549_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+FP32_FLOOR = 1e-36
+
+
+@pytest.fixture(scope="module")
+def pdr():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_07549_gb300 import build, pdr as _pdr
+
+    build.build()
+    _pdr.load()
+    return _pdr
+
+
+def small_instances():
+    rng = np.random.default_rng(31)
+    out = [I.grid5_k10(1.3), I.grid5_k10(1.3).with_factor(0.6)]
+    out.append(I.make_instance("digraph30_k7", I.random_digraph(30, 3, rng), 7, ("uniform_int", 1, 9), 1.1, rng))
+    out.append(I.make_instance("grid6_k33", I.grid_graph(6), 33, ("lognormal", 1.0, 0.5), 1.2, rng))
+    return out
+
+
+def check_step(inst, prm, f, v, beta, t, got_f, got_v, got_b, tol, floor):
+    """Compares one GPU step with the oracle edge by edge (see module docstring)."""
+    P = oracle.Problem.from_instance(inst)
+    _, h = P.excess(f)
+    psi = P.congestion(f)
+    ambiguous = 0
+    for e in range(inst.m):
+        hi, hj = h[inst.src[e]], h[inst.col[e]]
+        fe, ve, be, acc, dz = oracle.gd_edge(prm, hi, hj, psi[e], inst.u[e], f[e], v[e], beta[e], t)
+        d = hi - hj
+        df = np.maximum(-f[e], beta[e] * (d - psi[e]))
+        psin = max(0.0, (f[e] + df).sum() - inst.u[e])
+        bound = 1e-5 * (psi[e] ** 2 + psin ** 2 + np.sum(df * df + np.abs(d * df))) + 1e-30
+        scale = np.maximum(np.abs(fe), np.abs(f[e]) + np.abs(hi) + np.abs(hj) + np.abs(v[e]))
+        ok = np.all(np.abs(got_f[e] - fe) <= tol * scale + floor)
+        if prm["momentum"]:
+            ok = ok and np.all(np.abs(got_v[e] - ve) <= tol * scale + floor)
+        ok = ok and abs(got_b[e] - be) <= tol * be
+        if ok:
+            continue
+        # a mismatch is only allowed where the decision is a rounding tie
+        assert abs(dz) <= bound, (inst.name, e, acc, dz, bound, np.abs(got_f[e] - fe).max(), got_b[e], be)
+        ambiguous += 1
+    return ambiguous
+
+
+@pytest.mark.parametrize("momentum", [False, True])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_one_gradient_step_matches_oracle(pdr, momentum, prec):
+    rng = np.random.default_rng(7)
+    algo = pdr.ALGO_GDM if momentum else pdr.ALGO_AGD
+    p = pdr.PREC_FP32 if prec == "fp32" else pdr.PREC_FP64
+    tol, floor = (1e-5, FP32_FLOOR) if prec == "fp32" else (1e-12, 0.0)
+    total_amb = 0
+    for inst in small_instances():
+        prm = oracle.gd_params(momentum, inst.K)
+        for trial in range(3):
+            f = rng.exponential(0.7, (inst.m, inst.K)) * (rng.random((inst.m, inst.K)) < 0.5)
+            v = rng.normal(0, 0.3, (inst.m, inst.K)) if momentum else np.zeros((inst.m, inst.K))
+            beta = rng.uniform(prm["beta_min"], prm["beta_max"], inst.m)
+            if prec == "fp32":
+                f, v, beta = (x.astype(np.float32).astype(np.float64) for x in (f, v, beta))
+            with pdr.Solver.from_instance(inst, precision=p, algo=algo) as s:
+                s.set_flows(f)
+                s.set_gd_state(beta, v if momentum else None)
+                s.sweeps(1)  # at t = 0: the schedule doubles beta after the decision
+                got_f = s.flows()
+                got_b, got_v = s.gd_state()
+            total_amb += check_step(inst, prm, f, v, beta, 0, got_f, got_v, got_b, tol, floor)
+    assert total_amb <= 5
+
+
+@pytest.mark.parametrize("momentum", [False, True])
+def test_large_k_block_form_gradient_step(pdr, momentum):
+    rng = np.random.default_rng(8)
+    algo = pdr.ALGO_GDM if momentum else pdr.ALGO_AGD
+    for K in (3001, 10000):
+        inst = I.make_instance(f"grid11_k{K}", I.grid_graph(11), K, ("uniform_int", 1, 5), 0.9, rng)
+        prm = oracle.gd_params(momentum, inst.K)
+        f = rng.exponential(0.5, (inst.m, inst.K)) * (rng.random((inst.m, inst.K)) < 0.5)
+        v = rng.normal(0, 0.2, (inst.m, inst.K)) if momentum else np.zeros((inst.m, inst.K))
+        beta = rng.uniform(prm["beta_min"], prm["beta_max"], inst.m)
+        f, v, beta = (x.astype(np.float32).astype(np.float64) for x in (f, v, beta))
+        with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32, algo=algo) as s:
+            s.set_flows(f)
+            s.set_gd_state(beta, v if momentum else None)
+            s.sweeps(1)
+            got_f = s.flows()
+            got_b, got_v = s.gd_state()
+        assert check_step(inst, prm, f, v, beta, 0, got_f, got_v, got_b, 1e-5, FP32_FLOOR) <= 2
+
+
+@pytest.mark.parametrize("momentum", [False, True])
+def test_fp64_gd_solve_matches_oracle(pdr, momentum):
+    """FP64 on the device: same stop sweep as the oracle and the same z trace.
+
+    An edge whose dz is zero to within FP64 rounding may be accepted by one
+    side and rejected by the other (the oracle sums sequentially, the GPU in
+    a tree); the trajectories then differ by one small step on one edge and
+    re-converge, so the trace is compared to 1e-6 relative, not bit for bit."""
+    algo = pdr.ALGO_GDM if momentum else pdr.ALGO_AGD
+    for inst in small_instances()[:3]:
+        P = oracle.Problem.from_instance(inst)
+        prm = oracle.gd_params(momentum, inst.K)
+        f_ref, _, _, rep, zt = P.solve_gd(prm, max_sweeps=30000, eps_obj=1e-6, trace=True)
+        with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64, algo=algo, eps_obj=1e-6, resid_tol=0.0,
+                                      trace_len=40000) as s:
+            r = s.solve()
+            tr = s.trace()
+            f = s.flows()
+        assert r["sweeps"] == rep["sweeps"], (inst.name, r, rep)
+        np.testing.assert_allclose(tr, zt, rtol=1e-6)
+        if not momentum:
+            assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])  # Alg. 3 never raises z
+        np.testing.assert_allclose(f, f_ref, rtol=1e-4, atol=1e-5 * inst.d.max())
+
+
+@pytest.mark.parametrize("momentum", [False, True])
+def test_gd_verdicts(pdr, momentum):
+    algo = pdr.ALGO_GDM if momentum else pdr.ALGO_AGD
+    for inst in small_instances():
+        with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32_FP64TAIL, algo=algo, eps_obj=0.0,
+                                      resid_tol=1e-6, eps_rel=1e-13, max_sweeps=600000) as s:
+            r = s.solve()
+        want = inst.feasible_by_construction
+        if want is not None:
+            assert (r["verdict"] == pdr.VERDICT_FEASIBLE) == want, (inst.name, r)
+            assert r["verdict"] != pdr.VERDICT_UNKNOWN, (inst.name, r)
+
+
+def test_gd_state_round_trip_and_reset(pdr):
+    inst = I.grid5_k10()
+    with pdr.Solver.from_instance(inst, algo=pdr.ALGO_GDM) as s:
+        b, v = s.gd_state()
+        assert np.all(b == np.float32(0.1)) and np.all(v == 0.0)
+        s.sweeps(7)
+        b1, v1 = s.gd_state()
+        assert np.any(v1 != 0.0)
+        s.reset()
+        b2, v2 = s.gd_state()
+        assert np.all(b2 == np.float32(0.1)) and np.all(v2 == 0.0)
+        with pytest.raises(pdr.PdrError):
+            s.set_gd_state(np.zeros(inst.m))
+    with pdr.Solver.from_instance(inst) as s:
+        with pytest.raises(pdr.PdrError):
+            s.gd_state()
