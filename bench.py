@@ -44,7 +44,15 @@ if ROOT not in sys.path:
 
 METRIC = "PDR edge·commodity updates/s, time-to-residual 1e-6, % of HBM peak"
 UNIT = "edge·commodity updates/s"
-WORKLOAD = "knn2500_k500: n=2500, m=15000 (3-NN both ways), K=500, d~U{1..20}, u=1.2x routing load, seed 0"
+WORKLOADS = {
+    "knn2500_k500": "knn2500_k500: n=2500, m=15000 (3-NN both ways), K=500, d~U{1..20}, u=1.2x routing load, seed 0",
+    "grid100_k10000": "grid100_k10000: 100x100 grid, n=10000, m=39600, K=10000, d~lognormal(1,0.5), u=1.1x routing "
+                      "load, seed 0",
+    "digraph20k_k2000": "digraph20k_k2000: random digraph n=20000, out-degree 5, m=100000, K=2000, d~U{1..10}, "
+                        "u=1.05x routing load, seed 0",
+}
+ALGOS = {"eso": 0, "agd": 1, "gdm": 2}
+WORKLOAD = WORKLOADS["knn2500_k500"]
 FLUSH_BYTES = 256 << 20
 
 
@@ -53,7 +61,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per step")
+    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 2000; 100 on the large workloads)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="knn2500_k500")
+    ap.add_argument("--algo", choices=sorted(ALGOS), default="eso",
+                    help="eso: Alg. 1 + Alg. 2; agd: Alg. 3; gdm: Alg. 4")
+    ap.add_argument("--compare-algos", action="store_true",
+                    help="time Alg. 1, Alg. 3 and Alg. 4 on the workload and print one comparison line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -224,6 +237,60 @@ def run_reference(args, inst):
     print(json.dumps(line), flush=True)
 
 
+def update_bytes(algo: str, inst) -> int:
+    """Algorithmic bytes of one launch of the flow-update kernel (FP32).
+
+    All: read f, write f', read h once (4K(2m + n)), tail/head/capacity per
+    edge (12m).  Alg. 3 / Alg. 4 add the rates read and written (8m); Alg. 4
+    adds the velocities read and written (8Km)."""
+    m, n, K = inst.m, inst.n, inst.K
+    b = 4 * K * (2 * m + n) + 12 * m
+    if algo in ("agd", "gdm"):
+        b += 8 * m
+    if algo == "gdm":
+        b += 8 * K * m
+    return b
+
+
+def compare_algos(args, inst, pdr, torch, stream):
+    """Alg. 1 (ESO), Alg. 3 (AGD) and Alg. 4 (GDM) on the same instance: time
+    per sweep (CUDA events around a fixed number of sweeps from f = 0), the
+    objective reached, and each update kernel alone with a cold L2."""
+    peak, peak_src = load_peaks()
+    out = {"kind": "algorithm comparison", "workload": WORKLOAD, "sweeps": args.sweeps, "dtype": "f32",
+           "peak_gbs": peak, "peak_source": peak_src, "algos": {}}
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for name, code in ALGOS.items():
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, algo=code,
+                                          eps_obj=0.0, resid_tol=0.0, max_sweeps=args.sweeps) as sv:
+                sv.solve()  # warm-up (graph capture, first touch)
+                times = []
+                for q in range(3):
+                    sv.reset()
+                    flush.fill_(q & 0xFF)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = sv.solve()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = sorted(times)[1]
+                t_up = sv.time_kernel("qp", 10, FLUSH_BYTES)
+                t_ex = sv.time_kernel("excess", 10, FLUSH_BYTES)
+        b_up = update_bytes(name, inst)
+        b_ex = 4 * inst.K * (inst.m + inst.n) + 8 * inst.m + 8 * inst.n
+        out["algos"][name] = {
+            "ms_per_sweep": ms / args.sweeps, "updates_per_s": inst.m * inst.K * args.sweeps / (ms / 1e3),
+            "z_after": r["z"], "cons_rel_after": r["cons_rel"],
+            "update_kernel_us_cold": t_up * 1e3, "update_gbs": b_up / (t_up / 1e3) / 1e9,
+            "update_frac": b_up / (t_up / 1e3) / 1e9 / peak,
+            "excess_kernel_us_cold": t_ex * 1e3, "excess_gbs": b_ex / (t_ex / 1e3) / 1e9,
+            "excess_frac": b_ex / (t_ex / 1e3) / 1e9 / peak,
+        }
+    print(json.dumps(out), flush=True)
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 
@@ -232,7 +299,13 @@ def main():
     rank, world, local = dist_info()
     from paper_2108_07549_gb300 import instances
 
-    inst = instances.knn2500_k500(1.2, seed=0)
+    inst = {"knn2500_k500": lambda: instances.knn2500_k500(1.2, seed=0),
+            "grid100_k10000": lambda: instances.grid100_k10000(1.1, seed=0),
+            "digraph20k_k2000": lambda: instances.digraph20k_k2000(1.05, seed=0)}[args.workload]()
+    if args.sweeps <= 0:
+        args.sweeps = 2000 if args.workload == "knn2500_k500" else 100
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, inst)
         return
@@ -255,13 +328,17 @@ def main():
     stream = torch.cuda.Stream()
     if args.profile_sweeps > 0:
         with torch.cuda.stream(stream):
-            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32,
+                                          algo=ALGOS[args.algo]) as sv:
                 sv.sweeps(args.profile_sweeps)
         torch.cuda.synchronize()
         return
+    if args.compare_algos:
+        compare_algos(args, inst, pdr, torch, stream)
+        return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
-                use_graph=0 if args.host_loop else 1)
+                use_graph=0 if args.host_loop else 1, algo=ALGOS[args.algo])
     m, K = inst.m, inst.K
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -349,19 +426,25 @@ def main():
             t_qp = solver.time_kernel("qp", 50, FLUSH_BYTES)
             t_ex = solver.time_kernel("excess", 50, FLUSH_BYTES)
         n = inst.n
-        bytes_qp = 4 * K * (2 * m + n) + 12 * m  # f in, f out, h once; tail, head, capacity per edge
+        bytes_qp = update_bytes(args.algo, inst)
         bytes_ex = 4 * K * (m + n) + 4 * 2 * m + 8 * n  # f once, h out; incidence lists
         share_qp = t_qp / (t_qp + t_ex)
-        dom, t_dom, b_dom = ("edge_qp", t_qp, bytes_qp) if t_qp >= t_ex else ("excess_height", t_ex, bytes_ex)
+        upd = {"eso": "edge_qp", "agd": "agd_step", "gdm": "gdm_step"}[args.algo]
+        dom, t_dom, b_dom = (upd, t_qp, bytes_qp) if t_qp >= t_ex else ("excess_height", t_ex, bytes_ex)
         peak, peak_src = load_peaks()
         achieved = b_dom / (t_dom / 1e3) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": ncu_traffic(dom), "kernel": dom,
                             "peak_source": f"{peak_src} hbm_gbs (burst copy)",
-                            "kernel_us": {"edge_qp": t_qp * 1e3, "excess_height": t_ex * 1e3},
-                            "algorithmic_bytes": {"edge_qp": bytes_qp, "excess_height": bytes_ex},
-                            "share_edge_qp": share_qp}
+                            "kernel_us": {upd: t_qp * 1e3, "excess_height": t_ex * 1e3},
+                            "algorithmic_bytes": {upd: bytes_qp, "excess_height": bytes_ex},
+                            "share_update": share_qp}
         # time to the paper's stop rule (|z^(t) - z^(t-1)| < 1e-6) from f = 0
+        if args.workload != "knn2500_k500":
+            line["cpu_baseline"] = cpu_baseline(inst, budget_s=12.0)
+            solver.close()
+            print(json.dumps(line), flush=True)
+            return
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
                                           resid_tol=1e-6, max_sweeps=1000000) as sv:

@@ -178,6 +178,13 @@ pdr_status pdr_set_flows(pdr_ctx *ctx, const double *f);
 /* Copies the current flows to host f[m*K] (double, edge-major). */
 pdr_status pdr_flows(pdr_ctx *ctx, double *f);
 
+/* Selected rows of the current state: out[q*K + k] = f_{edges[q],k}
+ * (which = 0) or the Alg. 4 velocity v_{edges[q],k} (which = 1), for
+ * q < count (double).  For checking large instances edge by edge without
+ * copying every row.  Errors: PDR_ERR_INVALID_ARG (NULL, an edge id outside
+ * [0, m), or which = 1 on a context that does not run Alg. 4). */
+pdr_status pdr_flow_rows(pdr_ctx *ctx, int32_t which, const int64_t *edges, int64_t count, double *out);
+
 /* State of Alg. 3 / Alg. 4 of the current iteration: learning rates beta[m]
  * and (Alg. 4) velocities v[m*K] (edge-major) into host arrays; either may
  * be NULL.  Errors: PDR_ERR_INVALID_ARG if the context runs Alg. 1. */

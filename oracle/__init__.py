@@ -103,6 +103,10 @@ def _load():
             lib.orc_adjacency.restype = C.c_int32
             lib.orc_excess.argtypes = [P, vp, vp, vp]
             lib.orc_excess.restype = None
+            lib.orc_excess_vertex.argtypes = [P, vp, vp, C.c_int32, vp, vp]
+            lib.orc_excess_vertex.restype = C.c_int32
+            lib.orc_congestion_edge.argtypes = [C.c_int32, vp, C.c_double]
+            lib.orc_congestion_edge.restype = C.c_double
             lib.orc_congestion.argtypes = [P, vp, vp]
             lib.orc_congestion.restype = None
             lib.orc_objective.argtypes = [P, vp, vp]
@@ -191,6 +195,17 @@ class Problem:
         h = np.empty((self.n, self.K))
         _load().orc_excess(C.byref(self._c), _ptr(f), _ptr(Delta), _ptr(h))
         return Delta, h
+
+    def excess_vertex(self, i, row_of_edge, rows):
+        """(Delta_i, h_i) at one vertex from a compact row store: rows[row_of_edge[e]] is
+        f[e, :] for every edge incident to i (row_of_edge[e] = -1 where absent)."""
+        row_of_edge = np.ascontiguousarray(row_of_edge, dtype=np.int64)
+        rows = np.ascontiguousarray(rows, dtype=np.float64)
+        D = np.empty(self.K)
+        h = np.empty(self.K)
+        if _load().orc_excess_vertex(C.byref(self._c), _ptr(row_of_edge), _ptr(rows), int(i), _ptr(D), _ptr(h)):
+            raise ValueError("a row incident to the vertex is missing")
+        return D, h
 
     def congestion(self, f):
         """psi [m]: eq. (41)."""
@@ -281,6 +296,12 @@ class Problem:
         if trace:
             return f, out, zt[: out["sweeps"] + 1]
         return f, out
+
+
+def congestion_edge(f_row, u) -> float:
+    """eq. (41) for one edge from its row of flows."""
+    f_row = np.ascontiguousarray(f_row, dtype=np.float64)
+    return float(_load().orc_congestion_edge(int(f_row.shape[0]), _ptr(f_row), float(u)))
 
 
 def gd_edge(params: dict, hi, hj, psi, u, f, v, beta, t):

@@ -146,6 +146,32 @@ void orc_excess(const orc_problem *P, const double *f, double *Delta, double *h)
     }
 }
 
+/* eq. (3), (3h), (2) at one vertex i, reading the flows of edge e from
+ * rows[row_of_edge[e]*K ...] (a compact store holding only the rows that
+ * are needed; every edge incident to i must be present).  Same summation
+ * order as orc_excess.  Returns 0, or -1 if an incident row is missing. */
+int32_t orc_excess_vertex(const orc_problem *P, const int64_t *row_of_edge, const double *rows, int32_t i,
+                          double *Delta, double *h)
+{
+    const int32_t K = P->K;
+    for (int64_t q = P->in_ptr[i]; q < P->in_ptr[i + 1]; ++q)
+        if (row_of_edge[P->in_eid[q]] < 0) return -1;
+    for (int64_t e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e)
+        if (row_of_edge[e] < 0) return -1;
+    for (int32_t k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int64_t q = P->in_ptr[i]; q < P->in_ptr[i + 1]; ++q) acc += rows[row_of_edge[P->in_eid[q]] * K + k];
+        for (int64_t e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) acc -= rows[row_of_edge[e] * K + k];
+        double hat = 0.0;
+        if (i == P->s[k]) hat = P->d[k];
+        else if (i == P->t[k]) hat = -P->d[k];
+        acc += hat;
+        Delta[k] = acc;
+        h[k] = (P->deg[i] > 0) ? acc / (double)P->deg[i] : 0.0;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Congestion: eq. (41)                                                      */
 /* ------------------------------------------------------------------------ */
@@ -162,6 +188,15 @@ void orc_congestion(const orc_problem *P, const double *f, double *psi)
         double over = tot - P->u[e];
         psi[e] = over > 0.0 ? over : 0.0;
     }
+}
+
+/* eq. (41) for one edge from its row of flows. */
+double orc_congestion_edge(int32_t K, const double *f_row, double u)
+{
+    double tot = 0.0;
+    for (int32_t k = 0; k < K; ++k) tot += f_row[k];
+    double over = tot - u;
+    return over > 0.0 ? over : 0.0;
 }
 
 /* ------------------------------------------------------------------------ */

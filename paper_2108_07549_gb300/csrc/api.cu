@@ -912,6 +912,38 @@ pdr_status pdr_flows(pdr_ctx* ctx, double* f)
                          : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
 }
 
+pdr_status pdr_flow_rows(pdr_ctx* ctx, int32_t which, const int64_t* edges, int64_t count, double* out)
+{
+    if (!ctx || count < 0 || (count > 0 && (!edges || !out)) || (which != 0 && which != 1))
+        return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "bad row request") : PDR_ERR_INVALID_ARG;
+    if (which == 1 && ctx->opt.algo != PDR_ALGO_GDM)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "velocities exist only for Alg. 4");
+    for (int64_t q = 0; q < count; ++q)
+        if (edges[q] < 0 || edges[q] >= ctx->m)
+            return ctx->fail(PDR_ERR_INVALID_ARG, "edge id out of range at " + std::to_string(q));
+    if (which == 1) {
+        pdr_status s = ctx->cur_prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
+        if (s != PDR_OK) return s;
+    }
+    const int K = ctx->K;
+    if (ctx->cur_prec) {
+        const double* base = which ? ctx->v64[ctx->cur] : ctx->f64[ctx->cur];
+        for (int64_t q = 0; q < count; ++q)
+            CK(cudaMemcpyAsync(out + q * K, base + edges[q] * ctx->Kp, sizeof(double) * K, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return PDR_OK;
+    }
+    const float* base = which ? ctx->v32[ctx->cur] : ctx->f32[ctx->cur];
+    std::vector<float> tmp((size_t)count * K);
+    for (int64_t q = 0; q < count; ++q)
+        CK(cudaMemcpyAsync(tmp.data() + q * K, base + edges[q] * ctx->Kp, sizeof(float) * K, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t q = 0; q < tmp.size(); ++q) out[q] = tmp[q];
+    return PDR_OK;
+}
+
 pdr_status pdr_gd_state(pdr_ctx* ctx, double* beta, double* v)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;

@@ -32,7 +32,7 @@ EXPORTS = (
     "pdr_default_options", "pdr_create", "pdr_set_options", "pdr_solve", "pdr_sweeps", "pdr_reset",
     "pdr_set_flows", "pdr_flows", "pdr_heights", "pdr_congestion", "pdr_objective", "pdr_adjacency",
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
-    "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state",
+    "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
 )
 
 
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "pdr_destroy": ([vp], None),
         "pdr_adjacency_static": ([i32, i64, vp, vp, vp, vp, vp, vp], i32),
         "pdr_gd_state": ([vp, vp, vp], i32),
+        "pdr_flow_rows": ([vp, i32, vp, i64, vp], i32),
         "pdr_set_gd_state": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -253,11 +254,19 @@ class Solver:
         self._check(self._lib.pdr_flows(self._h, _ptr(f)))
         return f
 
-    def gd_state(self):
-        """(beta [m], v [m, K]) of Alg. 3 / Alg. 4 at the current iteration."""
+    def flow_rows(self, edges, velocities: bool = False) -> np.ndarray:
+        """Rows f[e, :] (or the Alg. 4 velocities v[e, :]) for the given edge ids ([len(edges), K])."""
+        edges = np.ascontiguousarray(edges, dtype=np.int64)
+        out = np.empty((edges.shape[0], self.K), dtype=np.float64)
+        self._check(self._lib.pdr_flow_rows(self._h, 1 if velocities else 0, _ptr(edges), int(edges.shape[0]),
+                                            _ptr(out)))
+        return out
+
+    def gd_state(self, with_velocities: bool = True):
+        """(beta [m], v [m, K] or None) of Alg. 3 / Alg. 4 at the current iteration."""
         beta = np.empty(self.m, dtype=np.float64)
-        v = np.empty((self.m, self.K), dtype=np.float64)
-        self._check(self._lib.pdr_gd_state(self._h, _ptr(beta), _ptr(v)))
+        v = np.empty((self.m, self.K), dtype=np.float64) if with_velocities else None
+        self._check(self._lib.pdr_gd_state(self._h, _ptr(beta), None if v is None else _ptr(v)))
         return beta, v
 
     def set_gd_state(self, beta, v=None):
