@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
 
 // One block of B threads per edge (large K); thread l holds row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B) gd_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) gd_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
@@ -294,9 +294,11 @@ cudaError_t launch_gd(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
     case 6: gd_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
     case 7: gd_block_kernel<T, 256, 2><<<g, 256, 0, stream>>>(a); break;
     case 8: gd_block_kernel<T, 512, 2><<<g, 512, 0, stream>>>(a); break;
-    case 9: gd_block_kernel<T, 1024, 2><<<g, 1024, 0, stream>>>(a); break;
-    case 10: gd_block_kernel<T, 1024, 4><<<g, 1024, 0, stream>>>(a); break;
-    case 11: gd_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
+    case 9: gd_block_kernel<T, 512, 3><<<g, 512, 0, stream>>>(a); break;
+    case 10: gd_block_kernel<T, 512, 4><<<g, 512, 0, stream>>>(a); break;
+    case 11: gd_block_kernel<T, 512, 5><<<g, 512, 0, stream>>>(a); break;
+    case 12: gd_block_kernel<T, 512, 8><<<g, 512, 0, stream>>>(a); break;
+    case 13: gd_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B) edge_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
@@ -451,8 +451,10 @@ struct EdgeCfg {
     int V;        // vectors per lane
 };
 constexpr EdgeCfg kCfg[] = {
-    {4, 0, 1},  {8, 0, 1},  {16, 0, 1},   {32, 0, 1},   {32, 0, 2},   {32, 0, 4},
-    {32, 0, 8}, {0, 256, 2}, {0, 512, 2}, {0, 1024, 2}, {0, 1024, 4}, {0, 1024, 8},
+    // ordered by capacity (elements per row); two 512-thread blocks fit on an
+    // SM, so the block forms keep two edges in flight per SM up to 16,384
+    {4, 0, 1},   {8, 0, 1},   {16, 0, 1},  {32, 0, 1},  {32, 0, 2},  {32, 0, 4},  {32, 0, 8},
+    {0, 256, 2}, {0, 512, 2}, {0, 512, 3}, {0, 512, 4}, {0, 512, 5}, {0, 512, 8}, {0, 1024, 8},
 };
 constexpr int kNumCfg = sizeof(kCfg) / sizeof(kCfg[0]);
 
@@ -548,9 +550,11 @@ cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
     case 6: edge_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
     case 7: edge_block_kernel<T, 256, 2><<<g, 256, 0, stream>>>(a); break;
     case 8: edge_block_kernel<T, 512, 2><<<g, 512, 0, stream>>>(a); break;
-    case 9: edge_block_kernel<T, 1024, 2><<<g, 1024, 0, stream>>>(a); break;
-    case 10: edge_block_kernel<T, 1024, 4><<<g, 1024, 0, stream>>>(a); break;
-    case 11: edge_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
+    case 9: edge_block_kernel<T, 512, 3><<<g, 512, 0, stream>>>(a); break;
+    case 10: edge_block_kernel<T, 512, 4><<<g, 512, 0, stream>>>(a); break;
+    case 11: edge_block_kernel<T, 512, 5><<<g, 512, 0, stream>>>(a); break;
+    case 12: edge_block_kernel<T, 512, 8><<<g, 512, 0, stream>>>(a); break;
+    case 13: edge_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
