@@ -272,6 +272,63 @@ pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_
 pdr_status pdr_adjacency_static(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, int64_t *in_ptr,
                                 int32_t *in_eid, int32_t *deg, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched form: many independent instances, one graph launch per solve      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pdr_batch pdr_batch; /* opaque; owns one context per instance */
+
+/* One instance of eq. (1), with the same meaning and rules as the
+ * arguments of pdr_create. */
+typedef struct {
+    int32_t n;
+    int32_t K;
+    int64_t m;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *u;
+    const int32_t *s;
+    const int32_t *t;
+    const double *d;
+} pdr_instance;
+
+/* Creates a batch of `count` independent instances (Alg. 1 applied to each,
+ * with the options opt shared by all).  Every instance gets its own context
+ * on `stream`; an autotuner then times the edge-kernel variants that fit each
+ * instance's row length (lanes per edge, vectors per lane, block size) on
+ * that instance and keeps the fastest.  Errors: PDR_ERR_INVALID_ARG (count <
+ * 1, NULL, or an instance rejected by pdr_create: the message names it),
+ * PDR_ERR_OOM, PDR_ERR_CUDA, PDR_ERR_UNSUPPORTED. */
+pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_options *opt, void *stream,
+                            pdr_batch **out);
+
+/* Solves every instance from its current state with one CUDA graph launch:
+ * a conditional while loop whose body holds one chain of sweeps per
+ * instance; the chains are independent, so the instances run concurrently.
+ * Each instance stops by its own stop rules (a stopped instance's kernels
+ * return at once); the loop ends when the last one stops.  Then each
+ * instance's residuals and verdict are evaluated as by pdr_residuals.
+ * results may be NULL, else it receives `count` results in input order.
+ * Errors: PDR_ERR_CUDA, PDR_ERR_NUMERIC (some instance's objective became
+ * non-finite). */
+pdr_status pdr_batch_solve(pdr_batch *batch, pdr_result *results);
+
+/* Resets every instance (as pdr_reset). */
+pdr_status pdr_batch_reset(pdr_batch *batch);
+
+/* The context of instance `index`, owned by the batch (do not destroy it):
+ * use it with pdr_flows, pdr_residuals, pdr_adjacency and the other read-out
+ * calls.  Errors: PDR_ERR_INVALID_ARG. */
+pdr_status pdr_batch_context(pdr_batch *batch, int32_t index, pdr_ctx **ctx);
+
+/* The edge-kernel variant the autotuner chose for each instance
+ * (cfg[count], an index into the library's variant table) and its mean
+ * launch time in microseconds (us[count]); either may be NULL. */
+pdr_status pdr_batch_tuning(const pdr_batch *batch, int32_t *cfg, double *us);
+
+/* Frees the batch and every context it owns.  NULL is ignored. */
+void pdr_batch_destroy(pdr_batch *batch);
+
 /* Message of the last failure on ctx (or, if ctx is NULL, of the last failed
  * pdr_create or pdr_adjacency_static on this thread).  Never NULL; valid
  * until the next call. */

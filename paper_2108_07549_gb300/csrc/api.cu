@@ -254,6 +254,7 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.psi_out = nullptr;
     a.st = ctx->st;
     a.trace = ctx->trace;
+    a.active = nullptr;
     a.cond = cond;
     a.use_cond = use_cond;
     a.mode = mode;
@@ -579,6 +580,35 @@ pdr_status destroy_graphs(pdr_ctx* ctx)
     return PDR_OK;
 }
 
+// Host-side checks of an instance (the domain stated in include/pdr.h);
+// returns an empty string if it is valid.
+std::string validate_instance(int32_t n, int64_t m, const int64_t* row_ptr, const int32_t* col, const double* u,
+                              int32_t K, const int32_t* s, const int32_t* t, const double* d)
+{
+    if (n < 1) return "n must be >= 1";
+    if (m < 0 || m > (int64_t)INT32_MAX) return "m must satisfy 0 <= m < 2^31";
+    if (K < 1) return "K must be >= 1";
+    if (!row_ptr || (m > 0 && (!col || !u)) || !s || !t || !d) return "NULL input array";
+    if (row_ptr[0] != 0) return "row_ptr[0] must be 0";
+    if (row_ptr[n] != m) return "row_ptr[n] must equal m";
+    for (int32_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr must be non-decreasing (vertex " + std::to_string(i) + ")";
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col[e] < 0 || col[e] >= n) return "col out of range at edge " + std::to_string(e);
+            if (col[e] == i) return "self-loop at edge " + std::to_string(e);
+        }
+    }
+    for (int64_t e = 0; e < m; ++e)
+        if (!std::isfinite(u[e]) || u[e] < 0.0) return "capacity must be finite and >= 0 at edge " + std::to_string(e);
+    for (int32_t k = 0; k < K; ++k) {
+        if (s[k] < 0 || s[k] >= n || t[k] < 0 || t[k] >= n)
+            return "commodity endpoint out of range at k = " + std::to_string(k);
+        if (s[k] == t[k]) return "s_k == t_k at k = " + std::to_string(k);
+        if (!std::isfinite(d[k]) || !(d[k] > 0.0)) return "demand must be finite and > 0 at k = " + std::to_string(k);
+    }
+    return "";
+}
+
 }  // namespace
 
 extern "C" {
@@ -624,26 +654,9 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     };
     if (!out) return bad("out is NULL");
     *out = nullptr;
-    if (n < 1) return bad("n must be >= 1");
-    if (m < 0 || m > (int64_t)INT32_MAX) return bad("m must satisfy 0 <= m < 2^31");
-    if (K < 1) return bad("K must be >= 1");
-    if (!row_ptr || (m > 0 && (!col || !u)) || !s || !t || !d) return bad("NULL input array");
-    if (row_ptr[0] != 0) return bad("row_ptr[0] must be 0");
-    if (row_ptr[n] != m) return bad("row_ptr[n] must equal m");
-    for (int32_t i = 0; i < n; ++i) {
-        if (row_ptr[i + 1] < row_ptr[i]) return bad("row_ptr must be non-decreasing (vertex " + std::to_string(i) + ")");
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            if (col[e] < 0 || col[e] >= n) return bad("col out of range at edge " + std::to_string(e));
-            if (col[e] == i) return bad("self-loop at edge " + std::to_string(e));
-        }
-    }
-    for (int64_t e = 0; e < m; ++e)
-        if (!std::isfinite(u[e]) || u[e] < 0.0) return bad("capacity must be finite and >= 0 at edge " + std::to_string(e));
-    for (int32_t k = 0; k < K; ++k) {
-        if (s[k] < 0 || s[k] >= n || t[k] < 0 || t[k] >= n)
-            return bad("commodity endpoint out of range at k = " + std::to_string(k));
-        if (s[k] == t[k]) return bad("s_k == t_k at k = " + std::to_string(k));
-        if (!std::isfinite(d[k]) || !(d[k] > 0.0)) return bad("demand must be finite and > 0 at k = " + std::to_string(k));
+    {
+        const std::string why = validate_instance(n, m, row_ptr, col, u, K, s, t, d);
+        if (!why.empty()) return bad(why);
     }
     pdr_options o;
     fill_defaults(&o);
@@ -725,7 +738,8 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_dem_d, double, Kp);
     ALLOC(ctx->inv_dem_f, float, Kp);
     const int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
-    const int64_t np = ctx->n_psi[0] > ctx->n_psi[1] ? ctx->n_psi[0] : ctx->n_psi[1];
+    int64_t np = ctx->n_psi[0] > ctx->n_psi[1] ? ctx->n_psi[0] : ctx->n_psi[1];
+    if (np < m + 8) np = m + 8;  // any variant writes at most m + 8 edge partials
     ALLOC(ctx->part_h, double, gv);
     ALLOC(ctx->part_cons, double, gv);
     ALLOC(ctx->part_capb, double, gv);
@@ -1248,6 +1262,352 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
     cleanup();
     *ms = total / launches;
     return PDR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched form
+
+struct pdr_batch {
+    int32_t count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaStream_t> pool;  // capture streams: one branch per instance
+    std::vector<pdr_ctx*> ctx;
+    std::vector<int32_t> tuned_cfg;
+    std::vector<double> tuned_us;
+    unsigned int* active = nullptr;  // device counter of running instances
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_prec = -1;
+    bool graph_tried = false, graph_ok = false;
+};
+
+namespace {
+
+constexpr int kBatchUnroll = 2;  // sweeps per instance per iteration of the batch's while loop
+constexpr int kBatchPool = 32;   // capture streams
+
+pdr_status batch_fail(pdr_status code, const std::string& msg)
+{
+    pdr::set_thread_error(msg);
+    return code;
+}
+
+// Times the edge-kernel variants that hold this instance's rows (the
+// smallest three by capacity) and keeps the fastest.  Launches read the
+// current flows and write the other buffer, so the state is unchanged.
+template <typename T>
+pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
+{
+    const int p = Prec<T>::id;
+    std::vector<int> cand;
+    for (int c = 0; c < num_edge_configs() && (int)cand.size() < 3; ++c)
+        if (edge_capacity<T>(c) >= ctx->Kp) cand.push_back(c);
+    *best_cfg = ctx->cfg[p];
+    *best_us = -1.0;
+    if (ctx->m == 0 || cand.size() <= 1) return PDR_OK;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(launch_excess<T>(make_args<T>(ctx, MODE_EVAL), ctx->stream));
+    double best = 1e30;
+    for (int c : cand) {
+        ctx->cfg[p] = c;
+        ctx->grid_e[p] = edge_grid<T>(c, ctx->m, ctx->num_sms);
+        ctx->n_psi[p] = edge_parts<T>(c, ctx->grid_e[p]);
+        double tot = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(e0, ctx->stream);
+            launch_update<T>(ctx, make_args<T>(ctx, MODE_FORCED), ctx->stream);
+            cudaEventRecord(e1, ctx->stream);
+            cudaError_t err = cudaEventSynchronize(e1);
+            if (err != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return ctx->cuda_fail("autotune", err);
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) tot += ms;  // the first launch warms up
+        }
+        const double us = tot / 3.0 * 1e3;
+        if (us < best) {
+            best = us;
+            *best_cfg = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->cfg[p] = *best_cfg;
+    ctx->grid_e[p] = edge_grid<T>(*best_cfg, ctx->m, ctx->num_sms);
+    ctx->n_psi[p] = edge_parts<T>(*best_cfg, ctx->grid_e[p]);
+    *best_us = best;
+    destroy_graphs(ctx);
+    pdr_status s = refresh_psi<T>(ctx);
+    if (s != PDR_OK) return s;
+    return init_state(ctx, true, 0);
+}
+
+void batch_destroy_graph(pdr_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_tried = b->graph_ok = false;
+}
+
+template <typename T>
+SweepArgs<T> batch_args(pdr_batch* b, pdr_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, int par)
+{
+    SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, use_cond, h, par, 0);
+    a.active = b->active;
+    return a;
+}
+
+// One graph: a conditional while node whose body forks one branch per
+// instance (kBatchUnroll sweeps each) and joins them.
+template <typename T>
+void batch_build_graph(pdr_batch* b)
+{
+    b->graph_tried = true;
+    b->graph_prec = Prec<T>::id;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t node;
+    cudaGraphNodeParams np{};
+    cudaGraph_t body, captured;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    bool ok = true;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) goto fail;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) goto fail;
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) goto fail;
+    body = np.conditional.phGraph_out[0];
+    ev.resize(b->pool.size() + 1);
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) ok = false;
+    if (!ok) goto fail;
+    if (cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        goto fail;
+    {
+        cudaError_t e = cudaEventRecord(ev[0], b->cap_stream);
+        for (size_t p = 0; p < b->pool.size() && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(b->pool[p], ev[0], 0);
+        for (int32_t i = 0; i < b->count && e == cudaSuccess; ++i) {
+            cudaStream_t s = b->pool[i % b->pool.size()];
+            for (int q = 0; q < kBatchUnroll && e == cudaSuccess; ++q) {
+                SweepArgs<T> a = batch_args<T>(b, b->ctx[i], 1, h, q & 1);
+                e = launch_excess<T>(a, s);
+                if (e == cudaSuccess) e = launch_update<T>(b->ctx[i], a, s);
+            }
+        }
+        for (size_t p = 0; p < b->pool.size() && e == cudaSuccess; ++p) {
+            e = cudaEventRecord(ev[p + 1], b->pool[p]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, ev[p + 1], 0);
+        }
+        cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &captured);
+        if (e != cudaSuccess || e3 != cudaSuccess) goto fail;
+    }
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) goto fail;
+    for (auto& e : ev) cudaEventDestroy(e);
+    b->graph = g;
+    b->exec = exec;
+    b->graph_ok = true;
+    return;
+fail:
+    cudaGetLastError();
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    b->graph_ok = false;
+}
+
+__global__ void set_counter_kernel(unsigned int* c, unsigned int v) { *c = v; }
+
+template <typename T>
+pdr_status batch_run(pdr_batch* b)
+{
+    for (pdr_ctx* c : b->ctx) {
+        pdr_status s = ensure_velocity<T>(c);
+        if (s != PDR_OK) return s;
+        s = flows_to_buffer0<T>(c);
+        if (s != PDR_OK) return s;
+        s = init_state(c, true, 0);
+        if (s != PDR_OK) return s;
+    }
+    set_counter_kernel<<<1, 1, 0, b->stream>>>(b->active, (unsigned int)b->count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+    const bool use_graph = b->ctx[0]->opt.use_graph != 0;
+    if (use_graph && (!b->graph_tried || b->graph_prec != Prec<T>::id)) {
+        batch_destroy_graph(b);
+        batch_build_graph<T>(b);
+    }
+    if (use_graph && b->graph_ok) {
+        e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    } else {
+        // host loop: chunks of an even number of sweeps for every instance
+        for (;;) {
+            for (int q = 0; q < 64; ++q)
+                for (pdr_ctx* c : b->ctx) {
+                    SweepArgs<T> a = batch_args<T>(b, c, 0, 0, q & 1);
+                    launch_excess<T>(a, b->stream);
+                    launch_update<T>(c, a, b->stream);
+                }
+            unsigned int left = 0;
+            e = cudaMemcpyAsync(&left, b->active, sizeof(left), cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+            if (left == 0) break;
+        }
+    }
+    for (pdr_ctx* c : b->ctx) {
+        pdr_status s = read_state(c);
+        if (s != PDR_OK) return s;
+        c->cur = (int)(c->hst->t & 1);
+    }
+    return PDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pdr_status pdr_batch_create(int32_t count, const pdr_instance* inst, const pdr_options* opt, void* stream,
+                            pdr_batch** out)
+{
+    pdr::set_thread_error("");
+    if (!out) return batch_fail(PDR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !inst) return batch_fail(PDR_ERR_INVALID_ARG, "count must be >= 1 and inst non-NULL");
+    pdr_options o;
+    fill_defaults(&o);
+    if (opt) o = *opt;
+    if (o.precision == PDR_PREC_FP32_FP64TAIL)
+        return batch_fail(PDR_ERR_UNSUPPORTED, "the batched form runs PDR_PREC_FP32 or PDR_PREC_FP64");
+    {
+        std::string why;
+        if (!options_ok(&o, &why)) return batch_fail(PDR_ERR_INVALID_ARG, why);
+    }
+    for (int32_t i = 0; i < count; ++i) {
+        const pdr_instance& q = inst[i];
+        const std::string why = validate_instance(q.n, q.m, q.row_ptr, q.col, q.u, q.K, q.s, q.t, q.d);
+        if (!why.empty()) return batch_fail(PDR_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": " + why);
+    }
+    pdr_batch* b = new pdr_batch();
+    b->count = count;
+    b->stream = static_cast<cudaStream_t>(stream);
+    auto give_up = [&](pdr_status code, const std::string& msg) {
+        pdr_batch_destroy(b);
+        return batch_fail(code, msg);
+    };
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return give_up(PDR_ERR_CUDA, "batch: stream creation failed");
+    const int np = count < kBatchPool ? count : kBatchPool;
+    for (int p = 0; p < np; ++p) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return give_up(PDR_ERR_CUDA, "batch: stream creation failed");
+        b->pool.push_back(s);
+    }
+    if (cudaMalloc(&b->active, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        return give_up(PDR_ERR_OOM, "batch: counter allocation failed");
+    }
+    for (int32_t i = 0; i < count; ++i) {
+        const pdr_instance& q = inst[i];
+        pdr_ctx* c = nullptr;
+        pdr_status s = pdr_create(q.n, q.m, q.row_ptr, q.col, q.u, q.K, q.s, q.t, q.d, &o, stream, &c);
+        if (s != PDR_OK) {
+            const std::string why = pdr_last_error(nullptr);
+            return give_up(s, "instance " + std::to_string(i) + ": " + why);
+        }
+        b->ctx.push_back(c);
+    }
+    b->tuned_cfg.assign(count, -1);
+    b->tuned_us.assign(count, -1.0);
+    for (int32_t i = 0; i < count; ++i) {
+        pdr_ctx* c = b->ctx[i];
+        pdr_status s = c->cur_prec ? autotune<double>(c, &b->tuned_cfg[i], &b->tuned_us[i])
+                                   : autotune<float>(c, &b->tuned_cfg[i], &b->tuned_us[i]);
+        if (s != PDR_OK) return give_up(s, "instance " + std::to_string(i) + ": " + c->err);
+    }
+    *out = b;
+    return PDR_OK;
+}
+
+pdr_status pdr_batch_solve(pdr_batch* b, pdr_result* results)
+{
+    if (!b) return PDR_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    pdr_status s = b->ctx[0]->cur_prec ? batch_run<double>(b) : batch_run<float>(b);
+    if (s != PDR_OK) return s;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool numeric = false;
+    for (int32_t i = 0; i < b->count; ++i) {
+        pdr_ctx* c = b->ctx[i];
+        pdr_result r{};
+        r.sweeps = c->hst->t;
+        r.sweeps_fp64 = c->cur_prec ? c->hst->t : 0;
+        r.dz = c->hst->dz;
+        r.stop_reason = c->hst->reason;
+        s = residuals_into(c, &r);
+        if (s != PDR_OK) return batch_fail(s, "instance " + std::to_string(i) + ": " + c->err);
+        r.ms_total = ms;
+        c->last = r;
+        if (results) results[i] = r;
+        if (r.stop_reason == STOP_NUMERIC) numeric = true;
+    }
+    if (numeric) return batch_fail(PDR_ERR_NUMERIC, "an instance's objective became non-finite");
+    return PDR_OK;
+}
+
+pdr_status pdr_batch_reset(pdr_batch* b)
+{
+    if (!b) return PDR_ERR_INVALID_ARG;
+    for (pdr_ctx* c : b->ctx) {
+        pdr_status s = pdr_reset(c);
+        if (s != PDR_OK) return s;
+    }
+    return PDR_OK;
+}
+
+pdr_status pdr_batch_context(pdr_batch* b, int32_t index, pdr_ctx** ctx)
+{
+    if (!b || !ctx || index < 0 || index >= b->count) return PDR_ERR_INVALID_ARG;
+    *ctx = b->ctx[index];
+    return PDR_OK;
+}
+
+pdr_status pdr_batch_tuning(const pdr_batch* b, int32_t* cfg, double* us)
+{
+    if (!b) return PDR_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < b->count; ++i) {
+        if (cfg) cfg[i] = b->tuned_cfg[i];
+        if (us) us[i] = b->tuned_us[i];
+    }
+    return PDR_OK;
+}
+
+void pdr_batch_destroy(pdr_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_destroy_graph(b);
+    for (pdr_ctx* c : b->ctx) pdr_destroy(c);
+    for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->active) cudaFree(b->active);
+    cudaGetLastError();
+    delete b;
 }
 
 }  // extern "C"

@@ -110,6 +110,7 @@ struct SweepArgs {
     T* psi_out;         // optional [m] congestion output of the edge kernel
     DevState* st;
     double* trace;
+    unsigned int* active;  // batched solves: instances still running (NULL for one instance)
     cudaGraphConditionalHandle cond;
     int use_cond;
     int mode;
@@ -130,6 +131,9 @@ template <typename T>
 int edge_grid(int cfg, int64_t m, int num_sms);  // grid size of that variant
 template <typename T>
 int64_t edge_parts(int cfg, int grid);  // number of partials that grid writes
+template <typename T>
+int edge_capacity(int cfg);             // elements per row a variant holds (-1 if none)
+int num_edge_configs();
 int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
 template <typename T>
 int excess_resident_blocks();  // excess blocks resident per SM (occupancy)

@@ -493,6 +493,14 @@ int edge_grid(int cfg, int64_t m, int num_sms)
 }
 
 template <typename T>
+int edge_capacity(int cfg)
+{
+    return (cfg >= 0 && cfg < kNumCfg) ? capacity<T>(cfg) : -1;
+}
+
+int num_edge_configs() { return kNumCfg; }
+
+template <typename T>
 int64_t edge_parts(int cfg, int grid)
 {
     return kCfg[cfg].G ? (int64_t)grid * (kThreads / 32) : (int64_t)grid;
@@ -573,6 +581,8 @@ template int edge_config<float>(int);
 template int edge_config<double>(int);
 template int edge_grid<float>(int, int64_t, int);
 template int64_t edge_parts<float>(int, int);
+template int edge_capacity<float>(int);
+template int edge_capacity<double>(int);
 template int64_t edge_parts<double>(int, int);
 template int edge_grid<double>(int, int64_t, int);
 template cudaError_t launch_excess<float>(const SweepArgs<float>&, cudaStream_t);

@@ -220,7 +220,9 @@ __device__ void finalize(const SweepArgs<T>& a, double zsum, double cons, double
     if (stop) {
         st->stop = 1;
         st->reason = reason;
-        if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+        // one instance: its stop ends the loop; a batch ends with its last instance
+        const bool last = a.active ? atomicSub(a.active, 1u) == 1u : true;
+        if (a.use_cond && last) cudaGraphSetConditional(a.cond, 0);
     } else {
         st->z_prev = z;
         st->t += 1;

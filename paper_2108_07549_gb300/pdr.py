@@ -33,6 +33,8 @@ EXPORTS = (
     "pdr_set_flows", "pdr_flows", "pdr_heights", "pdr_congestion", "pdr_objective", "pdr_adjacency",
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
+    "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
+    "pdr_batch_destroy",
 )
 
 
@@ -66,6 +68,11 @@ class Result(C.Structure):
         out["verdict_name"] = VERDICT_NAMES.get(self.verdict, "?")
         out["stop_name"] = STOP_NAMES.get(self.stop_reason, "?")
         return out
+
+
+class InstanceC(C.Structure):
+    _fields_ = [("n", C.c_int32), ("K", C.c_int32), ("m", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("u", C.c_void_p), ("s", C.c_void_p), ("t", C.c_void_p), ("d", C.c_void_p)]
 
 
 _lib = None
@@ -104,6 +111,12 @@ def load(path: str = LIB_PATH):
         "pdr_adjacency_static": ([i32, i64, vp, vp, vp, vp, vp, vp], i32),
         "pdr_gd_state": ([vp, vp, vp], i32),
         "pdr_flow_rows": ([vp, i32, vp, i64, vp], i32),
+        "pdr_batch_create": ([i32, P(InstanceC), P(Options), vp, P(vp)], i32),
+        "pdr_batch_solve": ([vp, P(Result)], i32),
+        "pdr_batch_reset": ([vp], i32),
+        "pdr_batch_context": ([vp, i32, P(vp)], i32),
+        "pdr_batch_tuning": ([vp, vp, vp], i32),
+        "pdr_batch_destroy": ([vp], None),
         "pdr_set_gd_state": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -319,3 +332,91 @@ class Solver:
         w = {"qp": 0, "excess": 1}[which]
         self._check(self._lib.pdr_time_kernel(self._h, w, int(launches), int(flush_bytes), C.byref(ms)))
         return ms.value
+
+
+class _BorrowedSolver(Solver):
+    """A Solver view of a context owned by a Batch (never destroyed by Python)."""
+
+    def __init__(self, lib, handle, inst_sizes, options):
+        self._lib = lib
+        self._h = handle
+        self.n, self.m, self.K = inst_sizes
+        self.options = options
+        self.Kp = self.sizes()[3]
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Many independent instances solved together (the batched form).
+
+    ``instances`` is a sequence of objects with ``n, row_ptr, col, u, s, t, d``
+    (e.g. ``instances.Instance``).  One CUDA graph launch per ``solve()``
+    runs every instance to its own stop rule.
+    """
+
+    def __init__(self, instances, stream=None, **options):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        arr = (InstanceC * len(instances))()
+        for i, inst in enumerate(instances):
+            a = [np.ascontiguousarray(x, dt) for x, dt in ((inst.row_ptr, np.int64), (inst.col, np.int32),
+                                                            (inst.u, np.float64), (inst.s, np.int32),
+                                                            (inst.t, np.int32), (inst.d, np.float64))]
+            self._keep.append(a)
+            arr[i] = InstanceC(int(inst.n), int(a[3].shape[0]), int(a[1].shape[0]), *(_ptr(x) for x in a))
+        self.options = default_options(**options)
+        if stream is None:
+            stream = _current_stream()
+        elif not isinstance(stream, C.c_void_p):
+            stream = C.c_void_p(int(stream))
+        h = C.c_void_p()
+        st = lib.pdr_batch_create(len(instances), arr, C.byref(self.options), stream, C.byref(h))
+        if st != 0:
+            raise PdrError(st, lib.pdr_last_error(None).decode())
+        self._h = h
+        self.count = len(instances)
+        self._sizes = [(int(x.n), int(x.col.shape[0]), int(x.s.shape[0])) for x in instances]
+
+    def _check(self, status):
+        if status != 0:
+            raise PdrError(status, self._lib.pdr_last_error(None).decode())
+
+    def solve(self):
+        res = (Result * self.count)()
+        self._check(self._lib.pdr_batch_solve(self._h, res))
+        return [r.as_dict() for r in res]
+
+    def reset(self):
+        self._check(self._lib.pdr_batch_reset(self._h))
+
+    def solver(self, index: int) -> Solver:
+        """A read-out view of instance ``index`` (flows, residuals, adjacency...)."""
+        h = C.c_void_p()
+        self._check(self._lib.pdr_batch_context(self._h, int(index), C.byref(h)))
+        return _BorrowedSolver(self._lib, h, self._sizes[index], self.options)
+
+    def tuning(self):
+        cfg = np.empty(self.count, dtype=np.int32)
+        us = np.empty(self.count, dtype=np.float64)
+        self._check(self._lib.pdr_batch_tuning(self._h, _ptr(cfg), _ptr(us)))
+        return cfg, us
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pdr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

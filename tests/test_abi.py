@@ -104,3 +104,24 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pdr_sweeps(None, 1) == 1
     assert lib.pdr_reset(None) == 1
     lib.pdr_destroy(None)
+
+
+def test_batch_create_rejects_invalid_instances(lib):
+    from paper_2108_07549_gb300 import pdr
+
+    good = pdr.InstanceC(3, 1, 3, *(x.ctypes.data_as(C.c_void_p) for x in _BASE_ARRAYS))
+    bad = pdr.InstanceC(3, 1, 3, *(x.ctypes.data_as(C.c_void_p) for x in _BAD_ARRAYS))
+    arr = (pdr.InstanceC * 2)(good, bad)
+    h = C.c_void_p()
+    assert lib.pdr_batch_create(0, arr, None, None, C.byref(h)) == 1
+    assert lib.pdr_batch_create(2, arr, None, None, C.byref(h)) == 1
+    assert "instance 1" in lib.pdr_last_error(None).decode() and "self-loop" in lib.pdr_last_error(None).decode()
+    o = pdr.default_options(precision=pdr.PREC_FP32_FP64TAIL)
+    assert lib.pdr_batch_create(1, arr, C.byref(o), None, C.byref(h)) == 6
+    assert not h.value
+
+
+_BASE_ARRAYS = [np.array([0, 1, 2, 3], np.int64), np.array([1, 2, 0], np.int32), np.ones(3),
+                np.array([0], np.int32), np.array([2], np.int32), np.ones(1)]
+_BAD_ARRAYS = [np.array([0, 1, 2, 3], np.int64), np.array([1, 2, 2], np.int32), np.ones(3),
+               np.array([0], np.int32), np.array([2], np.int32), np.ones(1)]
