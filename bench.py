@@ -50,6 +50,8 @@ WORKLOADS = {
                       "load, seed 0",
     "digraph20k_k2000": "digraph20k_k2000: random digraph n=20000, out-degree 5, m=100000, K=2000, d~U{1..10}, "
                         "u=1.05x routing load, seed 0",
+    "batch256": "batch256: 256 random out-degree-4 digraphs, n~U[100,5000], K~U[10,1000], d~U{1..10}, u=1.2x "
+                "routing load (20% at 0.7x), seed 0",
 }
 ALGOS = {"eso": 0, "agd": 1, "gdm": 2}
 WORKLOAD = WORKLOADS["knn2500_k500"]
@@ -291,6 +293,63 @@ def compare_algos(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+def bench_batch(args, insts, pdr, torch, stream):
+    """The batched form against the single-instance form on the same GPU: the
+    same instances, the same S sweeps each (Alg. 1 + Alg. 2, FP32), solved
+    (a) by one batch (one graph launch per solve) and (b) one after another,
+    each by its own context (one graph launch per instance).  Both include
+    the per-instance reset and FP64 residual pass."""
+    import numpy as np
+
+    S = args.sweeps
+    opts = dict(precision=pdr.PREC_FP32, eps_obj=0.0, resid_tol=0.0, max_sweeps=S)
+    total = sum(x.m * x.K for x in insts) * S
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        B = pdr.Batch(insts, stream=stream.cuda_stream, **opts)
+        t_create = time.perf_counter() - t0
+        cfg, us = B.tuning()
+        B.solve()
+        bt = []
+        for q in range(max(1, args.steps)):
+            B.reset()
+            flush.fill_(q & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = B.solve()
+            bt.append(time.perf_counter() - t0)
+        verdicts = [r["verdict_name"] for r in res]
+        assert all(r["sweeps"] == S for r in res)
+        B.close()
+        singles = [pdr.Solver.from_instance(x, stream=stream.cuda_stream, **opts) for x in insts]
+        for sv in singles:
+            sv.solve()
+        st = []
+        for q in range(max(1, args.steps)):
+            for sv in singles:
+                sv.reset()
+            flush.fill_(q & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for sv in singles:
+                sv.solve()
+            st.append(time.perf_counter() - t0)
+        for sv in singles:
+            sv.close()
+    tb, ts = sorted(bt)[len(bt) // 2], sorted(st)[len(st) // 2]
+    vals, counts = np.unique(cfg, return_counts=True)
+    print(json.dumps({
+        "kind": "batched form", "workload": WORKLOAD, "instances": len(insts), "sweeps_per_instance": S,
+        "updates_per_solve": total, "dtype": "f32",
+        "batch": {"s_per_solve": tb, "updates_per_s": total / tb, "create_and_autotune_s": t_create},
+        "single_form_sequential": {"s_per_solve": ts, "updates_per_s": total / ts},
+        "speedup": ts / tb,
+        "autotuner_variants": {str(int(v)): int(c) for v, c in zip(vals, counts)},
+        "verdicts_after_S": {v: verdicts.count(v) for v in sorted(set(verdicts))},
+    }), flush=True)
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 
@@ -301,7 +360,9 @@ def main():
 
     inst = {"knn2500_k500": lambda: instances.knn2500_k500(1.2, seed=0),
             "grid100_k10000": lambda: instances.grid100_k10000(1.1, seed=0),
-            "digraph20k_k2000": lambda: instances.digraph20k_k2000(1.05, seed=0)}[args.workload]()
+            "digraph20k_k2000": lambda: instances.digraph20k_k2000(1.05, seed=0),
+            # a spawn pool, before any CUDA work in this process
+            "batch256": lambda: instances.batch256(seed=0, processes=os.cpu_count() or 1)}[args.workload]()
     if args.sweeps <= 0:
         args.sweeps = 2000 if args.workload == "knn2500_k500" else 100
     global WORKLOAD
@@ -335,6 +396,9 @@ def main():
         return
     if args.compare_algos:
         compare_algos(args, inst, pdr, torch, stream)
+        return
+    if args.workload == "batch256":
+        bench_batch(args, inst, pdr, torch, stream)
         return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,

@@ -284,23 +284,36 @@ def digraph20k_k2000(factor: float = 1.05, seed: int = 0) -> Instance:
     return make_instance(f"digraph20k_k2000@{factor:g}", g, 2000, ("uniform_int", 1, 10), factor, rng)
 
 
+def _batch_member(args):
+    seed, b, n, K, factor = args
+    sub = np.random.default_rng([seed, b])
+    g = random_digraph(n, 4, sub)
+    return make_instance(f"batch{b}@{factor:g}", g, K, ("uniform_int", 1, 10), factor, sub)
+
+
 def batch256(seed: int = 0, count: int = 256, n_range=(100, 5000), k_range=(10, 1000),
-             infeasible_share: float = 0.2):
+             infeasible_share: float = 0.2, processes: int = 0):
     """Independent instances of uneven size: random out-degree-4 digraphs.
 
     n and K are uniform in their ranges, demands integers in [1, 10],
     capacities 1.2x the routing load, and ``infeasible_share`` of the
-    instances scaled to 0.7x instead (infeasible by construction).
+    instances scaled to 0.7x instead (infeasible by construction).  Instance
+    b draws from its own generator seeded by (seed, b), so ``processes > 1``
+    (a spawn-context pool; call it before any CUDA work) gives the same
+    instances faster.
     """
     rng = np.random.default_rng(seed)
-    out = []
     n_bad = int(round(infeasible_share * count))
     bad = set(rng.choice(count, size=n_bad, replace=False).tolist())
+    jobs = []
     for b in range(count):
         n = int(rng.integers(n_range[0], n_range[1] + 1))
         K = int(rng.integers(k_range[0], k_range[1] + 1))
-        sub = np.random.default_rng([seed, b])
-        g = random_digraph(n, 4, sub)
-        factor = 0.7 if b in bad else 1.2
-        out.append(make_instance(f"batch{b}@{factor:g}", g, K, ("uniform_int", 1, 10), factor, sub))
-    return out
+        jobs.append((seed, b, n, K, 0.7 if b in bad else 1.2))
+    if processes and processes > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(max_workers=processes, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_member, jobs, chunksize=4))
+    return [_batch_member(j) for j in jobs]
