@@ -655,3 +655,127 @@ int32_t orc_solve_gd(const orc_problem *P, const orc_options *opt, const orc_gd_
     free(psi);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode through T unrolled sweeps of Alg. 1 (differentiated form)    */
+/* ------------------------------------------------------------------------ */
+
+/* L(u, d) = z(f^(T)) with f^(0) = 0 and f^(t+1) = one sweep of Alg. 1 (eq. (3),
+ * (2), then Alg. 2 on every edge).  Computes L and its gradient with respect
+ * to the capacities u (grad_u[m]) and the demands d (grad_d[K]).
+ *
+ * Derivatives used (all from the paper's formulas):
+ *  - dz/df_e,k = psi_e + h_jk - h_ik (eq. "cpgrad"); dz/du_e = -psi_e;
+ *    dz/dd_k = h_{s_k,k} - h_{t_k,k} (d_k enters Delta at s_k with +, at t_k
+ *    with -, eq. (3h), and d(1/2 delta h^2)/dDelta = h).
+ *  - Alg. 2 output f'_k = max(0, c_k - theta): uncongested (theta = 0):
+ *    df'_k/dc_k = [c_k > 0]; congested, A = {c_k > theta},
+ *    theta = (sum_A c - u)/(2 + |A|): df'_k/dc_l = [k in A]([k = l] - [l in A]/(2 + |A|)),
+ *    df'_k/du = [k in A]/(2 + |A|).
+ *  - c_k = f_k + (h_ik - h_jk)/2, h = Delta/delta, Delta linear in f and d.
+ * Stores every f^(t) (memory T*m*K doubles: for small instances).
+ * Returns 0, or -1 on allocation failure. */
+int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *grad_u, double *grad_d)
+{
+    const int32_t n = P->n, K = P->K;
+    const int64_t m = P->m, mk = m * (int64_t)K, nk = (int64_t)n * K;
+    double *fs = (double *)calloc((size_t)(T + 1) * (size_t)mk + 1, sizeof(double)); /* f^(0..T) */
+    double *Delta = (double *)malloc(sizeof(double) * (size_t)nk + 8);
+    double *h = (double *)malloc(sizeof(double) * (size_t)nk + 8);
+    double *psi = (double *)malloc(sizeof(double) * (size_t)m + 8);
+    double *fbar = (double *)malloc(sizeof(double) * (size_t)mk + 8);   /* dL/df^(t+1), then dL/df^(t) */
+    double *cbar = (double *)malloc(sizeof(double) * (size_t)mk + 8);
+    double *Dbar = (double *)malloc(sizeof(double) * (size_t)nk + 8);   /* dL/dDelta^(t) */
+    double *c = (double *)malloc(sizeof(double) * (size_t)K + 8);
+    double *pos = (double *)malloc(sizeof(double) * (size_t)K + 8);
+    double *fn = (double *)malloc(sizeof(double) * (size_t)K + 8);
+    if (!fs || !Delta || !h || !psi || !fbar || !cbar || !Dbar || !c || !pos || !fn) {
+        free(fs); free(Delta); free(h); free(psi); free(fbar); free(cbar); free(Dbar); free(c); free(pos); free(fn);
+        return -1;
+    }
+    /* forward: f^(t+1) from f^(t) */
+    for (int64_t t = 0; t < T; ++t) {
+        orc_excess(P, fs + t * mk, Delta, h);
+        orc_qp_all(P, h, fs + t * mk, fs + (t + 1) * mk, NULL);
+    }
+    /* L = z(f^(T)) and its seeds */
+    orc_excess(P, fs + T * mk, Delta, h);
+    orc_congestion(P, fs + T * mk, psi);
+    *L_out = orc_objective(P, h, psi);
+    for (int64_t e = 0; e < m; ++e) {
+        const double *hi = h + (int64_t)P->src[e] * K, *hj = h + (int64_t)P->col[e] * K;
+        for (int32_t k = 0; k < K; ++k) fbar[e * K + k] = psi[e] + hj[k] - hi[k];
+        grad_u[e] = -psi[e];
+    }
+    for (int32_t k = 0; k < K; ++k)
+        grad_d[k] = h[(int64_t)P->s[k] * K + k] - h[(int64_t)P->t[k] * K + k];
+    /* reverse through the sweeps */
+    for (int64_t t = T - 1; t >= 0; --t) {
+        const double *f = fs + t * mk;
+        orc_excess(P, f, Delta, h);
+        /* Alg. 2 backward, edge by edge: fbar holds dL/df^(t+1) */
+        for (int64_t e = 0; e < m; ++e) {
+            const double *hi = h + (int64_t)P->src[e] * K, *hj = h + (int64_t)P->col[e] * K;
+            double r, theta2;
+            orc_edge_qp(K, hi, hj, f + e * K, P->u[e], fn, &r, &theta2, c, pos); /* psi' = 2 theta */
+            /* orc_edge_qp leaves c_k = 1/2((h_ik + f_k) - (h_jk - f_k)) in c */
+            double theta = theta2 / 2.0;
+            int32_t congested = theta2 > 0.0;
+            double Sbar = 0.0;
+            int32_t nA = 0;
+            for (int32_t k = 0; k < K; ++k) {
+                int32_t act = congested ? (c[k] > theta) : (c[k] > 0.0);
+                if (act) {
+                    Sbar += fbar[e * K + k];
+                    ++nA;
+                }
+            }
+            double corr = congested ? Sbar / (2.0 + (double)nA) : 0.0;
+            for (int32_t k = 0; k < K; ++k) {
+                int32_t act = congested ? (c[k] > theta) : (c[k] > 0.0);
+                cbar[e * K + k] = act ? fbar[e * K + k] - corr : 0.0;
+            }
+            grad_u[e] += corr;
+        }
+        /* c = f + (h_i - h_j)/2: hbar_i += cbar/2 on out-edges, hbar_j -= cbar/2 on in-edges;
+         * Dbar = hbar / delta */
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = 0; k < K; ++k) {
+                double hb = 0.0;
+                for (int64_t e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) hb += 0.5 * cbar[e * K + k];
+                for (int64_t q = P->in_ptr[i]; q < P->in_ptr[i + 1]; ++q) hb -= 0.5 * cbar[P->in_eid[q] * K + k];
+                Dbar[(int64_t)i * K + k] = P->deg[i] > 0 ? hb / (double)P->deg[i] : 0.0;
+            }
+        /* Delta = sum_in f - sum_out f + hat-Delta(d) */
+        for (int32_t k = 0; k < K; ++k)
+            grad_d[k] += Dbar[(int64_t)P->s[k] * K + k] - Dbar[(int64_t)P->t[k] * K + k];
+        for (int64_t e = 0; e < m; ++e)
+            for (int32_t k = 0; k < K; ++k)
+                fbar[e * K + k] = cbar[e * K + k] + Dbar[(int64_t)P->col[e] * K + k] - Dbar[(int64_t)P->src[e] * K + k];
+    }
+    free(fs); free(Delta); free(h); free(psi); free(fbar); free(cbar); free(Dbar); free(c); free(pos); free(fn);
+    return 0;
+}
+
+/* L(u, d) = z(f^(T)) alone (the forward of orc_adjoint_eso), for finite differences. */
+double orc_unrolled_objective(const orc_problem *P, int64_t T)
+{
+    const int64_t mk = P->m * (int64_t)P->K, nk = (int64_t)P->n * P->K;
+    double *f = (double *)calloc((size_t)mk + 1, sizeof(double));
+    double *g = (double *)calloc((size_t)mk + 1, sizeof(double));
+    double *Delta = (double *)malloc(sizeof(double) * (size_t)nk + 8);
+    double *h = (double *)malloc(sizeof(double) * (size_t)nk + 8);
+    double *psi = (double *)malloc(sizeof(double) * (size_t)P->m + 8);
+    for (int64_t t = 0; t < T; ++t) {
+        orc_excess(P, f, Delta, h);
+        orc_qp_all(P, h, f, g, NULL);
+        double *x = f;
+        f = g;
+        g = x;
+    }
+    orc_excess(P, f, Delta, h);
+    orc_congestion(P, f, psi);
+    double z = orc_objective(P, h, psi);
+    free(f); free(g); free(Delta); free(h); free(psi);
+    return z;
+}
