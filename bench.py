@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="knn2500_k500")
     ap.add_argument("--algo", choices=sorted(ALGOS), default="eso",
                     help="eso: Alg. 1 + Alg. 2; agd: Alg. 3; gdm: Alg. 4")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the differentiated form (T = 50 sweeps, checkpoints every 10) on the workload")
     ap.add_argument("--compare-algos", action="store_true",
                     help="time Alg. 1, Alg. 3 and Alg. 4 on the workload and print one comparison line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
@@ -293,6 +295,36 @@ def compare_algos(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
+    """The differentiated form: L = z(f^(T)) and its gradient w.r.t. u and d
+    by reverse mode through T sweeps with checkpoints every ckpt, against the
+    T forward sweeps alone (FP32, CUDA events on the solver stream)."""
+    import numpy as np
+
+    out = {"kind": "differentiated form", "workload": WORKLOAD, "T": T, "ckpt_every": ckpt, "dtype": "f32"}
+    with torch.cuda.stream(stream):
+        with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
+            sv.backward(T, ckpt)  # warm-up
+            for key, grads in (("forward_only", False), ("forward_and_gradient", True)):
+                times = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    L, gu, gd = sv.backward(T, ckpt, grads=grads)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                out[key + "_ms"] = sorted(times)[1]
+            out["L"] = L
+            out["grad_u_norm"] = float(np.linalg.norm(gu))
+            out["grad_d_norm"] = float(np.linalg.norm(gd))
+            out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
+    out["gradient_over_forward"] = out["forward_and_gradient_ms"] / out["forward_only_ms"]
+    out["forward_updates_per_s"] = inst.m * inst.K * T / (out["forward_only_ms"] / 1e3)
+    print(json.dumps(out), flush=True)
+
+
 def bench_batch(args, insts, pdr, torch, stream):
     """The batched form against the single-instance form on the same GPU: the
     same instances, the same S sweeps each (Alg. 1 + Alg. 2, FP32), solved
@@ -399,6 +431,9 @@ def main():
         return
     if args.workload == "batch256":
         bench_batch(args, inst, pdr, torch, stream)
+        return
+    if args.adjoint:
+        bench_adjoint(args, inst, pdr, torch, stream)
         return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,

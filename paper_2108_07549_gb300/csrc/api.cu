@@ -609,6 +609,114 @@ std::string validate_instance(int32_t n, int64_t m, const int64_t* row_ptr, cons
     return "";
 }
 
+
+// Reverse mode through T sweeps (pdr_backward), precision T.
+template <typename T>
+pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* grad_u, double* grad_d)
+{
+    const size_t fm = (size_t)ctx->m * ctx->Kp, hn = (size_t)ctx->n * ctx->Kp;
+    const size_t mm = (size_t)(ctx->m > 0 ? ctx->m : 1);
+    const int64_t nseg = Tn > 0 ? (Tn + C - 1) / C : 0;
+    const bool grads = grad_u || grad_d;
+    std::vector<void*> owned;
+    pdr_status st = PDR_OK;
+    auto cleanup = [&]() {
+        for (void* q : owned) cudaFree(q);
+    };
+    auto grab = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        owned.push_back(q);
+        return q;
+    };
+#define CKB(call)                                        \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) {                         \
+            st = ctx->cuda_fail(#call, _e);              \
+            cleanup();                                   \
+            return st;                                   \
+        }                                                \
+    } while (0)
+    // checkpoints of the flows and of the warm-start roots at t = 0, C, 2C, ...
+    std::vector<T*> ck(grads ? nseg : 0), thck(grads ? nseg : 0), seg, th;
+    for (auto& q : ck)
+        if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
+    for (auto& q : thck)
+        if (!(q = (T*)grab(sizeof(T) * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
+    T *fbar = nullptr, *cbar = nullptr, *Dbar = nullptr;
+    double *ubar = nullptr, *dbar = nullptr;
+    if (grads) {
+        seg.resize(C + 1);
+        th.resize(C);
+        for (auto& q : seg)
+            if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
+        for (auto& q : th)
+            if (!(q = (T*)grab(sizeof(T) * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
+        fbar = (T*)grab(sizeof(T) * fm);
+        cbar = (T*)grab(sizeof(T) * fm);
+        Dbar = (T*)grab(sizeof(T) * hn);
+        ubar = (double*)grab(sizeof(double) * mm);
+        dbar = (double*)grab(sizeof(double) * ctx->K);
+        if (!fbar || !cbar || !Dbar || !ubar || !dbar) return cleanup(), ctx->fail(PDR_ERR_OOM, "adjoint allocation failed");
+    }
+    // forward from f = 0 (pdr_backward reset the flows), cold roots
+    T* theta = reinterpret_cast<T*>(ctx->theta);
+    for (int64_t t = 0; t < Tn; ++t) {
+        if (grads && t % C == 0) {
+            CKB(cudaMemcpyAsync(ck[t / C], Prec<T>::f(ctx, ctx->cur), sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
+            CKB(cudaMemcpyAsync(thck[t / C], theta, sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
+        CKB(launch_excess<T>(a, ctx->stream));
+        CKB(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
+        ctx->cur ^= 1;
+    }
+    // L = z(f^(T)) and the seeds
+    {
+        SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
+        CKB(launch_excess<T>(a, ctx->stream));
+        CKB(launch_finalize<T>(a, ctx->stream));
+        if (grads) CKB(launch_seed<T>(a, fbar, ubar, dbar, ctx->num_sms, ctx->stream));
+    }
+    st = read_state(ctx);
+    if (st != PDR_OK) return cleanup(), st;
+    if (L) *L = ctx->hst->z;
+    // backward, segment by segment from the last
+    for (int64_t sgi = nseg - 1; grads && sgi >= 0; --sgi) {
+        const int64_t t0 = sgi * C, t1 = (t0 + C < Tn) ? t0 + C : Tn;
+        CKB(cudaMemcpyAsync(seg[0], ck[sgi], sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
+        CKB(cudaMemcpyAsync(theta, thck[sgi], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int64_t t = t0; t < t1; ++t) {  // recompute f^(t0+1..t1-1), record each sweep's roots
+            SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
+            a.f = seg[t - t0];
+            a.f_out = seg[t - t0 + 1];
+            CKB(launch_excess<T>(a, ctx->stream));
+            CKB(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
+            CKB(cudaMemcpyAsync(th[t - t0], theta, sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
+            a.f = seg[t - t0];
+            CKB(launch_excess<T>(a, ctx->stream));  // h^(t)
+            CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, ctx->num_sms, ctx->stream));
+        }
+    }
+    if (grad_u && ctx->m > 0)
+        CKB(cudaMemcpyAsync(grad_u, ubar, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad_d) CKB(cudaMemcpyAsync(grad_d, dbar, sizeof(double) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+    CKB(cudaStreamSynchronize(ctx->stream));
+#undef CKB
+    cleanup();
+    // f^(T) stays the current flows; partials and state follow it
+    st = refresh_psi<T>(ctx);
+    if (st != PDR_OK) return st;
+    return init_state(ctx, true, 0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -924,6 +1032,71 @@ pdr_status pdr_flows(pdr_ctx* ctx, double* f)
     if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
     return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64[ctx->cur], ctx->m, f)
                          : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
+}
+
+pdr_status pdr_backward(pdr_ctx* ctx, int64_t T, int32_t ckpt_every, double* L, double* grad_u, double* grad_d)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (T < 0 || ckpt_every < 1) return ctx->fail(PDR_ERR_INVALID_ARG, "T must be >= 0 and ckpt_every >= 1");
+    if (ctx->opt.algo != PDR_ALGO_ESO)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "the differentiated form runs Alg. 1 (algo = PDR_ALGO_ESO)");
+    pdr_status s = pdr_reset(ctx);  // f = 0 in the starting precision
+    if (s != PDR_OK) return s;
+    return ctx->cur_prec ? backward_T<double>(ctx, T, ckpt_every, L, grad_u, grad_d)
+                         : backward_T<float>(ctx, T, ckpt_every, L, grad_u, grad_d);
+}
+
+pdr_status pdr_set_data(pdr_ctx* ctx, const double* u, const double* d)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (u)
+        for (int64_t e = 0; e < ctx->m; ++e)
+            if (!std::isfinite(u[e]) || u[e] < 0.0)
+                return ctx->fail(PDR_ERR_INVALID_ARG, "capacity must be finite and >= 0 at edge " + std::to_string(e));
+    if (d)
+        for (int32_t k = 0; k < ctx->K; ++k)
+            if (!std::isfinite(d[k]) || !(d[k] > 0.0))
+                return ctx->fail(PDR_ERR_INVALID_ARG, "demand must be finite and > 0 at k = " + std::to_string(k));
+    if (u && ctx->m > 0) {
+        double usum = 0.0;
+        int64_t upos = 0;
+        for (int64_t e = 0; e < ctx->m; ++e)
+            if (u[e] > 0.0) {
+                usum += u[e];
+                ++upos;
+            }
+        const double ubar = upos ? usum / (double)upos : 1.0;
+        std::vector<double> inv(ctx->m);
+        std::vector<float> uf(ctx->m), invf(ctx->m);
+        for (int64_t e = 0; e < ctx->m; ++e) {
+            inv[e] = 1.0 / (u[e] > ubar ? u[e] : ubar);
+            invf[e] = (float)inv[e];
+            uf[e] = (float)u[e];
+        }
+        CK(cudaMemcpyAsync(ctx->u_d, u, sizeof(double) * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->u_f, uf.data(), sizeof(float) * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->inv_scale, inv.data(), sizeof(double) * ctx->m, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->inv_scale_f, invf.data(), sizeof(float) * ctx->m, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (d) {
+        const int Kp = ctx->Kp;
+        std::vector<double> dp(Kp, 0.0), idd(Kp, 0.0);
+        std::vector<float> dpf(Kp, 0.0f), idf(Kp, 0.0f);
+        for (int k = 0; k < ctx->K; ++k) {
+            dp[k] = d[k];
+            dpf[k] = (float)d[k];
+            idd[k] = 1.0 / d[k];
+            idf[k] = (float)(1.0 / d[k]);
+        }
+        CK(cudaMemcpyAsync(ctx->dem_d, dp.data(), sizeof(double) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->dem_f, dpf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->inv_dem_d, idd.data(), sizeof(double) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->inv_dem_f, idf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return refresh_psi_current(ctx);
 }
 
 pdr_status pdr_flow_rows(pdr_ctx* ctx, int32_t which, const int64_t* edges, int64_t count, double* out)

@@ -150,6 +150,13 @@ cudaError_t build_adjacency(int32_t n, int64_t m, const int64_t* row_ptr, const 
                             int64_t* in_ptr, int32_t* in_eid, int64_t* inc_ptr, int32_t* inc, int32_t* deg,
                             int64_t* work, cudaStream_t stream);
 
+// Reverse mode through unrolled sweeps (adjoint.cu).
+template <typename T>
+cudaError_t launch_seed(const SweepArgs<T>& a, T* fbar, double* ubar, double* dbar, int num_sms, cudaStream_t s);
+template <typename T>
+cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar, T* cbar, T* Dbar, double* ubar,
+                                  double* dbar, int num_sms, cudaStream_t s);
+
 // Residuals and certificate (residuals.cu).
 struct ResidOut {
     double z, cap_abs, cap_rel, cons_abs, cons_rel, f_min, margin, margin_scale;

@@ -34,7 +34,7 @@ EXPORTS = (
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
-    "pdr_batch_destroy",
+    "pdr_batch_destroy", "pdr_set_data", "pdr_backward",
 )
 
 
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH):
         "pdr_batch_context": ([vp, i32, P(vp)], i32),
         "pdr_batch_tuning": ([vp, vp, vp], i32),
         "pdr_batch_destroy": ([vp], None),
+        "pdr_set_data": ([vp, vp, vp], i32),
+        "pdr_backward": ([vp, i64, i32, P(dbl), vp, vp], i32),
         "pdr_set_gd_state": ([vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -286,6 +288,26 @@ class Solver:
         beta = np.ascontiguousarray(beta, dtype=np.float64)
         vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
         self._check(self._lib.pdr_set_gd_state(self._h, _ptr(beta), None if vv is None else _ptr(vv)))
+
+    def set_data(self, u=None, d=None):
+        """Replace the capacities and/or demands (the flows are kept)."""
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        dd = None if d is None else np.ascontiguousarray(d, dtype=np.float64)
+        if uu is not None and uu.shape != (self.m,):
+            raise ValueError("u must have shape (m,)")
+        if dd is not None and dd.shape != (self.K,):
+            raise ValueError("d must have shape (K,)")
+        self._check(self._lib.pdr_set_data(self._h, None if uu is None else _ptr(uu), None if dd is None else _ptr(dd)))
+
+    def backward(self, T: int, ckpt_every: int = 10, grads: bool = True):
+        """(L, dL/du, dL/dd) for L = z(f^(T)) after T sweeps of Alg. 1 from f = 0
+        (gradients None if grads is False)."""
+        L = C.c_double()
+        gu = np.empty(self.m) if grads else None
+        gd = np.empty(self.K) if grads else None
+        self._check(self._lib.pdr_backward(self._h, int(T), int(ckpt_every), C.byref(L),
+                                           None if gu is None else _ptr(gu), None if gd is None else _ptr(gd)))
+        return L.value, gu, gd
 
     def heights(self) -> np.ndarray:
         h = np.empty((self.n, self.K), dtype=np.float64)

@@ -1,0 +1,157 @@
+"""GPU reverse mode (pdr_backward) against the oracle's reverse mode and FP64
+finite differences.
+
+The instances get non-integer capacities and demands so that exact ties (the
+kinks of max(0, .) and of Alg. 2's active sets, which integer data make
+common) are unlikely; where the FP32 forward takes a different branch than
+the FP64 oracle at a near-tie, individual gradient entries can jump, so the
+FP32 comparisons are made on the norm of the error.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_07549_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pdr():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_07549_gb300 import build, pdr as _pdr
+
+    build.build()
+    _pdr.load()
+    return _pdr
+
+
+def jittered(inst, seed):
+    rng = np.random.default_rng(seed)
+    return I.Instance(inst.name + "~", inst.n, inst.row_ptr, inst.col, inst.u * rng.uniform(0.9, 1.1, inst.m),
+                      inst.s, inst.t, inst.d * rng.uniform(0.9, 1.1, inst.K), inst.factor, inst.load, inst.hops)
+
+
+def cases():
+    rng = np.random.default_rng(21)
+    return [jittered(I.grid5_k10(1.0), 1), jittered(I.grid5_k10(0.6), 2),
+            jittered(I.make_instance("dg40_k9", I.random_digraph(40, 3, rng), 9, ("uniform_int", 1, 9), 0.9, rng), 3),
+            jittered(I.make_instance("grid6_k33", I.grid_graph(6), 33, ("lognormal", 1.0, 0.5), 1.1, rng), 4)]
+
+
+@pytest.mark.parametrize("T,ckpt", [(0, 1), (1, 1), (7, 3), (20, 10), (25, 25)])
+def test_fp64_reverse_mode_matches_oracle(pdr, T, ckpt):
+    for inst in cases():
+        Lr, gur, gdr = oracle.Problem.from_instance(inst).adjoint_eso(T)
+        with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64) as s:
+            L, gu, gd = s.backward(T, ckpt)
+        assert abs(L - Lr) <= 1e-12 * Lr
+        np.testing.assert_allclose(gd, gdr, rtol=1e-9, atol=1e-12 * np.abs(gdr).max())
+        np.testing.assert_allclose(gu, gur, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(gur).max()))
+
+
+def test_fp32_reverse_mode_matches_fp64_oracle(pdr):
+    for inst in cases():
+        Lr, gur, gdr = oracle.Problem.from_instance(inst).adjoint_eso(30)
+        with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32) as s:
+            L, gu, gd = s.backward(30, 10)
+        assert abs(L - Lr) <= 1e-5 * Lr
+        g, gr = np.concatenate([gu, gd]), np.concatenate([gur, gdr])
+        assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), (inst.name, np.linalg.norm(g - gr) / np.linalg.norm(gr))
+
+
+def test_euler_identity_on_gpu(pdr):
+    """z(f^(T)) is homogeneous of degree 2 in (u, d): u . dL/du + d . dL/dd = 2 L."""
+    for inst in cases():
+        for prec, tol in ((pdr.PREC_FP64, 1e-10), (pdr.PREC_FP32, 1e-5)):
+            with pdr.Solver.from_instance(inst, precision=prec) as s:
+                L, gu, gd = s.backward(15, 4)
+            assert abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) <= tol * max(1.0, L)
+
+
+def test_backward_leaves_final_flows_and_matches_solve(pdr):
+    inst = cases()[0]
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64, eps_obj=0.0, resid_tol=0.0, max_sweeps=12) as s:
+        L, _, _ = s.backward(12, 5)
+        f_back = s.flows()
+        s.reset()
+        r = s.solve()
+        assert r["sweeps"] == 12 and abs(r["z"] - L) <= 1e-12 * L
+        np.testing.assert_array_equal(s.flows(), f_back)
+
+
+def test_set_data_and_errors(pdr):
+    inst = cases()[2]
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64) as s:
+        L0, _, _ = s.backward(5, 2, grads=False)
+        s.set_data(u=inst.u * 2.0, d=inst.d * 2.0)
+        L1, _, _ = s.backward(5, 2, grads=False)
+        assert abs(L1 - 4.0 * L0) <= 1e-11 * L1  # degree-2 homogeneity again
+        with pytest.raises(pdr.PdrError):
+            s.set_data(u=-inst.u)
+        with pytest.raises(pdr.PdrError):
+            s.backward(-1, 2)
+    with pdr.Solver.from_instance(inst, algo=pdr.ALGO_AGD) as s:
+        with pytest.raises(pdr.PdrError):
+            s.backward(3, 1)
+
+
+def test_torch_autograd_function(pdr):
+    import torch
+
+    from paper_2108_07549_gb300.autograd import unrolled_objective
+
+    inst = cases()[3]
+    Lr, gur, gdr = oracle.Problem.from_instance(inst).adjoint_eso(10)
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64) as s:
+        u = torch.tensor(inst.u, dtype=torch.float64, requires_grad=True)
+        d = torch.tensor(inst.d, dtype=torch.float64, requires_grad=True)
+        L = unrolled_objective(s, u, d, T=10, ckpt_every=3)
+        (3.0 * L).backward()
+    assert abs(float(L.detach()) - Lr) <= 1e-12 * Lr
+    np.testing.assert_allclose(u.grad.numpy(), 3.0 * gur, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(gur).max()))
+    np.testing.assert_allclose(d.grad.numpy(), 3.0 * gdr, rtol=1e-9, atol=1e-12 * np.abs(gdr).max())
+
+
+@pytest.mark.slow
+def test_full_size_fp32_gradient_vs_fp64_finite_differences(pdr):
+    """digraph20k_k2000 (n=20,000, m=100,000, K=2,000), T = 50 sweeps with
+    checkpoints every 10: the FP32 reverse mode against FP64 central
+    differences of the GPU's FP64 forward on sampled capacities and demands."""
+    inst = I.digraph20k_k2000(1.05, seed=0)
+    T = 50
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32) as s32:
+        L32, gu, gd = s32.backward(T, 10)
+    rng = np.random.default_rng(0)
+    edges = rng.choice(np.nonzero(inst.u > 0)[0], 8, replace=False)
+    comms = rng.choice(inst.K, 8, replace=False)
+    checked = 0
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64) as s64:
+        L64, _, _ = s64.backward(T, 10, grads=False)
+        assert abs(L32 - L64) <= 1e-5 * L64
+
+        def L_at(u, d):
+            s64.set_data(u=u, d=d)
+            return s64.backward(T, 10, grads=False)[0]
+
+        for which, idx, g in [("u", e, gu[e]) for e in edges] + [("d", k, gd[k]) for k in comms]:
+            base = inst.u if which == "u" else inst.d
+            h = 1e-4 * base[idx]
+            vals = []
+            for q in (-1, 0, 1):
+                x = base.copy()
+                x[idx] += q * h
+                vals.append(L_at(x, inst.d) if which == "u" else L_at(inst.u, x))
+            left, right = (vals[1] - vals[0]) / h, (vals[2] - vals[1]) / h
+            central = (vals[2] - vals[0]) / (2 * h)
+            scale = max(abs(central), 1e-3 * abs(L64) / base[idx])
+            if abs(right - left) > 1e-3 * max(abs(left), abs(right), 1e-12):
+                continue  # a kink inside the stencil
+            assert abs(g - central) <= 1e-3 * scale, (which, idx, g, central)
+            checked += 1
+        s64.set_data(u=inst.u, d=inst.d)
+    assert checked >= 12
