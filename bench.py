@@ -71,6 +71,10 @@ def parse():
                     help="time the differentiated form (T = 50 sweeps, checkpoints every 10) on the workload")
     ap.add_argument("--compare-algos", action="store_true",
                     help="time Alg. 1, Alg. 3 and Alg. 4 on the workload and print one comparison line")
+    ap.add_argument("--edge-variant", type=int, default=-1,
+                    help="edge-kernel variant (index of the library's variant table; -1 = the library's choice)")
+    ap.add_argument("--compare-variants", action="store_true",
+                    help="time every edge-kernel variant that holds the rows (Alg. 1) and print one JSON line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -295,6 +299,42 @@ def compare_algos(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+def compare_variants(args, inst, pdr, torch, stream):
+    """Alg. 1 with each edge-kernel variant that holds the rows: time per
+    sweep inside the graph loop (CUDA events around a fixed number of sweeps
+    from f = 0) and the edge kernel alone with a cold L2."""
+    peak, peak_src = load_peaks()
+    out = {"kind": "edge-kernel variant comparison", "workload": WORKLOAD, "sweeps": args.sweeps, "dtype": "f32",
+           "peak_gbs": peak, "peak_source": peak_src, "variants": {}}
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    b_up = update_bytes("eso", inst)
+    for v, cap, pipe in pdr.edge_variants(pdr.PREC_FP32):
+        if cap < inst.K:
+            continue
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
+                                          resid_tol=0.0, max_sweeps=args.sweeps, edge_variant=v) as sv:
+                sv.solve()
+                times = []
+                for q in range(3):
+                    sv.reset()
+                    flush.fill_(q & 0xFF)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = sv.solve()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = sorted(times)[1]
+                t_up = sv.time_kernel("qp", 10, FLUSH_BYTES)
+        out["variants"][str(v)] = {
+            "capacity": cap, "pipelined": pipe, "us_per_sweep": ms / args.sweeps * 1e3,
+            "updates_per_s": inst.m * inst.K * args.sweeps / (ms / 1e3), "z_after": r["z"],
+            "qp_kernel_us_cold": t_up * 1e3, "qp_frac": b_up / (t_up / 1e3) / 1e9 / peak,
+        }
+    print(json.dumps(out), flush=True)
+
+
 def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
     """The differentiated form: L = z(f^(T)) and its gradient w.r.t. u and d
     by reverse mode through T sweeps with checkpoints every ckpt, against the
@@ -422,12 +462,15 @@ def main():
     if args.profile_sweeps > 0:
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32,
-                                          algo=ALGOS[args.algo]) as sv:
+                                          algo=ALGOS[args.algo], edge_variant=args.edge_variant) as sv:
                 sv.sweeps(args.profile_sweeps)
         torch.cuda.synchronize()
         return
     if args.compare_algos:
         compare_algos(args, inst, pdr, torch, stream)
+        return
+    if args.compare_variants:
+        compare_variants(args, inst, pdr, torch, stream)
         return
     if args.workload == "batch256":
         bench_batch(args, inst, pdr, torch, stream)
@@ -437,7 +480,7 @@ def main():
         return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
-                use_graph=0 if args.host_loop else 1, algo=ALGOS[args.algo])
+                use_graph=0 if args.host_loop else 1, algo=ALGOS[args.algo], edge_variant=args.edge_variant)
     m, K = inst.m, inst.K
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -546,7 +589,7 @@ def main():
             return
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
-                                          resid_tol=1e-6, max_sweeps=1000000) as sv:
+                                          resid_tol=1e-6, max_sweeps=1000000, edge_variant=args.edge_variant) as sv:
                 rr = sv.solve()
         line["time_to_eps"] = {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"],
                                "ms": rr["ms_total"], "z": rr["z"], "cap_rel": rr["cap_rel"],

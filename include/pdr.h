@@ -100,6 +100,13 @@ typedef struct {
      * 0.25, beta_max 0.5; GDM beta_init 0.1, beta_max 0.2, gamma 0.9; both
      * beta_min 1/K, alpha_inc 2, alpha_dec 0.5.  Ignored by PDR_ALGO_ESO. */
     double beta_init, beta_min, beta_max, alpha_inc, alpha_dec, gamma;
+    /* Kernel variant of the edge update (a tuning choice; every variant
+     * computes the same step).  -1 (default): the library's choice for K.
+     * 0..pdr_num_edge_variants()-1: that entry of the variant table (the
+     * numbering pdr_batch_tuning reports); its row capacity
+     * (pdr_edge_variant_capacity) must hold K in every precision the solve
+     * uses, else PDR_ERR_INVALID_ARG. */
+    int32_t edge_variant;
 } pdr_options;
 
 typedef struct {
@@ -240,6 +247,15 @@ pdr_status pdr_sizes(const pdr_ctx *ctx, int32_t *n, int64_t *m, int32_t *K, int
  * heights).  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
 pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_t flush_bytes, double *ms);
 
+/* Number of entries in the edge-kernel variant table (pdr_options.edge_variant). */
+int32_t pdr_num_edge_variants(void);
+
+/* Row capacity of variant v: the largest K it holds in `precision`
+ * (PDR_PREC_FP32 or PDR_PREC_FP64).  *pipelined (may be NULL) receives 1 for
+ * the persistent pipelined forms of Alg. 2, which Alg. 3/4 run in their plain
+ * form.  Returns -1 if v or precision is out of range (nothing written). */
+int32_t pdr_edge_variant_capacity(int32_t v, int32_t precision, int32_t *pipelined);
+
 /* In-adjacency and degrees of a graph that already lives in device memory,
  * computed without allocating any memory.  The paper has no counterpart:
  * this is a deployment entry point, not a step of the method.
@@ -315,7 +331,8 @@ typedef struct {
  * with the options opt shared by all).  Every instance gets its own context
  * on `stream`; an autotuner then times the edge-kernel variants that fit each
  * instance's row length (lanes per edge, vectors per lane, block size) on
- * that instance and keeps the fastest.  Errors: PDR_ERR_INVALID_ARG (count <
+ * that instance and keeps the fastest; opt->edge_variant >= 0 fixes the
+ * variant for every instance instead.  Errors: PDR_ERR_INVALID_ARG (count <
  * 1, NULL, or an instance rejected by pdr_create: the message names it),
  * PDR_ERR_OOM, PDR_ERR_CUDA, PDR_ERR_UNSUPPORTED. */
 pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_options *opt, void *stream,

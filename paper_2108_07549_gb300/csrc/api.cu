@@ -43,6 +43,7 @@ void fill_defaults(pdr_options* o)
     o->algo = PDR_ALGO_ESO;
     o->beta_init = o->beta_min = o->beta_max = o->alpha_inc = o->alpha_dec = 0.0;
     o->gamma = -1.0;
+    o->edge_variant = -1;
 }
 
 bool options_ok(const pdr_options* o, std::string* why)
@@ -75,6 +76,10 @@ bool options_ok(const pdr_options* o, std::string* why)
         }
     if (o->gamma >= 1.0) {
         *why = "gamma must be < 1";
+        return false;
+    }
+    if (o->edge_variant < -1 || o->edge_variant >= num_edge_configs()) {
+        *why = "edge_variant must be -1 or an index of the variant table";
         return false;
     }
     return true;
@@ -398,6 +403,37 @@ pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr)
 pdr_status refresh_psi_current(pdr_ctx* ctx)
 {
     return ctx->cur_prec ? refresh_psi<double>(ctx) : refresh_psi<float>(ctx);
+}
+
+// The edge-kernel variant of each precision: the caller's (it must hold the
+// rows in every precision the solve uses) or the library's choice.  Sets
+// cfg, grid_e and n_psi; cfg = -1 for a precision whose rows no variant holds.
+pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
+{
+    const int Kp = ctx->Kp;
+    int c32, c64;
+    if (o.edge_variant >= 0) {
+        c32 = c64 = o.edge_variant;
+        const bool need32 = o.precision != PDR_PREC_FP64, need64 = o.precision != PDR_PREC_FP32;
+        if ((need32 && edge_capacity<float>(c32) < Kp) || (need64 && edge_capacity<double>(c64) < Kp))
+            return ctx->fail(PDR_ERR_INVALID_ARG, "edge_variant " + std::to_string(o.edge_variant) +
+                                                      " does not hold rows of K = " + std::to_string(ctx->K));
+        if (edge_capacity<float>(c32) < Kp) c32 = edge_config<float>(Kp);
+        if (edge_capacity<double>(c64) < Kp) c64 = edge_config<double>(Kp);
+    } else {
+        c32 = edge_config<float>(Kp);
+        c64 = edge_config<double>(Kp);
+    }
+    if (c32 < 0 || (o.precision != PDR_PREC_FP32 && c64 < 0))
+        return ctx->fail(PDR_ERR_UNSUPPORTED,
+                         "K = " + std::to_string(ctx->K) + " exceeds the largest edge-kernel row supported by this build");
+    ctx->cfg[0] = c32;
+    ctx->cfg[1] = c64;
+    ctx->grid_e[0] = edge_grid<float>(c32, ctx->m, ctx->num_sms);
+    ctx->grid_e[1] = c64 >= 0 ? edge_grid<double>(c64, ctx->m, ctx->num_sms) : 1;
+    ctx->n_psi[0] = edge_parts<float>(c32, ctx->grid_e[0]);
+    ctx->n_psi[1] = c64 >= 0 ? edge_parts<double>(c64, ctx->grid_e[1]) : 1;
+    return PDR_OK;
 }
 
 __global__ void set_state_kernel(DevState* st, DevState v) { *st = v; }
@@ -795,19 +831,12 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     CKC(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
 
     const int Kp = ctx->Kp;
-    const int cfg32 = edge_config<float>(Kp), cfg64 = edge_config<double>(Kp);
-    if (cfg32 < 0 || (o.precision != PDR_PREC_FP32 && cfg64 < 0)) {
-        ctx->err = "K = " + std::to_string(K) + " exceeds the largest edge-kernel row supported by this build";
-        return give_up(PDR_ERR_UNSUPPORTED);
+    {
+        const pdr_status vs = select_edge_variants(ctx, o);
+        if (vs != PDR_OK) return give_up(vs);
     }
-    ctx->cfg[0] = cfg32;
-    ctx->cfg[1] = cfg64;
     ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms, excess_resident_blocks<float>());
     ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms, excess_resident_blocks<double>());
-    ctx->grid_e[0] = edge_grid<float>(cfg32, m, ctx->num_sms);
-    ctx->grid_e[1] = cfg64 >= 0 ? edge_grid<double>(cfg64, m, ctx->num_sms) : 1;
-    ctx->n_psi[0] = edge_parts<float>(cfg32, ctx->grid_e[0]);
-    ctx->n_psi[1] = cfg64 >= 0 ? edge_parts<double>(cfg64, ctx->grid_e[1]) : 1;
     ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms, 8);
     {
         int64_t we = (m * 32 + 255) / 256;
@@ -950,8 +979,13 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
     if (opt) o = *opt;
     std::string why;
     if (!options_ok(&o, &why)) return ctx->fail(PDR_ERR_INVALID_ARG, why);
-    if (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0)
-        return ctx->fail(PDR_ERR_UNSUPPORTED, "K exceeds the largest FP64 edge-kernel row supported by this build");
+    const bool variant_changed = o.edge_variant != ctx->opt.edge_variant ||
+                                 (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0);
+    if (variant_changed) {
+        const pdr_status vs = select_edge_variants(ctx, o);  // writes nothing on failure
+        if (vs != PDR_OK) return vs;
+        destroy_graphs(ctx);  // the graphs captured the old launch shapes
+    }
     if (o.trace_len != ctx->trace_cap) {
         if (ctx->trace) cudaFree(ctx->trace);
         pdr_status st = PDR_OK;
@@ -984,8 +1018,11 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
         // a new algorithm or new rates: learning rates and velocities restart, the flows stay
         pdr_status s = flows_to_buffer0_current(ctx);
         if (s != PDR_OK) return s;
-        return init_gd_state_current(ctx);
+        s = init_gd_state_current(ctx);
+        if (s != PDR_OK) return s;
     }
+    // a new variant writes its congestion partials in another layout
+    if (variant_changed) return refresh_psi_current(ctx);
     return PDR_OK;
 }
 
@@ -1374,6 +1411,15 @@ pdr_status pdr_sizes(const pdr_ctx* ctx, int32_t* n, int64_t* m, int32_t* K, int
     return PDR_OK;
 }
 
+int32_t pdr_num_edge_variants(void) { return num_edge_configs(); }
+
+int32_t pdr_edge_variant_capacity(int32_t v, int32_t precision, int32_t* pipelined)
+{
+    if (v < 0 || v >= num_edge_configs() || (precision != PDR_PREC_FP32 && precision != PDR_PREC_FP64)) return -1;
+    if (pipelined) *pipelined = edge_config_pipelined(v) ? 1 : 0;
+    return precision == PDR_PREC_FP32 ? edge_capacity<float>(v) : edge_capacity<double>(v);
+}
+
 pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_t flush_bytes, double* ms)
 {
     if (!ctx || !ms) return PDR_ERR_INVALID_ARG;
@@ -1468,15 +1514,24 @@ pdr_status batch_fail(pdr_status code, const std::string& msg)
 }
 
 // Times the edge-kernel variants that hold this instance's rows (the
-// smallest three by capacity) and keeps the fastest.  Launches read the
+// smallest three plain forms by capacity and, for Alg. 2, the smallest
+// pipelined form) and keeps the fastest.  Launches read the
 // current flows and write the other buffer, so the state is unchanged.
 template <typename T>
 pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
 {
     const int p = Prec<T>::id;
     std::vector<int> cand;
-    for (int c = 0; c < num_edge_configs() && (int)cand.size() < 3; ++c)
-        if (edge_capacity<T>(c) >= ctx->Kp) cand.push_back(c);
+    bool pipe = false;
+    for (int c = 0; c < num_edge_configs(); ++c) {
+        if (edge_capacity<T>(c) < ctx->Kp) continue;
+        if (edge_config_pipelined(c)) {
+            if (!pipe && ctx->opt.algo == PDR_ALGO_ESO) cand.push_back(c);
+            pipe = true;
+        } else if ((int)cand.size() < 3) {
+            cand.push_back(c);
+        }
+    }
     *best_cfg = ctx->cfg[p];
     *best_us = -1.0;
     if (ctx->m == 0 || cand.size() <= 1) return PDR_OK;
@@ -1709,6 +1764,10 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance* inst, const pdr_o
     b->tuned_us.assign(count, -1.0);
     for (int32_t i = 0; i < count; ++i) {
         pdr_ctx* c = b->ctx[i];
+        if (o.edge_variant >= 0) {  // the caller's variant: no tuning
+            b->tuned_cfg[i] = c->cfg[c->cur_prec];
+            continue;
+        }
         pdr_status s = c->cur_prec ? autotune<double>(c, &b->tuned_cfg[i], &b->tuned_us[i])
                                    : autotune<float>(c, &b->tuned_cfg[i], &b->tuned_us[i]);
         if (s != PDR_OK) return give_up(s, "instance " + std::to_string(i) + ": " + c->err);

@@ -279,12 +279,14 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) gd_block_kernel(SweepAr
 
 }  // namespace
 
-// Same variant table as the edge-QP kernels (sweep.cu: kCfg).
+// Same variant table as the edge-QP kernels (sweep.cu: kCfg); a pipelined
+// variant runs the plain form of the same capacity (the kernels stride over
+// the edges, so any grid works).
 template <typename T>
 cudaError_t launch_gd(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
 {
     const int g = a.grid_e + 1;
-    switch (cfg) {
+    switch (edge_plain_config(cfg)) {
     case 0: gd_group_kernel<T, 4, 1><<<g, kThreads, 0, stream>>>(a); break;
     case 1: gd_group_kernel<T, 8, 1><<<g, kThreads, 0, stream>>>(a); break;
     case 2: gd_group_kernel<T, 16, 1><<<g, kThreads, 0, stream>>>(a); break;

@@ -134,6 +134,8 @@ int64_t edge_parts(int cfg, int grid);  // number of partials that grid writes
 template <typename T>
 int edge_capacity(int cfg);             // elements per row a variant holds (-1 if none)
 int num_edge_configs();
+int edge_plain_config(int cfg);          // the non-pipelined variant of the same capacity
+bool edge_config_pipelined(int cfg);
 int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
 template <typename T>
 int excess_resident_blocks();  // excess blocks resident per SM (occupancy)

@@ -309,6 +309,155 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
     }
 }
 
+// ------------------------------------------------------------------ edge QP, pipelined lane-group form
+
+// Persistent form of edge_group_kernel for one 32-lane group per edge: each
+// warp walks a fixed stride of edges and loads the next edge's three rows
+// into registers before it solves the current one, so the loads of edge
+// e + stride are in flight during the active-set search of edge e.
+template <typename T, int V>
+__device__ __forceinline__ void pipe_load(const SweepArgs<T>& a, int64_t e, int gl, int vpr,
+                                          typename VecOf<T>::type (&fv)[V], typename VecOf<T>::type (&av)[V],
+                                          typename VecOf<T>::type (&bv)[V])
+{
+    using VT = typename VecOf<T>::type;
+    const bool valid = e < a.m;
+    const VT* frow = reinterpret_cast<const VT*>(a.f + (valid ? e : 0) * a.Kp);
+    const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)(valid ? a.src[e] : 0) * a.Kp);
+    const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)(valid ? a.col[e] : 0) * a.Kp);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        const int v = gl + q * 32;
+        if (valid && v < vpr) {
+            fv[q] = frow[v];
+            av[q] = __ldg(hi + v);
+            bv[q] = __ldg(hj + v);
+        }
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
+{
+    using VT = typename VecOf<T>::type;
+    using A = Acc<T>;
+    constexpr int N = VecOf<T>::N;
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) return;
+    if (blockIdx.x == gridDim.x - 1) {
+        if (a.mode != MODE_PSI) reduce_and_finalize(a);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)(gridDim.x - 1) * blockDim.x) >> 5;
+    const int vpr = a.Kp / N;
+    const bool psi_only = (a.mode == MODE_PSI);
+    typename A::V zpsi = A::zero();
+    T capmax = T(0);
+    VT fv[V], av[V], bv[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) fv[q] = av[q] = bv[q] = VT{};
+    pipe_load<T, V>(a, warp, lane, vpr, fv, av, bv);
+    for (int64_t e = warp; e < a.m; e += nwarps) {
+        // rows of this edge into c, then start the next edge's loads
+        T c[V][N];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            T fx[N], ax[N], bx[N];
+            unpack(fv[q], fx);
+            unpack(av[q], ax);
+            unpack(bv[q], bx);
+#pragma unroll
+            for (int j = 0; j < N; ++j) c[q][j] = psi_only ? fx[j] : fma(T(0.5), ax[j] - bx[j], fx[j]);
+        }
+        const T ue = a.u[e];
+        const int64_t en = e + nwarps;
+#pragma unroll
+        for (int q = 0; q < V; ++q) fv[q] = av[q] = bv[q] = VT{};
+        if (en < a.m) pipe_load<T, V>(a, en, lane, vpr, fv, av, bv);
+        T theta = T(0);
+        if (!psi_only) {
+            const T w = a.theta[e] * T(0.999);
+            T sp = T(0), sw = T(0);
+            int np = 0, nw = 0;
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j];
+                    if (x > T(0)) {
+                        sp += x;
+                        ++np;
+                    }
+                    if (x > w) {
+                        sw += x;
+                        ++nw;
+                    }
+                }
+            const T s = group_sum<32>(sp);
+            const int n0 = group_sum<32>(np);
+            const T S_w = group_sum<32>(sw);
+            const int n_w = group_sum<32>(nw);
+            if (s > ue) {  // warp-uniform
+                int nA = n0;
+                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
+                    nA = n_w;
+                    theta = (S_w - ue) / T(2 + n_w);
+                } else {
+                    theta = (s - ue) / T(2 + n0);
+                }
+                for (int it = 0; it <= a.Kp + 2; ++it) {
+                    T sa = T(0);
+                    int na = 0;
+#pragma unroll
+                    for (int q = 0; q < V; ++q)
+#pragma unroll
+                        for (int j = 0; j < N; ++j)
+                            if (c[q][j] > theta) {
+                                sa += c[q][j];
+                                ++na;
+                            }
+                    const T S2 = group_sum<32>(sa);
+                    const int n2 = group_sum<32>(na);
+                    if (n2 >= nA) break;
+                    nA = n2;
+                    theta = (S2 - ue) / T(2 + n2);
+                }
+            }
+            if (lane == 0) a.theta[e] = theta;
+        }
+        T rs = T(0);
+        T* orow = a.f_out + e * a.Kp;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = lane + q * 32;
+            T o[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T x = c[q][j] - theta;
+                o[j] = x > T(0) ? x : T(0);
+                rs += o[j];
+            }
+            if (!psi_only && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
+        }
+        rs = group_sum<32>(rs);
+        if (lane == 0) {
+            const T over = rs - ue;
+            const T psi = over > T(0) ? over : T(0);
+            zpsi = A::add(zpsi, psi * psi);
+            const T cc = psi * a.inv_scale_t[e];
+            capmax = cc > capmax ? cc : capmax;
+            if (a.psi_out) a.psi_out[e] = psi;
+        }
+    }
+    warp_acc_max<T>(zpsi, capmax);
+    if (lane == 0) {
+        reinterpret_cast<typename A::S*>(a.part_psi)[warp] = A::store(zpsi);
+        a.part_cap[warp] = capmax;
+    }
+}
+
 // ------------------------------------------------------------------ edge QP, block form (large K)
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
@@ -449,12 +598,18 @@ struct EdgeCfg {
     int G;        // lanes per edge (0 = block form)
     int B;        // block size of the block form
     int V;        // vectors per lane
+    int P;        // 1 = pipelined persistent warp form (Alg. 2 only)
 };
 constexpr EdgeCfg kCfg[] = {
-    // ordered by capacity (elements per row); two 512-thread blocks fit on an
-    // SM, so the block forms keep two edges in flight per SM up to 16,384
-    {4, 0, 1},   {8, 0, 1},   {16, 0, 1},  {32, 0, 1},  {32, 0, 2},  {32, 0, 4},  {32, 0, 8},
-    {0, 256, 2}, {0, 512, 2}, {0, 512, 3}, {0, 512, 4}, {0, 512, 5}, {0, 512, 8}, {0, 1024, 8},
+    // 0..13 ordered by capacity (elements per row); two 512-thread blocks fit
+    // on an SM, so the block forms keep two edges in flight per SM up to 16,384
+    {4, 0, 1, 0},   {8, 0, 1, 0},   {16, 0, 1, 0},  {32, 0, 1, 0},  {32, 0, 2, 0},
+    {32, 0, 4, 0},  {32, 0, 8, 0},  {0, 256, 2, 0}, {0, 512, 2, 0}, {0, 512, 3, 0},
+    {0, 512, 4, 0}, {0, 512, 5, 0}, {0, 512, 8, 0}, {0, 1024, 8, 0},
+    // 14..16: the pipelined forms of 3..5 (the gradient kernels of Alg. 3/4
+    // run the plain form of the same capacity); at 8 vectors per lane the
+    // prefetched rows no longer fit in registers
+    {32, 0, 1, 1},  {32, 0, 2, 1},  {32, 0, 4, 1},
 };
 constexpr int kNumCfg = sizeof(kCfg) / sizeof(kCfg[0]);
 
@@ -471,8 +626,20 @@ template <typename T>
 int edge_config(int Kp)
 {
     for (int i = 0; i < kNumCfg; ++i)
-        if (capacity<T>(i) >= Kp) return i;
+        if (!kCfg[i].P && capacity<T>(i) >= Kp) return i;
     return -1;
+}
+
+template <typename T, int V>
+int pipe_resident()
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, edge_pipe_kernel<T, V>, kThreads, 0) != cudaSuccess ||
+        blocks < 1) {
+        cudaGetLastError();
+        return 2;
+    }
+    return blocks;
 }
 
 template <typename T>
@@ -480,7 +647,15 @@ int edge_grid(int cfg, int64_t m, int num_sms)
 {
     const EdgeCfg& c = kCfg[cfg];
     int64_t want, cap;
-    (void)num_sms;
+    if (c.P) {
+        // one wave of resident warps, each walking a stride of edges
+        const int per_sm = c.V == 1 ? pipe_resident<T, 1>() : c.V == 2 ? pipe_resident<T, 2>() : pipe_resident<T, 4>();
+        const int64_t per_block = kThreads / 32;
+        want = (m + per_block - 1) / per_block;
+        cap = (int64_t)num_sms * per_sm;
+        const int64_t g = want < cap ? want : cap;
+        return (int)(g < 1 ? 1 : g);
+    }
     if (c.G) {
         const int64_t per_block = kThreads / c.G;
         want = (m + per_block - 1) / per_block;
@@ -563,10 +738,17 @@ cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
     case 11: edge_block_kernel<T, 512, 5><<<g, 512, 0, stream>>>(a); break;
     case 12: edge_block_kernel<T, 512, 8><<<g, 512, 0, stream>>>(a); break;
     case 13: edge_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
+    case 14: edge_pipe_kernel<T, 1><<<g, kThreads, 0, stream>>>(a); break;
+    case 15: edge_pipe_kernel<T, 2><<<g, kThreads, 0, stream>>>(a); break;
+    case 16: edge_pipe_kernel<T, 4><<<g, kThreads, 0, stream>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
+
+int edge_plain_config(int cfg) { return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P) ? 3 + (cfg - 14) : cfg; }
+
+bool edge_config_pipelined(int cfg) { return cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P; }
 
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream)
 {

@@ -34,7 +34,7 @@ EXPORTS = (
     "pdr_residuals", "pdr_trace", "pdr_sizes", "pdr_time_kernel", "pdr_last_error", "pdr_destroy",
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
-    "pdr_batch_destroy", "pdr_set_data", "pdr_backward",
+    "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
 )
 
 
@@ -51,7 +51,7 @@ class Options(C.Structure):
         ("precision", C.c_int32), ("use_graph", C.c_int32), ("eps_obj", C.c_double), ("resid_tol", C.c_double),
         ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("algo", C.c_int32),
         ("beta_init", C.c_double), ("beta_min", C.c_double), ("beta_max", C.c_double), ("alpha_inc", C.c_double),
-        ("alpha_dec", C.c_double), ("gamma", C.c_double),
+        ("alpha_dec", C.c_double), ("gamma", C.c_double), ("edge_variant", C.c_int32),
     ]
 
 
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
         "pdr_trace": ([vp, vp, i64, P(i64)], i32),
         "pdr_sizes": ([vp, P(i32), P(i64), P(i32), P(i32)], i32),
         "pdr_time_kernel": ([vp, i32, i32, i64, P(dbl)], i32),
+        "pdr_num_edge_variants": ([], i32),
+        "pdr_edge_variant_capacity": ([i32, i32, P(i32)], i32),
         "pdr_last_error": ([vp], C.c_char_p),
         "pdr_destroy": ([vp], None),
         "pdr_adjacency_static": ([i32, i64, vp, vp, vp, vp, vp, vp], i32),
@@ -153,6 +155,17 @@ def _current_stream():
     except ImportError:
         pass
     return None
+
+
+def edge_variants(precision: int = 0) -> list:
+    """The edge-kernel variant table: (index, row capacity in `precision`, pipelined) per entry."""
+    lib = load()
+    out = []
+    for v in range(lib.pdr_num_edge_variants()):
+        pipe = C.c_int32(0)
+        cap = lib.pdr_edge_variant_capacity(v, precision, C.byref(pipe))
+        out.append((v, cap, bool(pipe.value)))
+    return out
 
 
 def adjacency_static(n, m, row_ptr, col, in_ptr, in_eid, deg, stream=None):

@@ -43,6 +43,7 @@ def test_default_options(lib):
     assert o.eps_obj == 1e-6 and o.resid_tol == 1e-6 and o.eps_rel == 0.0
     assert o.max_sweeps == 1000000 and o.trace_len == 0
     assert o.algo == pdr.ALGO_ESO and o.beta_init == 0.0 and o.gamma == -1.0
+    assert o.edge_variant == -1
     assert lib.pdr_default_options(None) == 1
 
 
@@ -97,6 +98,29 @@ def test_create_rejects_bad_options(lib):
     o = pdr.default_options(algo=2, gamma=1.5)
     st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
     assert st == 1 and "gamma" in msg
+    for v in (-2, lib.pdr_num_edge_variants()):
+        o = pdr.default_options(edge_variant=v)
+        st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
+        assert st == 1 and "edge_variant" in msg
+
+
+def test_edge_variant_table(lib):
+    """Every variant holds a whole number of vectors per lane (4 floats or 2
+    doubles), the plain forms come in ascending capacity, and each pipelined
+    form has a plain form of the same capacity."""
+    from paper_2108_07549_gb300 import pdr
+
+    t32, t64 = pdr.edge_variants(pdr.PREC_FP32), pdr.edge_variants(pdr.PREC_FP64)
+    assert len(t32) == lib.pdr_num_edge_variants() >= 14
+    plain = [c for _, c, p in t32 if not p]
+    assert plain == sorted(plain) and plain[0] == 16 and plain[-1] == 32768
+    for (v, c32, p32), (_, c64, p64) in zip(t32, t64):
+        assert c32 == 2 * c64 and c32 % 16 == 0 and p32 == p64
+        if p32:
+            assert c32 in plain
+    pipe = C.c_int32(7)
+    assert lib.pdr_edge_variant_capacity(-1, 0, C.byref(pipe)) == -1 and pipe.value == 7
+    assert lib.pdr_edge_variant_capacity(0, 2, None) == -1
 
 
 def test_null_context_calls_fail_cleanly(lib):
