@@ -149,6 +149,107 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     }
 }
 
+// ------------------------------------------------------------------ the root search of Alg. 2
+//
+// Every pass over a row returns three group-wide values for a threshold w:
+// S(w) = sum of the c_k > w, n(w) = their number and m(w) = the smallest of
+// them.  theta = (S(w) - u)/(2 + n(w)) is the root of the active set
+// A = {c > w}; if m(w) > theta, no element of A falls at or below theta, so A
+// is the active set of its own root and the search ends without another
+// pass.  Otherwise the elements c <= theta leave (Michelot's step) and the
+// next pass starts at theta.  In a converged solve the warm start w lies just
+// below the root with no element in between, so one pass decides the edge.
+
+template <int G, typename X>
+__device__ __forceinline__ X group_min(X x)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const X y = __shfl_xor_sync(kFull, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+template <typename T, int G, int V, int N>
+__device__ __forceinline__ void above(const T (&c)[V][N], T w, T& S, int& n, T& mn)
+{
+    T sl = T(0), ml = T(INFINITY);
+    int nl = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T x = c[q][j];
+            if (x > w) {
+                sl += x;
+                ++nl;
+                ml = x < ml ? x : ml;
+            }
+        }
+    S = group_sum<G>(sl);
+    n = group_sum<G>(nl);
+    mn = group_min<G>(ml);
+}
+
+// Case decision and root from the sums above a threshold w >= 0 that is known
+// to lie at or below the root (w = 0, or g(w) >= 0 certified).
+template <typename T>
+__device__ __forceinline__ void start_root(T S, int n, T mn, T ue, T& theta, int& nA, bool& done)
+{
+    if (S <= ue) {  // Case 1 of Alg. 2: nothing to shed
+        theta = T(0);
+        done = true;
+    } else {  // Case 2
+        theta = (S - ue) / T(2 + n);
+        nA = n;
+        done = mn > theta;
+    }
+}
+
+// theta = psi'/2 for the row c (all lanes of the warp call it; `valid` is
+// uniform over the lane group).  w0 is the warm start (>= 0).
+template <typename T, int G, int V, int N>
+__device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool valid, int Kp)
+{
+    T S, mn, theta = T(0);
+    int n, nA = 0;
+    bool done = !valid, cold = false;
+    above<T, G, V, N>(c, w0, S, n, mn);
+    if (valid) {
+        if (w0 <= T(0)) start_root(S, n, mn, ue, theta, nA, done);
+        else if (S - T(n) * w0 - ue - T(2) * w0 >= T(0)) {
+            // g(w0) = sum max(0, c - w0) - u - 2 w0 >= 0: w0 <= root, Case 2
+            theta = (S - ue) / T(2 + n);
+            nA = n;
+            done = mn > theta;
+        } else {
+            cold = true;  // the root dropped below the warm start
+        }
+    }
+    if (__any_sync(kFull, cold)) {
+        T S0, m0;
+        int n0;
+        above<T, G, V, N>(c, T(0), S0, n0, m0);
+        if (cold) start_root(S0, n0, m0, ue, theta, nA, done);
+    }
+    for (int it = 0; __any_sync(kFull, !done); ++it) {
+        T S2, m2;
+        int n2;
+        above<T, G, V, N>(c, theta, S2, n2, m2);
+        if (!done) {
+            if (n2 >= nA || n2 == 0) done = true;  // no element left (rounding only): keep theta
+            else {
+                nA = n2;
+                theta = (S2 - ue) / T(2 + n2);
+                done = m2 > theta;
+            }
+        }
+        if (it > Kp + 2) break;  // unreachable: nA drops every round
+    }
+    return theta;
+}
+
 // ------------------------------------------------------------------ edge QP, lane-group form
 
 // One aligned group of G lanes per edge; each lane keeps V vectors of the
@@ -214,87 +315,37 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
                 }
             }
         }
-        T theta = T(0);
+        T psi;
         if (!psi_only) {
-            // One pass gives s = sum_k max(0, c_k), |{c_k > 0}|, and the same
-            // two sums above a warm start w slightly below the previous
-            // sweep's root.  g(theta) = sum_k max(0, c_k - theta) - u - 2 theta
-            // decreases in theta and vanishes at the root, so g(w) >= 0
-            // certifies w <= root and the active set lies inside {c > w}.
+            // warm start slightly below the previous sweep's root
             const T w = valid ? a.theta[e] * T(0.999) : T(0);
-            T sp = T(0), sw = T(0);
-            int np = 0, nw = 0;
+            const T theta = qp_root_group<T, G, V, N>(c, ue, w, valid, a.Kp);
+            if (valid && gl == 0) a.theta[e] = theta;
+            // f' = max(0, c - theta); at the root sum f' - u = 2 theta, so the
+            // congestion of the new flows is psi' = 2 theta (0 in Case 1)
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = gl + q * G;
+                T o[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j] - theta;
+                    o[j] = x > T(0) ? x : T(0);
+                }
+                if (valid && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
+            }
+            psi = T(2) * theta;
+        } else {
+            // congestion of the stored flows
+            T rs = T(0);
 #pragma unroll
             for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    const T x = c[q][j];
-                    if (x > T(0)) {
-                        sp += x;
-                        ++np;
-                    }
-                    if (x > w) {
-                        sw += x;
-                        ++nw;
-                    }
-                }
-            const T s = group_sum<G>(sp);
-            const int n0 = group_sum<G>(np);
-            const T S_w = group_sum<G>(sw);
-            const int n_w = group_sum<G>(nw);
-            const bool congested = valid && s > ue;  // Case 2 of Alg. 2 (s <= u is Case 1)
-            bool done = !congested;
-            int nA = n0;
-            if (congested) {
-                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
-                    nA = n_w;
-                    theta = (S_w - ue) / T(2 + n_w);
-                } else {
-                    theta = (s - ue) / T(2 + n0);
-                }
-            }
-            for (int it = 0; __any_sync(kFull, !done); ++it) {
-                T sa = T(0);
-                int na = 0;
-#pragma unroll
-                for (int q = 0; q < V; ++q)
-#pragma unroll
-                    for (int j = 0; j < N; ++j)
-                        if (c[q][j] > theta) {
-                            sa += c[q][j];
-                            ++na;
-                        }
-                const T S2 = group_sum<G>(sa);
-                const int n2 = group_sum<G>(na);
-                if (!done) {
-                    if (n2 >= nA) done = true;
-                    else {
-                        nA = n2;
-                        theta = (S2 - ue) / T(2 + n2);
-                    }
-                }
-                if (it > a.Kp + 2) break;  // unreachable: nA drops every round
-            }
-            if (valid && gl == 0) a.theta[e] = theta;
+                for (int j = 0; j < N; ++j) rs += c[q][j];
+            rs = group_sum<G>(rs);
+            psi = rs - ue > T(0) ? rs - ue : T(0);
         }
-        // f' = max(0, c - psi'/2); psi of the stored flows
-        T rs = T(0);
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const int v = gl + q * G;
-            T o[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const T x = c[q][j] - theta;
-                o[j] = x > T(0) ? x : T(0);
-                rs += o[j];
-            }
-            if (!psi_only && valid && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
-        }
-        rs = group_sum<G>(rs);
         if (valid && gl == 0) {
-            const T over = rs - ue;
-            const T psi = over > T(0) ? over : T(0);
             zpsi = A::add(zpsi, psi * psi);
             const T c = psi * a.inv_scale_t[e];
             capmax = c > capmax ? c : capmax;
@@ -376,75 +427,33 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
 #pragma unroll
         for (int q = 0; q < V; ++q) fv[q] = av[q] = bv[q] = VT{};
         if (en < a.m) pipe_load<T, V>(a, en, lane, vpr, fv, av, bv);
-        T theta = T(0);
+        T psi;
         if (!psi_only) {
-            const T w = a.theta[e] * T(0.999);
-            T sp = T(0), sw = T(0);
-            int np = 0, nw = 0;
+            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta[e] * T(0.999), true, a.Kp);
+            if (lane == 0) a.theta[e] = theta;
+            T* orow = a.f_out + e * a.Kp;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = lane + q * 32;
+                T o[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j] - theta;
+                    o[j] = x > T(0) ? x : T(0);
+                }
+                if (v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
+            }
+            psi = T(2) * theta;  // sum f' - u at the root
+        } else {
+            T rs = T(0);
 #pragma unroll
             for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    const T x = c[q][j];
-                    if (x > T(0)) {
-                        sp += x;
-                        ++np;
-                    }
-                    if (x > w) {
-                        sw += x;
-                        ++nw;
-                    }
-                }
-            const T s = group_sum<32>(sp);
-            const int n0 = group_sum<32>(np);
-            const T S_w = group_sum<32>(sw);
-            const int n_w = group_sum<32>(nw);
-            if (s > ue) {  // warp-uniform
-                int nA = n0;
-                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
-                    nA = n_w;
-                    theta = (S_w - ue) / T(2 + n_w);
-                } else {
-                    theta = (s - ue) / T(2 + n0);
-                }
-                for (int it = 0; it <= a.Kp + 2; ++it) {
-                    T sa = T(0);
-                    int na = 0;
-#pragma unroll
-                    for (int q = 0; q < V; ++q)
-#pragma unroll
-                        for (int j = 0; j < N; ++j)
-                            if (c[q][j] > theta) {
-                                sa += c[q][j];
-                                ++na;
-                            }
-                    const T S2 = group_sum<32>(sa);
-                    const int n2 = group_sum<32>(na);
-                    if (n2 >= nA) break;
-                    nA = n2;
-                    theta = (S2 - ue) / T(2 + n2);
-                }
-            }
-            if (lane == 0) a.theta[e] = theta;
+                for (int j = 0; j < N; ++j) rs += c[q][j];
+            rs = group_sum<32>(rs);
+            psi = rs - ue > T(0) ? rs - ue : T(0);
         }
-        T rs = T(0);
-        T* orow = a.f_out + e * a.Kp;
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const int v = lane + q * 32;
-            T o[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const T x = c[q][j] - theta;
-                o[j] = x > T(0) ? x : T(0);
-                rs += o[j];
-            }
-            if (!psi_only && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
-        }
-        rs = group_sum<32>(rs);
         if (lane == 0) {
-            const T over = rs - ue;
-            const T psi = over > T(0) ? over : T(0);
             zpsi = A::add(zpsi, psi * psi);
             const T cc = psi * a.inv_scale_t[e];
             capmax = cc > capmax ? cc : capmax;
@@ -460,6 +469,48 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
 
 // ------------------------------------------------------------------ edge QP, block form (large K)
 
+// Block-wide S(w), n(w), m(w) of a row held by the whole block (thread l keeps
+// vectors l + q*B); the same value in every thread.
+template <typename T, int V, int N>
+__device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& n, T& mn, T* sa, int* sb, T* sm)
+{
+    T sl = T(0), ml = T(INFINITY);
+    int nl = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T x = c[q][j];
+            if (x > w) {
+                sl += x;
+                ++nl;
+                ml = x < ml ? x : ml;
+            }
+        }
+    sl = group_sum<32>(sl);
+    nl = group_sum<32>(nl);
+    ml = group_min<32>(ml);
+    const int wi = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sa[wi] = sl;
+        sb[wi] = nl;
+        sm[wi] = ml;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    T ts = T(0), tm = T(INFINITY);
+    int tn = 0;
+    for (int q = 0; q < nw; ++q) {  // same order in every thread
+        ts += sa[q];
+        tn += sb[q];
+        tm = sm[q] < tm ? sm[q] : tm;
+    }
+    S = ts;
+    n = tn;
+    mn = tm;
+    __syncthreads();
+}
+
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
 template <typename T, int B, int V>
 __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(SweepArgs<T> a)
@@ -469,6 +520,7 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(Sweep
     using A = Acc<T>;
     __shared__ T sa_buf[32];
     __shared__ int sb_buf[32];
+    __shared__ T sm_buf[32];
     volatile DevState* vst = a.st;
     if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
@@ -507,73 +559,54 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(Sweep
                 for (int j = 0; j < N; ++j) c[q][j] = T(0);
             }
         }
-        T theta = T(0);
+        T psi;
         if (!psi_only) {
-            // same warm-started active-set search as the lane-group form
-            const T w = a.theta[e] * T(0.999);
-            T s = T(0), S_w = T(0);
-            int n0 = 0, n_w = 0;
+            // the lane-group search with block-wide sums, counts and minima
+            const T w0 = a.theta[e] * T(0.999);
+            T S, mn, theta = T(0);
+            int n, nA = 0;
+            bool done = false;
+            block_above<T, V, N>(c, w0, S, n, mn, sa_buf, sb_buf, sm_buf);
+            if (w0 <= T(0)) start_root(S, n, mn, ue, theta, nA, done);
+            else if (S - T(n) * w0 - ue - T(2) * w0 >= T(0)) {
+                theta = (S - ue) / T(2 + n);
+                nA = n;
+                done = mn > theta;
+            } else {
+                block_above<T, V, N>(c, T(0), S, n, mn, sa_buf, sb_buf, sm_buf);
+                start_root(S, n, mn, ue, theta, nA, done);
+            }
+            for (int it = 0; !done && it <= a.Kp + 2; ++it) {  // block-uniform
+                block_above<T, V, N>(c, theta, S, n, mn, sa_buf, sb_buf, sm_buf);
+                if (n >= nA || n == 0) break;
+                nA = n;
+                theta = (S - ue) / T(2 + n);
+                done = mn > theta;
+            }
+            if (threadIdx.x == 0) a.theta[e] = theta;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = threadIdx.x + q * B;
+                T o[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j] - theta;
+                    o[j] = x > T(0) ? x : T(0);
+                }
+                if (v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
+            }
+            psi = T(2) * theta;  // sum f' - u at the root
+        } else {
+            T rs = T(0);
+            int dummy = 0;
 #pragma unroll
             for (int q = 0; q < V; ++q)
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    const T x = c[q][j];
-                    if (x > T(0)) {
-                        s += x;
-                        ++n0;
-                    }
-                    if (x > w) {
-                        S_w += x;
-                        ++n_w;
-                    }
-                }
-            block_sum2(s, n0, sa_buf, sb_buf);
-            block_sum2(S_w, n_w, sa_buf, sb_buf);
-            if (s > ue) {  // block-uniform
-                int nA = n0;
-                if (w > T(0) && S_w - T(n_w) * w - ue - T(2) * w >= T(0)) {
-                    nA = n_w;
-                    theta = (S_w - ue) / T(2 + n_w);
-                } else {
-                    theta = (s - ue) / T(2 + n0);
-                }
-                for (int it = 0; it <= a.Kp + 2; ++it) {
-                    T S2 = T(0);
-                    int n2 = 0;
-#pragma unroll
-                    for (int q = 0; q < V; ++q)
-#pragma unroll
-                        for (int j = 0; j < N; ++j)
-                            if (c[q][j] > theta) {
-                                S2 += c[q][j];
-                                ++n2;
-                            }
-                    block_sum2(S2, n2, sa_buf, sb_buf);
-                    if (n2 >= nA) break;
-                    nA = n2;
-                    theta = (S2 - ue) / T(2 + n2);
-                }
-            }
-            if (threadIdx.x == 0) a.theta[e] = theta;
+                for (int j = 0; j < N; ++j) rs += c[q][j];
+            block_sum2(rs, dummy, sa_buf, sb_buf);
+            psi = rs - ue > T(0) ? rs - ue : T(0);
         }
-        T rs = T(0);
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            const int v = threadIdx.x + q * B;
-            T o[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const T x = c[q][j] - theta;
-                o[j] = x > T(0) ? x : T(0);
-                rs += o[j];
-            }
-            if (!psi_only && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
-        }
-        int dummy = 0;
-        block_sum2(rs, dummy, sa_buf, sb_buf);
         if (threadIdx.x == 0) {
-            const T over = rs - ue;
-            const T psi = over > T(0) ? over : T(0);
             zpsi = A::add(zpsi, psi * psi);
             const T c = psi * a.inv_scale_t[e];
             capmax = c > capmax ? c : capmax;
