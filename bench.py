@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiler driver: run this many host-launched sweeps from f = 0 on the workload and exit")
+    ap.add_argument("--engine", choices=["graph", "persistent"], default="graph",
+                    help="sweep-loop engine of the solve (CUDA graph with a while node, or the persistent kernel)")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the sweep kernels from a host loop instead of the device-side graph loop "
                          "(same kernels; used for profiler runs)")
@@ -480,7 +482,8 @@ def main():
         return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
-                use_graph=0 if args.host_loop else 1, algo=ALGOS[args.algo], edge_variant=args.edge_variant)
+                use_graph=0 if args.host_loop else (2 if args.engine == "persistent" else 1), algo=ALGOS[args.algo],
+                edge_variant=args.edge_variant)
     m, K = inst.m, inst.K
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -519,8 +522,13 @@ def main():
     # S + 1 objective evaluations (the last one stops); the graph body holds 8
     # sweeps (two kernels each), the host loop launches chunks of 256 sweeps;
     # plus residuals (3), solve state init (1), reset (psi refresh + state init)
-    chunk = 256 if args.host_loop else 8
-    launches_per_step = 2 * chunk * (-(-(S + 1) // chunk)) + 3 + 1 + 2
+    if args.engine == "persistent" and not args.host_loop:
+        # one cooperative launch per 1024 sweeps (+ barrier reset each), the
+        # congestion refresh at the end, residuals, state init, reset
+        launches_per_step = 2 * (-(-(S + 1) // 1024)) + 1 + 3 + 1 + 2
+    else:
+        chunk = 256 if args.host_loop else 8
+        launches_per_step = 2 * chunk * (-(-(S + 1) // chunk)) + 3 + 1 + 2
 
     # ---------------------------------------------------------------- end to end through the C ABI
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
@@ -553,7 +561,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sweeps_per_step": S, "precision": "FP32 flows and edge QP, FP64 stop "
                    "test and certificate", "l2": "256 MiB buffer overwritten between timed steps",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "engine": "host loop" if args.host_loop else args.engine},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks.summary(),

@@ -86,9 +86,14 @@ typedef enum {
 
 typedef struct {
     int32_t precision;  /* pdr_precision (default PDR_PREC_FP32) */
-    int32_t use_graph;  /* 1: the sweep loop runs on the device as one CUDA graph with a conditional
-                           while node; 0: the same kernels are launched from a host loop that reads
-                           the stop flag between chunks of sweeps (default 1) */
+    int32_t use_graph;  /* sweep-loop engine.  1: the loop runs on the device as one CUDA graph with
+                           a conditional while node (default).  0: the same kernels are launched
+                           from a host loop that reads the stop flag between chunks of sweeps.
+                           2: one persistent cooperative kernel runs the excess pass and the edge
+                           QPs of every sweep, separated by grid barriers, for 1024 sweeps per
+                           launch (PDR_ALGO_ESO with a lane-group edge variant, K <= 1024 in FP32
+                           or 512 in FP64; otherwise 1 is used); a barrier that waits more than
+                           about a second ends the solve with PDR_ERR_CUDA */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */

@@ -56,6 +56,10 @@ bool options_ok(const pdr_options* o, std::string* why)
         *why = "eps_obj, resid_tol and eps_rel must be finite";
         return false;
     }
+    if (o->use_graph < 0 || o->use_graph > 2) {
+        *why = "use_graph must be 0 (host loop), 1 (CUDA graph) or 2 (persistent kernel)";
+        return false;
+    }
     if (o->max_sweeps < 0) {
         *why = "max_sweeps must be >= 0";
         return false;
@@ -123,6 +127,8 @@ struct pdr_ctx {
     double *part_cons = nullptr, *part_capb = nullptr, *part_psi = nullptr, *part_cap = nullptr;
     int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
     int64_t n_psi[2] = {1, 1};
+    int pgrid[2] = {0, 0};         // persistent kernel grid per precision (0: not available)
+    GridBarrier* bar = nullptr;    // its grid barrier
     DevState* st = nullptr;
     DevState* hst = nullptr;  // pinned mirror
     double* trace = nullptr;
@@ -383,9 +389,9 @@ int start_prec(const pdr_options& o) { return o.precision == PDR_PREC_FP64 ? 1 :
 
 // Recomputes the congestion partials of the current flows.
 template <typename T>
-pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr)
+pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr, bool keep_theta = false)
 {
-    if (!psi_out) {
+    if (!psi_out && !keep_theta) {
         // new flows: the edge QPs start their root search cold
         CK(cudaMemsetAsync(ctx->theta, 0, sizeof(double) * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
     }
@@ -433,6 +439,8 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
     ctx->grid_e[1] = c64 >= 0 ? edge_grid<double>(c64, ctx->m, ctx->num_sms) : 1;
     ctx->n_psi[0] = edge_parts<float>(c32, ctx->grid_e[0]);
     ctx->n_psi[1] = c64 >= 0 ? edge_parts<double>(c64, ctx->grid_e[1]) : 1;
+    ctx->pgrid[0] = persistent_grid<float>(c32, ctx->m, ctx->n, Kp, ctx->num_sms);
+    ctx->pgrid[1] = c64 >= 0 ? persistent_grid<double>(c64, ctx->m, ctx->n, Kp, ctx->num_sms) : 0;
     return PDR_OK;
 }
 
@@ -511,6 +519,50 @@ fail:
     return PDR_OK;  // the host loop takes over
 }
 
+constexpr int64_t kPersistChunk = 1024;  // sweeps per persistent launch (even)
+
+// The persistent engine applies to Alg. 1 with a lane-group variant.
+bool persistent_ok(const pdr_ctx* ctx, int p)
+{
+    return ctx->opt.use_graph == 2 && ctx->opt.algo == PDR_ALGO_ESO && ctx->pgrid[p] >= 2;
+}
+
+// Alg. 1 by the persistent kernel: launches of kPersistChunk sweeps until the
+// stop rules fire; the flows start in buffer 0.  *ran = false if the first
+// cooperative launch was refused (the caller then uses the graph engine).
+template <typename T>
+pdr_status run_persistent(pdr_ctx* ctx, bool* ran)
+{
+    const int p = Prec<T>::id;
+    const int grid = ctx->pgrid[p];
+    SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, 0, 0);
+    a.grid_v = grid;
+    a.grid_e = grid - 1;
+    a.n_psi = (int64_t)(grid - 1) * (kThreads / 32);
+    pdr_status s = PDR_OK;
+    *ran = false;
+    for (int launch = 0;; ++launch) {
+        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(GridBarrier), ctx->stream));
+        const cudaError_t le = launch_persistent<T>(a, ctx->cfg[p], grid, kPersistChunk, ctx->bar,
+                                                    launch == 0 ? 1 : 0, ctx->stream);
+        if (le != cudaSuccess) {
+            if (launch > 0) return ctx->cuda_fail("launch_persistent", le);
+            cudaGetLastError();  // e.g. too large for co-residency here: never try again
+            ctx->pgrid[0] = ctx->pgrid[1] = 0;
+            return PDR_OK;
+        }
+        *ran = true;
+        GridBarrier hb{};
+        CK(cudaMemcpyAsync(&hb, ctx->bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, ctx->stream));
+        s = read_state(ctx);  // synchronises the stream
+        if (s != PDR_OK) return s;
+        if (hb.failed) return ctx->fail(PDR_ERR_CUDA, "persistent sweep kernel: a grid barrier timed out");
+        if (ctx->hst->stop) break;
+    }
+    // the other engines read the congestion partials in the standalone layout
+    return refresh_psi<T>(ctx, nullptr, true);
+}
+
 // One phase of Alg. 1 in precision T, from the state set by init_state
 // (whose t is t_start).  Afterwards the current flows f^(t) sit in buffer
 // (t - t_start) mod 2: every sweep that does not stop swaps the buffers.
@@ -522,6 +574,15 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     if (s != PDR_OK) return s;
     s = flows_to_buffer0<T>(ctx);
     if (s != PDR_OK) return s;
+    if (persistent_ok(ctx, p)) {
+        bool ran = false;
+        s = run_persistent<T>(ctx, &ran);
+        if (s != PDR_OK) return s;
+        if (ran) {
+            ctx->cur = (int)((ctx->hst->t - t_start) & 1);
+            return PDR_OK;
+        }
+    }
     if (ctx->opt.use_graph && !ctx->graph_tried[p]) {
         s = build_graph<T>(ctx);
         if (s != PDR_OK) return s;
@@ -777,7 +838,7 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
                    ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta,
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
-                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp};
+                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (ctx->hst) cudaFreeHost(ctx->hst);
@@ -874,15 +935,20 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->dem_f, float, Kp);
     ALLOC(ctx->inv_dem_d, double, Kp);
     ALLOC(ctx->inv_dem_f, float, Kp);
-    const int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
+    int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
     int64_t np = ctx->n_psi[0] > ctx->n_psi[1] ? ctx->n_psi[0] : ctx->n_psi[1];
-    if (np < m + 8) np = m + 8;  // any variant writes at most m + 8 edge partials
+    if (np < m + 8) np = m + 8;  // any standalone variant writes at most m + 8 edge partials
+    // the persistent kernel: at most 8 blocks of 256 threads per SM, one
+    // partial per block and per warp
+    if (gv < 8 * ctx->num_sms) gv = 8 * ctx->num_sms;
+    if (np < 64 * (int64_t)ctx->num_sms) np = 64 * (int64_t)ctx->num_sms;
     ALLOC(ctx->part_h, double, gv);
     ALLOC(ctx->part_cons, double, gv);
     ALLOC(ctx->part_capb, double, gv);
     ALLOC(ctx->part_psi, double, np);
     ALLOC(ctx->part_cap, double, np);
     ALLOC(ctx->st, DevState, 1);
+    ALLOC(ctx->bar, GridBarrier, 1);
     ctx->trace_cap = o.trace_len;
     ALLOC(ctx->trace, double, ctx->trace_cap > 0 ? ctx->trace_cap : 1);
     ALLOC(ctx->r_h64, double, (size_t)n * Kp);

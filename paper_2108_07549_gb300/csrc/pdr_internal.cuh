@@ -63,6 +63,16 @@ struct DevState {
                           // the gradient-step kernels while the decision block advances t)
 };
 
+// Grid barrier of the persistent sweep kernel (device memory, zeroed before
+// each launch).  `failed` is set when a wait ran out of its iteration limit;
+// every block then leaves the kernel and the host reports the error.
+struct GridBarrier {
+    unsigned int count;   // blocks arrived at the current barrier
+    unsigned int gen;     // barrier generation, advanced by the last arrival
+    unsigned int failed;  // 1: a wait timed out
+    unsigned int pad;
+};
+
 template <typename T>
 struct SweepArgs {
     int32_t n;
@@ -137,6 +147,14 @@ int num_edge_configs();
 int edge_plain_config(int cfg);          // the non-pipelined variant of the same capacity
 bool edge_config_pipelined(int cfg);
 int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
+// Persistent sweep kernel (sweep.cu): excess and edge QP of every sweep in one
+// cooperative launch, separated by grid barriers; runs up to `sweeps` sweeps
+// of Alg. 1 or until the stop rules fire.  Only the lane-group variants.
+template <typename T>
+int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms);  // 0: not available
+template <typename T>
+cudaError_t launch_persistent(const SweepArgs<T>& a, int cfg, int grid, int64_t sweeps, GridBarrier* bar,
+                              int psi_prologue, cudaStream_t stream);
 template <typename T>
 int excess_resident_blocks();  // excess blocks resident per SM (occupancy)
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream);

@@ -37,21 +37,22 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(SweepArgs<T> a)
 
 // ------------------------------------------------------------------ excess and heights
 
+// Body of one excess pass run by block `block` of `nblocks` (the standalone
+// kernel passes its own grid; the persistent kernel its whole grid).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
+__device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, int nblocks)
 {
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
+    if (block == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
     const uint32_t vpr = (uint32_t)(a.Kp / N);
     const uint64_t total = (uint64_t)a.n * vpr;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = (uint64_t)nblocks * blockDim.x;
     typename A::V zacc = A::zero();
     T cons = T(0);
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    for (uint64_t idx = (uint64_t)block * blockDim.x + threadIdx.x; idx < total; idx += stride) {
         uint32_t i, v;
         if (total <= 0xffffffffull) {
             i = (uint32_t)idx / vpr;
@@ -132,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     // this block's fixed slice of the edge kernel's psi partials
     T capb = T(0);
     {
-        const int64_t lo = (int64_t)blockIdx.x * a.n_psi / gridDim.x;
-        const int64_t hi = (int64_t)(blockIdx.x + 1) * a.n_psi / gridDim.x;
+        const int64_t lo = (int64_t)block * a.n_psi / nblocks;
+        const int64_t hi = (int64_t)(block + 1) * a.n_psi / nblocks;
         const typename A::S* pp = reinterpret_cast<const typename A::S*>(a.part_psi);
         for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
             zacc = A::add(zacc, A::load(pp + b));
@@ -143,10 +144,18 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     }
     block_acc_max2<T>(zacc, cons, capb);
     if (threadIdx.x == 0) {
-        a.part_h[blockIdx.x] = A::to_double(zacc);
-        a.part_cons[blockIdx.x] = cons;
-        a.part_capb[blockIdx.x] = capb;
+        a.part_h[block] = A::to_double(zacc);
+        a.part_cons[block] = cons;
+        a.part_capb[block] = capb;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
+{
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    excess_body<T>(a, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ the root search of Alg. 2
@@ -255,24 +264,30 @@ __device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool 
 // One aligned group of G lanes per edge; each lane keeps V vectors of the
 // edge's row in registers (vector q of lane l is row vector l + q*G, so a
 // group reads contiguous memory).  K <= G * V * N.
-template <typename T, int G, int V>
-__global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
+// Loads of data written by an earlier kernel of the same sweep: through the
+// read-only path in a standalone kernel; plain (coherent) loads inside the
+// persistent kernel, where the data changes between its grid barriers.
+template <bool P, typename X>
+__device__ __forceinline__ X ld_row(const X* p)
+{
+    if constexpr (P) return *p;
+    else return __ldg(p);
+}
+
+// Body of one edge-QP pass of the lane-group form, run by edge block `block`
+// of `nblocks` (the decision block is not counted).
+template <typename T, int G, int V, bool P>
+__device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block, int nblocks)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
     constexpr int GPW = 32 / G;  // groups per warp
     using A = Acc<T>;
-    volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
-    if (blockIdx.x == gridDim.x - 1) {               // the decision block
-        if (a.mode != MODE_PSI) reduce_and_finalize(a);
-        return;
-    }
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int gw = lane / G;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)(gridDim.x - 1) * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)block * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)nblocks * blockDim.x) >> 5;
     const int vpr = a.Kp / N;
     const bool psi_only = (a.mode == MODE_PSI);
     typename A::V zpsi = A::zero();
@@ -304,8 +319,8 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
                 if (valid && v < vpr) {
                     T fx[N], ax[N], bx[N];
                     unpack(reinterpret_cast<const VT*>(frow)[v], fx);
-                    unpack(__ldg(hi + v), ax);
-                    unpack(__ldg(hj + v), bx);
+                    unpack(ld_row<P>(hi + v), ax);
+                    unpack(ld_row<P>(hj + v), bx);
                     // c_k = 1/2 ((h_ik + f_k) - (h_jk - f_k)) = f_k + (h_ik - h_jk)/2
 #pragma unroll
                     for (int j = 0; j < N; ++j) c[q][j] = fma(T(0.5), ax[j] - bx[j], fx[j]);
@@ -358,6 +373,18 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
         reinterpret_cast<typename A::S*>(a.part_psi)[warp] = A::store(zpsi);
         a.part_cap[warp] = capmax;
     }
+}
+
+template <typename T, int G, int V>
+__global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
+{
+    volatile DevState* vst = a.st;
+    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (blockIdx.x == gridDim.x - 1) {               // the decision block
+        if (a.mode != MODE_PSI) reduce_and_finalize(a);
+        return;
+    }
+    edge_group_body<T, G, V, false>(a, blockIdx.x, gridDim.x - 1);
 }
 
 // ------------------------------------------------------------------ edge QP, pipelined lane-group form
@@ -620,6 +647,101 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(Sweep
     }
 }
 
+// ------------------------------------------------------------------ persistent sweep kernel
+//
+// For instances whose two sweep kernels last only a few microseconds each,
+// the fixed cost of a kernel boundary (launch, ramp-up, drain) is a large
+// share of the sweep.  This kernel keeps one cooperative grid resident for
+// many sweeps: the excess pass over all blocks, a grid barrier, the edge QPs
+// over all blocks but the last, which reduces the objective and takes the stop
+// decision meanwhile (as the decision block of the standalone edge kernel),
+// and a second barrier after which every block reads the same stop flag.
+
+constexpr long long kBarrierSpins = 1ll << 21;  // ~1-2 s of polling, then give up
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Sense-by-generation barrier over the whole (co-resident) grid.  Returns
+// false in every thread of a block whose wait timed out or saw another
+// block's timeout.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the generation is read before arriving, so the last arrival's
+        // increment is always seen as a change
+        const unsigned int gen = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        int good = 1;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, gen + 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (ld_acquire_u32(&bar->failed) != 0u || ++spins > kBarrierSpins) {
+                    atomicExch(&bar->failed, 1u);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, int G, int V>
+__global__ void __launch_bounds__(kThreads, (V <= 4 ? 4 : 3))
+    persistent_kernel(SweepArgs<T> a, int64_t sweeps, GridBarrier* bar, int psi_prologue)
+{
+    volatile DevState* vst = a.st;
+    const int nb = gridDim.x - 1;  // edge blocks; block nb decides
+    // congestion partials of the current flows in this grid's layout (a
+    // later launch of the same solve finds them written by its predecessor)
+    if (psi_prologue) {
+        SweepArgs<T> b = a;
+        b.mode = MODE_PSI;
+        if ((int)blockIdx.x < nb) edge_group_body<T, G, V, true>(b, blockIdx.x, nb);
+        if (!grid_sync(bar)) return;
+    }
+    for (int64_t q = 0; q < sweeps; ++q) {
+        if (vst->stop) break;  // the same value in every block (read after a barrier)
+        SweepArgs<T> b = a;
+        if (q & 1) {
+            b.f = a.f_out;
+            b.f_out = a.f;
+        }
+        excess_body<T>(b, blockIdx.x, gridDim.x);
+        if (!grid_sync(bar)) return;
+        if ((int)blockIdx.x == nb) reduce_and_finalize(b);
+        else edge_group_body<T, G, V, true>(b, blockIdx.x, nb);
+        if (!grid_sync(bar)) return;
+    }
+}
+
+template <typename T, int G, int V>
+cudaError_t persistent_occupancy(int* blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, persistent_kernel<T, G, V>, kThreads, 0);
+}
+
 __global__ void convert_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t count)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
@@ -778,6 +900,65 @@ cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
     }
     return cudaGetLastError();
 }
+
+template <typename T>
+int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms)
+{
+    cfg = edge_plain_config(cfg);
+    if (cfg < 0 || cfg >= kNumCfg || !kCfg[cfg].G || m <= 0) return 0;
+    int per_sm = 0;
+    cudaError_t e;
+    switch (cfg) {
+    case 0: e = persistent_occupancy<T, 4, 1>(&per_sm); break;
+    case 1: e = persistent_occupancy<T, 8, 1>(&per_sm); break;
+    case 2: e = persistent_occupancy<T, 16, 1>(&per_sm); break;
+    case 3: e = persistent_occupancy<T, 32, 1>(&per_sm); break;
+    case 4: e = persistent_occupancy<T, 32, 2>(&per_sm); break;
+    case 5: e = persistent_occupancy<T, 32, 4>(&per_sm); break;
+    case 6: e = persistent_occupancy<T, 32, 8>(&per_sm); break;
+    default: return 0;
+    }
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    // no more blocks than either pass has work for (each costs an arrival at
+    // every barrier), at least one edge block and the decision block
+    const int64_t groups_per_block = kThreads / kCfg[cfg].G;
+    const int64_t want_e = (m + groups_per_block - 1) / groups_per_block + 1;
+    const int64_t want_v = ((int64_t)n * (Kp / VecOf<T>::N) + kThreads - 1) / kThreads;
+    int64_t g = want_e > want_v ? want_e : want_v;
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (g > cap) g = cap;
+    return g < 2 ? 2 : (int)g;
+}
+
+template <typename T>
+cudaError_t launch_persistent(const SweepArgs<T>& a, int cfg, int grid, int64_t sweeps, GridBarrier* bar,
+                              int psi_prologue, cudaStream_t stream)
+{
+    SweepArgs<T> args = a;
+    void* params[] = {&args, &sweeps, &bar, &psi_prologue};
+    void* fn = nullptr;
+    switch (edge_plain_config(cfg)) {
+    case 0: fn = (void*)persistent_kernel<T, 4, 1>; break;
+    case 1: fn = (void*)persistent_kernel<T, 8, 1>; break;
+    case 2: fn = (void*)persistent_kernel<T, 16, 1>; break;
+    case 3: fn = (void*)persistent_kernel<T, 32, 1>; break;
+    case 4: fn = (void*)persistent_kernel<T, 32, 2>; break;
+    case 5: fn = (void*)persistent_kernel<T, 32, 4>; break;
+    case 6: fn = (void*)persistent_kernel<T, 32, 8>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), params, 0, stream);
+}
+
+template int persistent_grid<float>(int, int64_t, int32_t, int, int);
+template int persistent_grid<double>(int, int64_t, int32_t, int, int);
+template cudaError_t launch_persistent<float>(const SweepArgs<float>&, int, int, int64_t, GridBarrier*, int,
+                                              cudaStream_t);
+template cudaError_t launch_persistent<double>(const SweepArgs<double>&, int, int, int64_t, GridBarrier*, int,
+                                               cudaStream_t);
 
 int edge_plain_config(int cfg) { return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P) ? 3 + (cfg - 14) : cfg; }
 
