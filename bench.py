@@ -73,6 +73,9 @@ def parse():
                     help="time Alg. 1, Alg. 3 and Alg. 4 on the workload and print one comparison line")
     ap.add_argument("--edge-variant", type=int, default=-1,
                     help="edge-kernel variant (index of the library's variant table; -1 = the library's choice)")
+    ap.add_argument("--compare-engines", action="store_true",
+                    help="time the sweep-loop engines (host loop, CUDA graph, persistent kernel) on instances "
+                         "from m = 80 to the bench workload and print one JSON line")
     ap.add_argument("--compare-variants", action="store_true",
                     help="time every edge-kernel variant that holds the rows (Alg. 1) and print one JSON line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
@@ -169,7 +172,7 @@ def source_digest():
     """Digest of the sweep kernels' sources (the files the ncu counters depend on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_07549_gb300", "csrc")
-    for name in ("sweep.cu", "pdr_internal.cuh"):
+    for name in ("sweep.cu", "sweep_common.cuh", "pdr_internal.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -337,6 +340,44 @@ def compare_variants(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+def compare_engines(args, inst, pdr, torch, stream):
+    """Alg. 1 in FP32 with each sweep-loop engine on instances of growing size
+    (the last one the bench workload): microseconds per sweep of a solve of a
+    fixed number of sweeps (CUDA events; the FP64 residual pass is included
+    and is below 1 % of these solves)."""
+    import numpy as np
+
+    from paper_2108_07549_gb300 import instances as I
+
+    rng = np.random.default_rng(0)
+    cases = [I.grid5_k10(1.2),
+             I.make_instance("digraph200_k50", I.random_digraph(200, 3, rng), 50, ("uniform_int", 1, 9), 1.1, rng),
+             I.make_instance("knn500_k100", I.knn_graph(500, 3, rng), 100, ("uniform_int", 1, 20), 1.2, rng),
+             I.make_instance("knn1000_k250", I.knn_graph(1000, 3, rng), 250, ("uniform_int", 1, 20), 1.2, rng),
+             inst]
+    S = args.sweeps
+    out = {"kind": "sweep-loop engine comparison", "sweeps": S, "dtype": "f32", "us_per_sweep": {}}
+    for c in cases:
+        row = {"m": c.m, "K": c.K}
+        for name, eng in (("host_loop", 0), ("graph", 1), ("persistent", 2)):
+            with torch.cuda.stream(stream):
+                with pdr.Solver.from_instance(c, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
+                                              resid_tol=0.0, max_sweeps=S, use_graph=eng) as sv:
+                    sv.solve()
+                    times = []
+                    for q in range(3):
+                        sv.reset()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        sv.solve()
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        times.append(e0.elapsed_time(e1))
+            row[name] = sorted(times)[1] * 1e3 / S
+        out["us_per_sweep"][c.name] = row
+    print(json.dumps(out), flush=True)
+
+
 def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
     """The differentiated form: L = z(f^(T)) and its gradient w.r.t. u and d
     by reverse mode through T sweeps with checkpoints every ckpt, against the
@@ -473,6 +514,9 @@ def main():
         return
     if args.compare_variants:
         compare_variants(args, inst, pdr, torch, stream)
+        return
+    if args.compare_engines:
+        compare_engines(args, inst, pdr, torch, stream)
         return
     if args.workload == "batch256":
         bench_batch(args, inst, pdr, torch, stream)

@@ -29,6 +29,9 @@ thread_local std::string g_create_error;
 int round_up4(int k) { return (k + 3) / 4 * 4; }
 
 constexpr int kUnroll = 8;  // sweeps per iteration of the graph's while loop (even)
+// Working sets above this stream from HBM every sweep (GB300: 129 MB of L2;
+// measured L2-resident streaming holds up to ~90 MB and collapses by 120 MB).
+constexpr double kL2Bytes = 96.0 * 1024 * 1024;
 
 void fill_defaults(pdr_options* o)
 {
@@ -128,6 +131,7 @@ struct pdr_ctx {
     int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
     int64_t n_psi[2] = {1, 1};
     int pgrid[2] = {0, 0};         // persistent kernel grid per precision (0: not available)
+    int64_t pf[2] = {0, 0};        // edge-kernel L2 prefetch distance per precision (edges)
     GridBarrier* bar = nullptr;    // its grid barrier
     DevState* st = nullptr;
     DevState* hst = nullptr;  // pinned mirror
@@ -262,6 +266,7 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.grid_v = ctx->grid_v[p];
     a.grid_e = ctx->grid_e[p];
     a.n_psi = ctx->n_psi[p];
+    a.pf_edges = ctx->pf[p];
     a.psi_out = nullptr;
     a.st = ctx->st;
     a.trace = ctx->trace;
@@ -411,6 +416,13 @@ pdr_status refresh_psi_current(pdr_ctx* ctx)
     return ctx->cur_prec ? refresh_psi<double>(ctx) : refresh_psi<float>(ctx);
 }
 
+template <typename T>
+int64_t prefetch_policy(const pdr_ctx* ctx, int cfg)
+{
+    const double rows = (2.0 * (double)ctx->m + (double)ctx->n) * (double)ctx->Kp;
+    return rows * sizeof(T) > kL2Bytes ? edge_prefetch_distance<T>(cfg, ctx->num_sms) : 0;
+}
+
 // The edge-kernel variant of each precision: the caller's (it must hold the
 // rows in every precision the solve uses) or the library's choice.  Sets
 // cfg, grid_e and n_psi; cfg = -1 for a precision whose rows no variant holds.
@@ -439,6 +451,11 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
     ctx->grid_e[1] = c64 >= 0 ? edge_grid<double>(c64, ctx->m, ctx->num_sms) : 1;
     ctx->n_psi[0] = edge_parts<float>(c32, ctx->grid_e[0]);
     ctx->n_psi[1] = c64 >= 0 ? edge_parts<double>(c64, ctx->grid_e[1]) : 1;
+    // L2 prefetch of later waves' rows pays only when the rows come from HBM:
+    // when both flow buffers and the heights fit in L2 (as they stay across
+    // sweeps) the prefetches are pure overhead
+    ctx->pf[0] = prefetch_policy<float>(ctx, c32);
+    ctx->pf[1] = c64 >= 0 ? prefetch_policy<double>(ctx, c64) : 0;
     ctx->pgrid[0] = persistent_grid<float>(c32, ctx->m, ctx->n, Kp, ctx->num_sms);
     ctx->pgrid[1] = c64 >= 0 ? persistent_grid<double>(c64, ctx->m, ctx->n, Kp, ctx->num_sms) : 0;
     return PDR_OK;
@@ -539,6 +556,8 @@ pdr_status run_persistent(pdr_ctx* ctx, bool* ran)
     a.grid_v = grid;
     a.grid_e = grid - 1;
     a.n_psi = (int64_t)(grid - 1) * (kThreads / 32);
+    // each warp's next edge: one round of the whole grid ahead
+    a.pf_edges = (int64_t)(grid - 1) * (kThreads / edge_group_lanes(ctx->cfg[p]));
     pdr_status s = PDR_OK;
     *ran = false;
     for (int launch = 0;; ++launch) {
@@ -1610,6 +1629,7 @@ pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
         ctx->cfg[p] = c;
         ctx->grid_e[p] = edge_grid<T>(c, ctx->m, ctx->num_sms);
         ctx->n_psi[p] = edge_parts<T>(c, ctx->grid_e[p]);
+        ctx->pf[p] = prefetch_policy<T>(ctx, c);
         double tot = 0.0;
         for (int r = 0; r < 4; ++r) {
             cudaEventRecord(e0, ctx->stream);
@@ -1636,6 +1656,8 @@ pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
     ctx->cfg[p] = *best_cfg;
     ctx->grid_e[p] = edge_grid<T>(*best_cfg, ctx->m, ctx->num_sms);
     ctx->n_psi[p] = edge_parts<T>(*best_cfg, ctx->grid_e[p]);
+    ctx->pf[p] = prefetch_policy<T>(ctx, *best_cfg);
+    ctx->pgrid[p] = persistent_grid<T>(*best_cfg, ctx->m, ctx->n, ctx->Kp, ctx->num_sms);
     *best_us = best;
     destroy_graphs(ctx);
     pdr_status s = refresh_psi<T>(ctx);

@@ -110,6 +110,8 @@ struct SweepArgs {
     T* part_cap;        // [n_psi] per edge warp/block: max psi/scale
     int32_t grid_v, grid_e;
     int64_t n_psi;      // number of edge partials
+    int64_t pf_edges;   // edge QP: L2 prefetch of the rows of edge e + pf_edges while
+                        // edge e is solved (about one wave of resident edges ahead; 0: off)
     // Alg. 3 / Alg. 4 state (double-buffered like the flows) and parameters
     const T* beta_in;   // [m] learning rates beta_ij of iteration t
     T* beta_out;        // [m] learning rates of iteration t+1
@@ -145,6 +147,9 @@ template <typename T>
 int edge_capacity(int cfg);             // elements per row a variant holds (-1 if none)
 int num_edge_configs();
 int edge_plain_config(int cfg);          // the non-pipelined variant of the same capacity
+int edge_group_lanes(int cfg);           // lanes per edge of a lane-group variant
+template <typename T>
+int64_t edge_prefetch_distance(int cfg, int num_sms);  // edges solved by one wave of resident blocks
 bool edge_config_pipelined(int cfg);
 int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
 // Persistent sweep kernel (sweep.cu): excess and edge QP of every sweep in one

@@ -295,6 +295,8 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
     for (int64_t base = warp * GPW; base < a.m; base += nwarps * GPW) {
         const int64_t e = base + gw;
         const bool valid = e < a.m;
+        if (a.pf_edges > 0 && valid && e + a.pf_edges < a.m)  // the flow row a later wave reads
+            prefetch_l2(a.f + (e + a.pf_edges) * a.Kp, (int64_t)a.Kp * sizeof(T), gl, G);
         const T ue = valid ? a.u[e] : T(0);
         T c[V][N];
         const T* frow = a.f + (valid ? e : 0) * a.Kp;
@@ -559,6 +561,14 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(Sweep
     typename A::V zpsi = A::zero();
     T capmax = T(0);
     for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x - 1) {
+        const int64_t ep = e + a.pf_edges;  // an edge of a later wave
+        const bool pf = a.pf_edges > 0 && ep < a.m;
+        int32_t ps = 0, pc = 0;
+        if (pf) {
+            ps = a.src[ep];
+            pc = a.col[ep];
+            prefetch_l2(a.f + ep * a.Kp, (int64_t)a.Kp * sizeof(T), threadIdx.x, B);
+        }
         const T ue = a.u[e];
         T c[V][N];
         const T* frow = a.f + e * a.Kp;
@@ -611,6 +621,10 @@ __global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(Sweep
                 done = mn > theta;
             }
             if (threadIdx.x == 0) a.theta[e] = theta;
+            if (pf) {  // its height rows, now that its endpoints have arrived
+                prefetch_l2(a.h + (int64_t)ps * a.Kp, (int64_t)a.Kp * sizeof(T), threadIdx.x, B);
+                prefetch_l2(a.h + (int64_t)pc * a.Kp, (int64_t)a.Kp * sizeof(T), threadIdx.x, B);
+            }
 #pragma unroll
             for (int q = 0; q < V; ++q) {
                 const int v = threadIdx.x + q * B;
@@ -959,6 +973,47 @@ template cudaError_t launch_persistent<float>(const SweepArgs<float>&, int, int,
                                               cudaStream_t);
 template cudaError_t launch_persistent<double>(const SweepArgs<double>&, int, int, int64_t, GridBarrier*, int,
                                                cudaStream_t);
+
+template <typename T>
+int64_t edge_prefetch_distance(int cfg, int num_sms)
+{
+    if (cfg < 0 || cfg >= kNumCfg || kCfg[cfg].P) return 0;
+    const EdgeCfg& c = kCfg[cfg];
+    int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    switch (cfg) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 4, 1>, kThreads, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 8, 1>, kThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 16, 1>, kThreads, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 1>, kThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 2>, kThreads, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 4>, kThreads, 0); break;
+    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 8>, kThreads, 0); break;
+    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 256, 2>, 256, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 2>, 512, 0); break;
+    case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 3>, 512, 0); break;
+    case 10: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 4>, 512, 0); break;
+    case 11: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 5>, 512, 0); break;
+    case 12: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 8>, 512, 0); break;
+    case 13: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 1024, 8>, 1024, 0); break;
+    default: return 0;
+    }
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int64_t per_block = c.G ? kThreads / c.G : 1;
+    return (int64_t)num_sms * per_sm * per_block;
+}
+
+template int64_t edge_prefetch_distance<float>(int, int);
+template int64_t edge_prefetch_distance<double>(int, int);
+
+int edge_group_lanes(int cfg)
+{
+    cfg = edge_plain_config(cfg);
+    return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].G) ? kCfg[cfg].G : 32;
+}
 
 int edge_plain_config(int cfg) { return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P) ? 3 + (cfg - 14) : cfg; }
 

@@ -41,6 +41,16 @@ __device__ __forceinline__ void unpack(const double2& v, double* x)
 __device__ __forceinline__ float4 pack4(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
 __device__ __forceinline__ double2 pack4(const double* x) { return make_double2(x[0], x[1]); }
 
+// L2 prefetch of the `bytes` bytes at p, one 128-byte line per thread and
+// round (thread `tid` of `nthreads`).  Only addresses inside the array are
+// passed; a prefetch never blocks the thread.
+__device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes, int tid, int nthreads)
+{
+    const char* c = static_cast<const char*>(p);
+    for (int64_t off = (int64_t)tid * 128; off < bytes; off += (int64_t)nthreads * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
+}
+
 // Sum over the G lanes of an aligned lane group (xor offsets below G stay
 // inside the group).  Every lane of the warp must call it.  IEEE addition is
 // commutative, so every lane of the group ends with the same value.

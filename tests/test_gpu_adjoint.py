@@ -121,13 +121,14 @@ def test_torch_autograd_function(pdr):
 def test_full_size_fp32_gradient_vs_fp64_finite_differences(pdr):
     """digraph20k_k2000 (n=20,000, m=100,000, K=2,000), T = 50 sweeps with
     checkpoints every 10: the FP32 reverse mode against FP64 central
-    differences of the GPU's FP64 forward on sampled capacities and demands."""
+    differences of the GPU's FP64 forward on 64 sampled capacities and 8
+    sampled demands (1e-3 relative)."""
     inst = I.digraph20k_k2000(1.05, seed=0)
     T = 50
     with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32) as s32:
         L32, gu, gd = s32.backward(T, 10)
     rng = np.random.default_rng(0)
-    edges = rng.choice(np.nonzero(inst.u > 0)[0], 8, replace=False)
+    edges = rng.choice(np.nonzero(inst.u > 0)[0], 64, replace=False)
     comms = rng.choice(inst.K, 8, replace=False)
     checked = 0
     with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP64) as s64:
@@ -143,6 +144,9 @@ def test_full_size_fp32_gradient_vs_fp64_finite_differences(pdr):
             h = 1e-4 * base[idx]
             vals = []
             for q in (-1, 0, 1):
+                if q == 0:
+                    vals.append(L64)  # the unperturbed objective
+                    continue
                 x = base.copy()
                 x[idx] += q * h
                 vals.append(L_at(x, inst.d) if which == "u" else L_at(inst.u, x))
@@ -154,4 +158,4 @@ def test_full_size_fp32_gradient_vs_fp64_finite_differences(pdr):
             assert abs(g - central) <= 1e-3 * scale, (which, idx, g, central)
             checked += 1
         s64.set_data(u=inst.u, d=inst.d)
-    assert checked >= 12
+    assert checked >= 56
