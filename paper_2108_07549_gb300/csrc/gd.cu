@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
 
 // One block of B threads per edge (large K); thread l holds row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) gd_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;

@@ -114,7 +114,7 @@ __device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, in
             if (a.s[k] == (int)i) acc[j] += a.dem[k];
             else if (a.t[k] == (int)i) acc[j] -= a.dem[k];
         }
-        const T dgt = T(q1 - q0);
+        const T dgt = T((int)(q1 - q0));  // delta_i < 2^31: a 32-bit conversion
         const T idg = a.inv_deg[i];
         T hv[N];
 #pragma unroll
@@ -542,7 +542,7 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B, (B <= 512 ? 2 : 1)) edge_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? 2 : 1))) edge_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
