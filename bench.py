@@ -73,6 +73,10 @@ def parse():
                     help="time Alg. 1, Alg. 3 and Alg. 4 on the workload and print one comparison line")
     ap.add_argument("--edge-variant", type=int, default=-1,
                     help="edge-kernel variant (index of the library's variant table; -1 = the library's choice)")
+    ap.add_argument("--to-residual", action="store_true",
+                    help="batch256: solve every instance to its verdict (residuals <= 1e-6 or a Farkas "
+                         "certificate, FP32 with the FP64 tail) as one batch and one after another")
+    ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--compare-engines", action="store_true",
                     help="time the sweep-loop engines (host loop, CUDA graph, persistent kernel) on instances "
                          "from m = 80 to the bench workload and print one JSON line")
@@ -408,6 +412,51 @@ def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
     print(json.dumps(out), flush=True)
 
 
+def bench_batch_to_residual(args, insts, pdr, torch, stream):
+    """The batched form against the single-instance form at residual <= 1e-6:
+    every instance solved to its verdict (FP32 sweeps, then FP64 sweeps once
+    FP32 stalls; stop when cap_rel and cons_rel <= 1e-6 or, for infeasible
+    instances, when the Farkas certificate holds), (a) as one batch and (b)
+    one after another.  Wall-clock time of each from f = 0, verdicts and
+    residuals compared."""
+    max_sweeps = args.sweeps if args.sweeps > 0 else 200000
+    opts = dict(precision=pdr.PREC_FP32_FP64TAIL, eps_obj=0.0, resid_tol=1e-6, eps_rel=1e-13, max_sweeps=max_sweeps)
+    with torch.cuda.stream(stream):
+        B = pdr.Batch(insts, stream=stream.cuda_stream, **opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = B.solve()
+        tb = time.perf_counter() - t0
+        B.close()
+        rs, ts = [], 0.0
+        for x in insts:
+            with pdr.Solver.from_instance(x, stream=stream.cuda_stream, **opts) as sv:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rs.append(sv.solve())
+                ts += time.perf_counter() - t0
+    want = [x.feasible_by_construction for x in insts]
+
+    def summary(res):
+        v = [r["verdict_name"] for r in res]
+        feas = [r for r in res if r["verdict_name"] == "feasible"]
+        return {"verdicts": {k: v.count(k) for k in sorted(set(v))},
+                "sweeps_max": max(r["sweeps"] for r in res), "sweeps_sum": sum(r["sweeps"] for r in res),
+                "max_cap_rel_feasible": max((r["cap_rel"] for r in feas), default=None),
+                "max_cons_rel_feasible": max((r["cons_rel"] for r in feas), default=None),
+                "verdicts_as_constructed": sum(
+                    1 for r, w in zip(res, want)
+                    if w is not None and r["verdict_name"] == ("feasible" if w else "infeasible"))}
+
+    print(json.dumps({
+        "kind": "batched form to residual 1e-6", "workload": WORKLOAD, "instances": len(insts),
+        "precision": "FP32 sweeps, FP64 tail, FP64 residuals and certificate", "max_sweeps": max_sweeps,
+        "batch": {"s": tb, **summary(rb)}, "single_form_sequential": {"s": ts, **summary(rs)},
+        "speedup": ts / tb,
+        "same_verdicts": all(a["verdict"] == b["verdict"] for a, b in zip(rb, rs)),
+    }), flush=True)
+
+
 def bench_batch(args, insts, pdr, torch, stream):
     """The batched form against the single-instance form on the same GPU: the
     same instances, the same S sweeps each (Alg. 1 + Alg. 2, FP32), solved
@@ -477,8 +526,9 @@ def main():
             "grid100_k10000": lambda: instances.grid100_k10000(1.1, seed=0),
             "digraph20k_k2000": lambda: instances.digraph20k_k2000(1.05, seed=0),
             # a spawn pool, before any CUDA work in this process
-            "batch256": lambda: instances.batch256(seed=0, processes=os.cpu_count() or 1)}[args.workload]()
-    if args.sweeps <= 0:
+            "batch256": lambda: instances.batch256(seed=0, count=args.instances,
+                                                   processes=os.cpu_count() or 1)}[args.workload]()
+    if args.sweeps <= 0 and not args.to_residual:
         args.sweeps = 2000 if args.workload == "knn2500_k500" else 100
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
@@ -519,7 +569,10 @@ def main():
         compare_engines(args, inst, pdr, torch, stream)
         return
     if args.workload == "batch256":
-        bench_batch(args, inst, pdr, torch, stream)
+        if args.to_residual:
+            bench_batch_to_residual(args, inst, pdr, torch, stream)
+        else:
+            bench_batch(args, inst, pdr, torch, stream)
         return
     if args.adjoint:
         bench_adjoint(args, inst, pdr, torch, stream)

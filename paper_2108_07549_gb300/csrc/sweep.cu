@@ -542,7 +542,7 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? 2 : 1))) edge_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2) : 1))) edge_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
