@@ -347,8 +347,11 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_o
  * a conditional while loop whose body holds one chain of sweeps per
  * instance; the chains are independent, so the instances run concurrently.
  * Each instance stops by its own stop rules (a stopped instance's kernels
- * return at once); the loop ends when the last one stops.  Then each
- * instance's residuals and verdict are evaluated as by pdr_residuals.
+ * return at once); the loop ends when the last one stops.  With
+ * PDR_PREC_FP32_FP64TAIL a second launch then runs FP64 sweeps for the
+ * instances whose FP32 phase stopped on the objective rules (as pdr_solve
+ * does for one instance).  Then each instance's residuals and verdict are
+ * evaluated as by pdr_residuals.
  * results may be NULL, else it receives `count` results in input order.
  * Errors: PDR_ERR_CUDA, PDR_ERR_NUMERIC (some instance's objective became
  * non-finite). */

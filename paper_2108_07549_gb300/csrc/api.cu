@@ -536,6 +536,38 @@ fail:
     return PDR_OK;  // the host loop takes over
 }
 
+// The FP32 phase of PDR_PREC_FP32_FP64TAIL hands over to FP64 when it stopped
+// on the objective rules or stalled (not on the residual rule, the sweep
+// limit or a non-finite z).
+bool needs_fp64_tail(int reason)
+{
+    return reason == STOP_OBJECTIVE || reason == STOP_RELATIVE || reason == STOP_STALL;
+}
+
+// Moves the current FP32 state (flows; Alg. 3/4 rates and velocities) into
+// FP64 buffer 0 and makes FP64 the working precision.
+pdr_status widen_to_fp64(pdr_ctx* ctx)
+{
+    pdr_status s = ensure_fp64(ctx);
+    if (s != PDR_OK) return s;
+    CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
+    if (ctx->opt.algo != PDR_ALGO_ESO && ctx->m > 0) {
+        // learning rates (and velocities) follow the flows into FP64
+        CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta, ctx->m,
+                                     ctx->stream));
+        CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->theta, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        if (ctx->opt.algo == PDR_ALGO_GDM) {
+            s = ensure_velocity<double>(ctx);
+            if (s != PDR_OK) return s;
+            CK(launch_convert_f32_to_f64(ctx->v32[ctx->cur], ctx->v64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
+        }
+    }
+    ctx->cur = 0;
+    ctx->cur_prec = 1;
+    return refresh_psi<double>(ctx);
+}
+
 constexpr int64_t kPersistChunk = 1024;  // sweeps per persistent launch (even)
 
 // The persistent engine applies to Alg. 1 with a lane-group variant.
@@ -1419,27 +1451,8 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     if (s != PDR_OK) return s;
     if (ctx->cur_prec == 0) sweeps32 = ctx->hst->t;
     const int r = ctx->hst->reason;
-    if (tail && ctx->cur_prec == 0 && (r == STOP_OBJECTIVE || r == STOP_RELATIVE || r == STOP_STALL)) {
-        // FP64 tail from the FP32 flows
-        s = ensure_fp64(ctx);
-        if (s != PDR_OK) return s;
-        CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
-        if (ctx->opt.algo != PDR_ALGO_ESO && ctx->m > 0) {
-            // learning rates (and velocities) follow the flows into FP64
-            CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta,
-                                         ctx->m, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->theta, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice,
-                               ctx->stream));
-            if (ctx->opt.algo == PDR_ALGO_GDM) {
-                s = ensure_velocity<double>(ctx);
-                if (s != PDR_OK) return s;
-                CK(launch_convert_f32_to_f64(ctx->v32[ctx->cur], ctx->v64[0], (int64_t)ctx->m * ctx->Kp,
-                                             ctx->stream));
-            }
-        }
-        ctx->cur = 0;
-        ctx->cur_prec = 1;
-        s = refresh_psi<double>(ctx);
+    if (tail && ctx->cur_prec == 0 && needs_fp64_tail(r)) {
+        s = widen_to_fp64(ctx);
         if (s != PDR_OK) return s;
         s = init_state(ctx, false, 0);
         if (s != PDR_OK) return s;
@@ -1581,10 +1594,11 @@ struct pdr_batch {
     std::vector<int32_t> tuned_cfg;
     std::vector<double> tuned_us;
     unsigned int* active = nullptr;  // device counter of running instances
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int graph_prec = -1;
-    bool graph_tried = false, graph_ok = false;
+    // one graph per precision, over the instances it was captured for
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<char> graph_mask[2];
+    bool graph_tried[2] = {false, false}, graph_ok[2] = {false, false};
 };
 
 namespace {
@@ -1665,13 +1679,14 @@ pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
     return init_state(ctx, true, 0);
 }
 
-void batch_destroy_graph(pdr_batch* b)
+void batch_destroy_graph(pdr_batch* b, int p)
 {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    b->exec = nullptr;
-    b->graph = nullptr;
-    b->graph_tried = b->graph_ok = false;
+    if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+    if (b->graph[p]) cudaGraphDestroy(b->graph[p]);
+    b->exec[p] = nullptr;
+    b->graph[p] = nullptr;
+    b->graph_tried[p] = b->graph_ok[p] = false;
+    b->graph_mask[p].clear();
 }
 
 template <typename T>
@@ -1683,12 +1698,13 @@ SweepArgs<T> batch_args(pdr_batch* b, pdr_ctx* ctx, int use_cond, cudaGraphCondi
 }
 
 // One graph: a conditional while node whose body forks one branch per
-// instance (kBatchUnroll sweeps each) and joins them.
+// running instance (kBatchUnroll sweeps each) and joins them.
 template <typename T>
-void batch_build_graph(pdr_batch* b)
+void batch_build_graph(pdr_batch* b, const std::vector<char>& run)
 {
-    b->graph_tried = true;
-    b->graph_prec = Prec<T>::id;
+    const int p = Prec<T>::id;
+    b->graph_tried[p] = true;
+    b->graph_mask[p] = run;
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h;
     cudaGraphNode_t node;
@@ -1715,8 +1731,9 @@ void batch_build_graph(pdr_batch* b)
     {
         cudaError_t e = cudaEventRecord(ev[0], b->cap_stream);
         for (size_t p = 0; p < b->pool.size() && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(b->pool[p], ev[0], 0);
-        for (int32_t i = 0; i < b->count && e == cudaSuccess; ++i) {
-            cudaStream_t s = b->pool[i % b->pool.size()];
+        for (int32_t i = 0, r = 0; i < b->count && e == cudaSuccess; ++i) {
+            if (!run[i]) continue;
+            cudaStream_t s = b->pool[(r++) % b->pool.size()];
             for (int q = 0; q < kBatchUnroll && e == cudaSuccess; ++q) {
                 SweepArgs<T> a = batch_args<T>(b, b->ctx[i], 1, h, q & 1);
                 e = launch_excess<T>(a, s);
@@ -1732,51 +1749,59 @@ void batch_build_graph(pdr_batch* b)
     }
     if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) goto fail;
     for (auto& e : ev) cudaEventDestroy(e);
-    b->graph = g;
-    b->exec = exec;
-    b->graph_ok = true;
+    b->graph[p] = g;
+    b->exec[p] = exec;
+    b->graph_ok[p] = true;
     return;
 fail:
     cudaGetLastError();
     for (auto& e : ev)
         if (e) cudaEventDestroy(e);
     if (g) cudaGraphDestroy(g);
-    b->graph_ok = false;
+    b->graph_ok[p] = false;
 }
 
 __global__ void set_counter_kernel(unsigned int* c, unsigned int v) { *c = v; }
 
+// Alg. 1 in precision T for the instances with run[i] set, from the states
+// their callers initialised (instance i's sweep counter starting at
+// t_start[i]); the others keep their stopped state.
 template <typename T>
-pdr_status batch_run(pdr_batch* b)
+pdr_status batch_run(pdr_batch* b, const std::vector<char>& run, const std::vector<int64_t>& t_start)
 {
-    for (pdr_ctx* c : b->ctx) {
+    const int p = Prec<T>::id;
+    unsigned int running = 0;
+    for (int32_t i = 0; i < b->count; ++i) {
+        if (!run[i]) continue;
+        pdr_ctx* c = b->ctx[i];
         pdr_status s = ensure_velocity<T>(c);
         if (s != PDR_OK) return s;
         s = flows_to_buffer0<T>(c);
         if (s != PDR_OK) return s;
-        s = init_state(c, true, 0);
-        if (s != PDR_OK) return s;
+        ++running;
     }
-    set_counter_kernel<<<1, 1, 0, b->stream>>>(b->active, (unsigned int)b->count);
+    if (running == 0) return PDR_OK;
+    set_counter_kernel<<<1, 1, 0, b->stream>>>(b->active, running);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
     const bool use_graph = b->ctx[0]->opt.use_graph != 0;
-    if (use_graph && (!b->graph_tried || b->graph_prec != Prec<T>::id)) {
-        batch_destroy_graph(b);
-        batch_build_graph<T>(b);
+    if (use_graph && (!b->graph_tried[p] || b->graph_mask[p] != run)) {
+        batch_destroy_graph(b, p);
+        batch_build_graph<T>(b, run);
     }
-    if (use_graph && b->graph_ok) {
-        e = cudaGraphLaunch(b->exec, b->stream);
+    if (use_graph && b->graph_ok[p]) {
+        e = cudaGraphLaunch(b->exec[p], b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     } else {
-        // host loop: chunks of an even number of sweeps for every instance
+        // host loop: chunks of an even number of sweeps for every running instance
         for (;;) {
             for (int q = 0; q < 64; ++q)
-                for (pdr_ctx* c : b->ctx) {
-                    SweepArgs<T> a = batch_args<T>(b, c, 0, 0, q & 1);
+                for (int32_t i = 0; i < b->count; ++i) {
+                    if (!run[i]) continue;
+                    SweepArgs<T> a = batch_args<T>(b, b->ctx[i], 0, 0, q & 1);
                     launch_excess<T>(a, b->stream);
-                    launch_update<T>(c, a, b->stream);
+                    launch_update<T>(b->ctx[i], a, b->stream);
                 }
             unsigned int left = 0;
             e = cudaMemcpyAsync(&left, b->active, sizeof(left), cudaMemcpyDeviceToHost, b->stream);
@@ -1785,10 +1810,12 @@ pdr_status batch_run(pdr_batch* b)
             if (left == 0) break;
         }
     }
-    for (pdr_ctx* c : b->ctx) {
+    for (int32_t i = 0; i < b->count; ++i) {
+        if (!run[i]) continue;
+        pdr_ctx* c = b->ctx[i];
         pdr_status s = read_state(c);
         if (s != PDR_OK) return s;
-        c->cur = (int)(c->hst->t & 1);
+        c->cur = (int)((c->hst->t - t_start[i]) & 1);
     }
     return PDR_OK;
 }
@@ -1807,8 +1834,6 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance* inst, const pdr_o
     pdr_options o;
     fill_defaults(&o);
     if (opt) o = *opt;
-    if (o.precision == PDR_PREC_FP32_FP64TAIL)
-        return batch_fail(PDR_ERR_UNSUPPORTED, "the batched form runs PDR_PREC_FP32 or PDR_PREC_FP64");
     {
         std::string why;
         if (!options_ok(&o, &why)) return batch_fail(PDR_ERR_INVALID_ARG, why);
@@ -1868,15 +1893,57 @@ pdr_status pdr_batch_solve(pdr_batch* b, pdr_result* results)
 {
     if (!b) return PDR_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
-    pdr_status s = b->ctx[0]->cur_prec ? batch_run<double>(b) : batch_run<float>(b);
+    const int32_t B = b->count;
+    const bool tail = b->ctx[0]->opt.precision == PDR_PREC_FP32_FP64TAIL;
+    std::vector<char> run32(B, 0), run64(B, 0);
+    std::vector<int64_t> t_start(B, 0), sweeps32(B, 0);
+    pdr_status s = PDR_OK;
+    // every instance starts a fresh solve from its current flows, as pdr_solve
+    for (int32_t i = 0; i < B; ++i) {
+        pdr_ctx* c = b->ctx[i];
+        s = init_state(c, true, (tail && c->cur_prec == 0) ? 1 : 0);
+        if (s != PDR_OK) return s;
+        (c->cur_prec ? run64 : run32)[i] = 1;
+    }
+    s = batch_run<float>(b, run32, t_start);
+    if (s != PDR_OK) return s;
+    if (tail) {
+        // instances whose FP32 phase stopped on the objective rules continue in FP64
+        bool any = false;
+        for (int32_t i = 0; i < B; ++i) {
+            pdr_ctx* c = b->ctx[i];
+            if (!run32[i]) continue;
+            s = read_state(c);
+            if (s != PDR_OK) return s;
+            sweeps32[i] = c->hst->t;
+            if (needs_fp64_tail(c->hst->reason)) {
+                s = widen_to_fp64(c);
+                if (s != PDR_OK) return s;
+                s = init_state(c, false, 0);
+                if (s != PDR_OK) return s;
+                t_start[i] = c->hst->t;
+                run64[i] = 1;
+            }
+            any = any || run64[i];
+        }
+        for (int32_t i = 0; i < B && !any; ++i) any = run64[i];
+        if (any)
+            for (pdr_ctx* c : b->ctx) {  // stable device pointers for the FP64 graph
+                s = ensure_fp64(c);
+                if (s != PDR_OK) return s;
+            }
+    }
+    s = batch_run<double>(b, run64, t_start);
     if (s != PDR_OK) return s;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     bool numeric = false;
     for (int32_t i = 0; i < b->count; ++i) {
         pdr_ctx* c = b->ctx[i];
+        s = read_state(c);
+        if (s != PDR_OK) return s;
         pdr_result r{};
         r.sweeps = c->hst->t;
-        r.sweeps_fp64 = c->cur_prec ? c->hst->t : 0;
+        r.sweeps_fp64 = c->cur_prec ? c->hst->t - sweeps32[i] : 0;
         r.dz = c->hst->dz;
         r.stop_reason = c->hst->reason;
         s = residuals_into(c, &r);
@@ -1921,7 +1988,8 @@ void pdr_batch_destroy(pdr_batch* b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    batch_destroy_graph(b);
+    batch_destroy_graph(b, 0);
+    batch_destroy_graph(b, 1);
     for (pdr_ctx* c : b->ctx) pdr_destroy(c);
     for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);

@@ -140,8 +140,9 @@ def test_batch_create_rejects_invalid_instances(lib):
     assert lib.pdr_batch_create(0, arr, None, None, C.byref(h)) == 1
     assert lib.pdr_batch_create(2, arr, None, None, C.byref(h)) == 1
     assert "instance 1" in lib.pdr_last_error(None).decode() and "self-loop" in lib.pdr_last_error(None).decode()
-    o = pdr.default_options(precision=pdr.PREC_FP32_FP64TAIL)
-    assert lib.pdr_batch_create(1, arr, C.byref(o), None, C.byref(h)) == 6
+    o = pdr.default_options(precision=7)
+    assert lib.pdr_batch_create(1, arr, C.byref(o), None, C.byref(h)) == 1
+    assert "precision" in lib.pdr_last_error(None).decode()
     assert not h.value
 
 

@@ -104,3 +104,27 @@ def test_batch_host_loop_matches_graph(pdr):
             out.append(B.solve())
     for x, y in zip(*out):
         assert x["verdict"] == y["verdict"] and abs(x["sweeps"] - y["sweeps"]) <= 2
+
+
+def test_batch_fp64_tail_matches_single_solves(pdr):
+    """PDR_PREC_FP32_FP64TAIL in the batch: FP32 sweeps for every instance,
+    then FP64 sweeps for the instances whose FP32 phase stopped on the
+    objective rules, each from its own FP32 flows, exactly as pdr_solve."""
+    insts = uneven_batch(seed=23, count=8)
+    opts = dict(precision=pdr.PREC_FP32_FP64TAIL, eps_obj=0.0, resid_tol=1e-6, eps_rel=1e-13, max_sweeps=600000)
+    with pdr.Batch(insts, **opts) as B:
+        res = B.solve()
+        flows = [B.solver(i).flows() for i in range(len(insts))]
+        again = B.solve()  # resumes: FP64 instances stay in FP64
+    for inst, r, f, r2 in zip(insts, res, flows, again):
+        want = inst.feasible_by_construction
+        if want is not None:
+            assert r["verdict"] == (pdr.VERDICT_FEASIBLE if want else pdr.VERDICT_INFEASIBLE), (inst.name, r)
+        with pdr.Solver.from_instance(inst, **opts) as s:
+            r1 = s.solve()
+        assert r["verdict"] == r1["verdict"], (inst.name, r, r1)
+        assert (r["sweeps_fp64"] > 0) == (r1["sweeps_fp64"] > 0), (inst.name, r, r1)
+        if r["verdict"] == pdr.VERDICT_FEASIBLE:
+            ref = oracle.Problem.from_instance(inst).residuals(f)
+            assert ref["cap_rel"] <= 1e-6 and ref["cons_rel"] <= 1e-6
+        assert r2["verdict"] == r["verdict"]
