@@ -542,7 +542,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2108_07549_gb300 import build, pdr
+    from paper_2108_07549_gb300 import build, pdr, replicas
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -613,12 +613,8 @@ def main():
             torch.cuda.synchronize()
         times = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         barrier()
-    ms_step = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * m * K * S / (ms_step / 1e3)
+    ms_step = replicas.slowest(sum(times) / len(times), world, device="cuda")
+    value = replicas.job_throughput(m * K * S, ms_step / 1e3, world)
     # S + 1 objective evaluations (the last one stops); the graph body holds 8
     # sweeps (two kernels each), the host loop launches chunks of 256 sweeps;
     # plus residuals (3), solve state init (1), reset (psi refresh + state init)
@@ -648,12 +644,8 @@ def main():
             t1 = time.perf_counter()
             if q >= max(1, args.warmup):
                 e2e_times.append(t1 - t0)
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * m * K * S / e2e_s
+    e2e_s = replicas.slowest(sum(e2e_times) / len(e2e_times), world, device="cuda")
+    e2e_value = replicas.job_throughput(m * K * S, e2e_s, world)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -708,7 +700,8 @@ def main():
                                         "frac": b_dom / (t_dom_c / 1e3) / 1e9 / peak}}
         # time to the paper's stop rule (|z^(t) - z^(t-1)| < 1e-6) from f = 0
         if args.workload != "knn2500_k500":
-            line["cpu_baseline"] = cpu_baseline(inst, budget_s=12.0)
+            if world == 1:
+                line["cpu_baseline"] = cpu_baseline(inst, budget_s=12.0)
             solver.close()
             print(json.dumps(line), flush=True)
             return
@@ -719,7 +712,8 @@ def main():
         line["time_to_eps"] = {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"],
                                "ms": rr["ms_total"], "z": rr["z"], "cap_rel": rr["cap_rel"],
                                "cons_rel": rr["cons_rel"], "verdict": rr["verdict_name"]}
-        line["cpu_baseline"] = cpu_baseline(inst)
+        if world == 1:  # the host cores are shared by the ranks of a multi-GPU run
+            line["cpu_baseline"] = cpu_baseline(inst)
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
