@@ -20,24 +20,43 @@
 namespace pdr {
 namespace {
 
+// All row accesses are vectors of 16 bytes (float4 / double2): rows are
+// padded to Kp, a multiple of the vector width, and the padding stays 0.
+
 // Warp per edge: seeds dL/df = psi + h_j - h_i and dL/du = -psi at f^(T).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) seed_edge_kernel(SweepArgs<T> a, T* __restrict__ fbar,
                                                              double* __restrict__ ubar)
 {
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
     const int lane = threadIdx.x & 31;
+    const int vpr = a.Kp / N;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t e = w0; e < a.m; e += nw) {
-        const T* fr = a.f + e * a.Kp;
+        const VT* fr = reinterpret_cast<const VT*>(a.f + e * a.Kp);
         T s = T(0);
-        for (int k = lane; k < a.K; k += 32) s += fr[k];
+        for (int v = lane; v < vpr; v += 32) {
+            T x[N];
+            unpack(fr[v], x);
+#pragma unroll
+            for (int j = 0; j < N; ++j) s += x[j];
+        }
         s = group_sum<32>(s);
         const T over = s - a.u[e];
         const T psi = over > T(0) ? over : T(0);
-        const T* hi = a.h + (int64_t)a.src[e] * a.Kp;
-        const T* hj = a.h + (int64_t)a.col[e] * a.Kp;
-        for (int k = lane; k < a.Kp; k += 32) fbar[e * a.Kp + k] = k < a.K ? psi + hj[k] - hi[k] : T(0);
+        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
+        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
+        VT* out = reinterpret_cast<VT*>(fbar + e * a.Kp);
+        for (int v = lane; v < vpr; v += 32) {
+            T x[N], y[N], o[N];
+            unpack(hi[v], x);
+            unpack(hj[v], y);
+#pragma unroll
+            for (int j = 0; j < N; ++j) o[j] = v * N + j < a.K ? psi + y[j] - x[j] : T(0);
+            out[v] = pack4(o);
+        }
         if (lane == 0) ubar[e] = -(double)psi;
     }
 }
@@ -53,78 +72,140 @@ __global__ void demand_kernel(SweepArgs<T> a, const T* __restrict__ x, double* _
 }
 
 // Warp per edge: Alg. 2's Jacobian applied to fbar (see the file comment).
+// The row is read twice (the second pass from L1/L2), so any K works.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a, const T* __restrict__ theta,
                                                                  const T* __restrict__ fbar, T* __restrict__ cbar,
                                                                  double* __restrict__ ubar)
 {
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
     const int lane = threadIdx.x & 31;
+    const int vpr = a.Kp / N;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t e = w0; e < a.m; e += nw) {
         const T th = theta[e];
         const bool congested = th > T(0);
         const T cut = congested ? th : T(0);
-        const T* fr = a.f + e * a.Kp;
-        const T* hi = a.h + (int64_t)a.src[e] * a.Kp;
-        const T* hj = a.h + (int64_t)a.col[e] * a.Kp;
-        const T* fb = fbar + e * a.Kp;
+        const VT* fr = reinterpret_cast<const VT*>(a.f + e * a.Kp);
+        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
+        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
+        const VT* fb = reinterpret_cast<const VT*>(fbar + e * a.Kp);
         T sb = T(0);
         int na = 0;
-        for (int k = lane; k < a.K; k += 32) {
-            const T c = fma(T(0.5), hi[k] - hj[k], fr[k]);  // the same c as the edge-QP kernel
-            if (c > cut) {
-                sb += fb[k];
-                ++na;
+        for (int v = lane; v < vpr; v += 32) {
+            T f[N], x[N], y[N], g[N];
+            unpack(fr[v], f);
+            unpack(hi[v], x);
+            unpack(hj[v], y);
+            unpack(fb[v], g);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T c = fma(T(0.5), x[j] - y[j], f[j]);  // the same c as the edge-QP kernel
+                if (c > cut) {
+                    sb += g[j];
+                    ++na;
+                }
             }
         }
         sb = group_sum<32>(sb);
         na = group_sum<32>(na);
         const T corr = congested ? sb / T(2 + na) : T(0);
-        for (int k = lane; k < a.Kp; k += 32) {
-            T out = T(0);
-            if (k < a.K) {
-                const T c = fma(T(0.5), hi[k] - hj[k], fr[k]);
-                out = c > cut ? fb[k] - corr : T(0);
+        VT* out = reinterpret_cast<VT*>(cbar + e * a.Kp);
+        for (int v = lane; v < vpr; v += 32) {
+            T f[N], x[N], y[N], g[N], o[N];
+            unpack(fr[v], f);
+            unpack(hi[v], x);
+            unpack(hj[v], y);
+            unpack(fb[v], g);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T c = fma(T(0.5), x[j] - y[j], f[j]);
+                o[j] = c > cut ? g[j] - corr : T(0);
             }
-            cbar[e * a.Kp + k] = out;
+            out[v] = pack4(o);
         }
         if (lane == 0) ubar[e] += (double)corr;
     }
 }
 
-// Thread per (vertex, k): Dbar = (sum_out cbar - sum_in cbar) / (2 delta).
+// Thread per (vertex, vector): Dbar = (sum_out cbar - sum_in cbar) / (2 delta),
+// the incidence list traversed in its stored order as by the excess kernel.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) vertex_backward_kernel(SweepArgs<T> a, const T* __restrict__ cbar,
                                                                    T* __restrict__ Dbar)
 {
-    const int64_t total = (int64_t)a.n * a.Kp;
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    const int64_t vpr = a.Kp / N;
+    const int64_t total = (int64_t)a.n * vpr;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)(idx / a.Kp);
-        const int32_t k = (int32_t)(idx - (int64_t)i * a.Kp);
-        T acc = T(0);
-        for (int64_t q = a.inc_ptr[i]; q < a.inc_ptr[i + 1]; ++q) {
-            const int32_t ev = a.inc[q];
+        const int32_t i = (int32_t)(idx / vpr);
+        const int64_t v = idx - (int64_t)i * vpr;
+        T acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = T(0);
+        const int64_t q1 = a.inc_ptr[i + 1];
+        int64_t q = a.inc_ptr[i];
+        for (; q + 4 <= q1; q += 4) {  // four rows in flight
+            int32_t ev[4];
+            T x[4][N];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ev[u] = a.inc[q + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = ev[u] >= 0 ? ev[u] : ~ev[u];
+                unpack(reinterpret_cast<const VT*>(cbar + e * a.Kp)[v], x[u]);
+            }
             // in-edges (ev >= 0) took -h_j/2, out-edges (~e) took +h_i/2
-            if (ev >= 0) acc -= cbar[(int64_t)ev * a.Kp + k];
-            else acc += cbar[(int64_t)(~ev) * a.Kp + k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] = ev[u] >= 0 ? acc[j] - x[u][j] : acc[j] + x[u][j];
         }
-        Dbar[idx] = T(0.5) * acc * a.inv_deg[i];
+        for (; q < q1; ++q) {
+            const int32_t ev = a.inc[q];
+            const int64_t e = ev >= 0 ? ev : ~ev;
+            T x[N];
+            unpack(reinterpret_cast<const VT*>(cbar + e * a.Kp)[v], x);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = ev >= 0 ? acc[j] - x[j] : acc[j] + x[j];
+        }
+        const T s = T(0.5) * a.inv_deg[i];
+        T o[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) o[j] = acc[j] * s;
+        reinterpret_cast<VT*>(Dbar + (int64_t)i * a.Kp)[v] = pack4(o);
     }
 }
 
-// Thread per (edge, k): dL/df^(t) = cbar + Dbar_j - Dbar_i.
+// Warp per edge: dL/df^(t) = cbar + Dbar_j - Dbar_i.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) edge_adjoint_kernel(SweepArgs<T> a, const T* __restrict__ cbar,
                                                                 const T* __restrict__ Dbar, T* __restrict__ fbar)
 {
-    const int64_t total = a.m * a.Kp;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = idx / a.Kp;
-        const int32_t k = (int32_t)(idx - e * a.Kp);
-        fbar[idx] = cbar[idx] + Dbar[(int64_t)a.col[e] * a.Kp + k] - Dbar[(int64_t)a.src[e] * a.Kp + k];
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    const int lane = threadIdx.x & 31;
+    const int vpr = a.Kp / N;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = w0; e < a.m; e += nw) {
+        const VT* cb = reinterpret_cast<const VT*>(cbar + e * a.Kp);
+        const VT* di = reinterpret_cast<const VT*>(Dbar + (int64_t)a.src[e] * a.Kp);
+        const VT* dj = reinterpret_cast<const VT*>(Dbar + (int64_t)a.col[e] * a.Kp);
+        VT* out = reinterpret_cast<VT*>(fbar + e * a.Kp);
+        for (int v = lane; v < vpr; v += 32) {
+            T c[N], x[N], y[N], o[N];
+            unpack(cb[v], c);
+            unpack(di[v], x);
+            unpack(dj[v], y);
+#pragma unroll
+            for (int j = 0; j < N; ++j) o[j] = c[j] + y[j] - x[j];
+            out[v] = pack4(o);
+        }
     }
 }
 
@@ -151,9 +232,10 @@ cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar
                                   double* dbar, int num_sms, cudaStream_t s)
 {
     edge_backward_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, theta, fbar, cbar, ubar);
-    vertex_backward_kernel<T><<<blocks((int64_t)a.n * a.Kp, kThreads, num_sms), kThreads, 0, s>>>(a, cbar, Dbar);
+    vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
+        a, cbar, Dbar);
     demand_kernel<T><<<blocks(a.K, kThreads, num_sms), kThreads, 0, s>>>(a, Dbar, dbar, 1);
-    edge_adjoint_kernel<T><<<blocks(a.m * a.Kp, kThreads, num_sms), kThreads, 0, s>>>(a, cbar, Dbar, fbar);
+    edge_adjoint_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, cbar, Dbar, fbar);
     return cudaGetLastError();
 }
 
