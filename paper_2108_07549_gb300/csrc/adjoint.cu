@@ -72,16 +72,19 @@ __global__ void demand_kernel(SweepArgs<T> a, const T* __restrict__ x, double* _
 }
 
 // Warp per edge: Alg. 2's Jacobian applied to fbar (see the file comment).
-// The row is read twice (the second pass from L1/L2), so any K works.
+// Pass 1 decides every element's membership of the active set (c > cut)
+// from f and both height rows and records it as warp ballots in `mask`
+// (N words per 32 vectors of the row); pass 2 then re-reads only fbar.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a, const T* __restrict__ theta,
                                                                  const T* __restrict__ fbar, T* __restrict__ cbar,
-                                                                 double* __restrict__ ubar)
+                                                                 double* __restrict__ ubar, uint32_t* __restrict__ mask)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
     const int lane = threadIdx.x & 31;
     const int vpr = a.Kp / N;
+    const int nq = (vpr + 31) / 32;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t e = w0; e < a.m; e += nw) {
@@ -92,38 +95,42 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
         const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
         const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
         const VT* fb = reinterpret_cast<const VT*>(fbar + e * a.Kp);
+        uint32_t* me = mask + e * (int64_t)nq * N;
         T sb = T(0);
         int na = 0;
-        for (int v = lane; v < vpr; v += 32) {
-            T f[N], x[N], y[N], g[N];
-            unpack(fr[v], f);
-            unpack(hi[v], x);
-            unpack(hj[v], y);
-            unpack(fb[v], g);
+        for (int q = 0; q < nq; ++q) {  // every lane takes every round: the ballots need the whole warp
+            const int v = q * 32 + lane;
+            const bool live = v < vpr;
+            T f[N] = {}, x[N] = {}, y[N] = {}, g[N] = {};
+            if (live) {
+                unpack(fr[v], f);
+                unpack(hi[v], x);
+                unpack(hj[v], y);
+                unpack(fb[v], g);
+            }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const T c = fma(T(0.5), x[j] - y[j], f[j]);  // the same c as the edge-QP kernel
-                if (c > cut) {
+                const bool act = live && fma(T(0.5), x[j] - y[j], f[j]) > cut;  // the edge-QP kernel's c
+                if (act) {
                     sb += g[j];
                     ++na;
                 }
+                const uint32_t b = __ballot_sync(kFull, act);
+                if (lane == j) me[q * N + j] = b;
             }
         }
+        __syncwarp();  // the ballots written above are read by every lane below
         sb = group_sum<32>(sb);
         na = group_sum<32>(na);
         const T corr = congested ? sb / T(2 + na) : T(0);
         VT* out = reinterpret_cast<VT*>(cbar + e * a.Kp);
-        for (int v = lane; v < vpr; v += 32) {
-            T f[N], x[N], y[N], g[N], o[N];
-            unpack(fr[v], f);
-            unpack(hi[v], x);
-            unpack(hj[v], y);
+        for (int q = 0; q < nq; ++q) {
+            const int v = q * 32 + lane;
+            if (v >= vpr) continue;
+            T g[N], o[N];
             unpack(fb[v], g);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const T c = fma(T(0.5), x[j] - y[j], f[j]);
-                o[j] = c > cut ? g[j] - corr : T(0);
-            }
+            for (int j = 0; j < N; ++j) o[j] = ((me[q * N + j] >> lane) & 1u) ? g[j] - corr : T(0);
             out[v] = pack4(o);
         }
         if (lane == 0) ubar[e] += (double)corr;
@@ -229,9 +236,10 @@ cudaError_t launch_seed(const SweepArgs<T>& a, T* fbar, double* ubar, double* db
 
 template <typename T>
 cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar, T* cbar, T* Dbar, double* ubar,
-                                  double* dbar, int num_sms, cudaStream_t s)
+                                  double* dbar, uint32_t* mask, int num_sms, cudaStream_t s)
 {
-    edge_backward_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, theta, fbar, cbar, ubar);
+    edge_backward_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, theta, fbar, cbar, ubar,
+                                                                                       mask);
     vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
         a, cbar, Dbar);
     demand_kernel<T><<<blocks(a.K, kThreads, num_sms), kThreads, 0, s>>>(a, Dbar, dbar, 1);
@@ -242,8 +250,8 @@ cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar
 template cudaError_t launch_seed<float>(const SweepArgs<float>&, float*, double*, double*, int, cudaStream_t);
 template cudaError_t launch_seed<double>(const SweepArgs<double>&, double*, double*, double*, int, cudaStream_t);
 template cudaError_t launch_backward_sweep<float>(const SweepArgs<float>&, const float*, float*, float*, float*,
-                                                  double*, double*, int, cudaStream_t);
+                                                  double*, double*, uint32_t*, int, cudaStream_t);
 template cudaError_t launch_backward_sweep<double>(const SweepArgs<double>&, const double*, double*, double*,
-                                                   double*, double*, double*, int, cudaStream_t);
+                                                   double*, double*, double*, uint32_t*, int, cudaStream_t);
 
 }  // namespace pdr

@@ -797,6 +797,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         if (!(q = (T*)grab(sizeof(T) * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
     T *fbar = nullptr, *cbar = nullptr, *Dbar = nullptr;
     double *ubar = nullptr, *dbar = nullptr;
+    uint32_t* mask = nullptr;
     if (grads) {
         seg.resize(C + 1);
         th.resize(C);
@@ -809,7 +810,9 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         Dbar = (T*)grab(sizeof(T) * hn);
         ubar = (double*)grab(sizeof(double) * mm);
         dbar = (double*)grab(sizeof(double) * ctx->K);
-        if (!fbar || !cbar || !Dbar || !ubar || !dbar) return cleanup(), ctx->fail(PDR_ERR_OOM, "adjoint allocation failed");
+        mask = (uint32_t*)grab(sizeof(uint32_t) * mm * backward_mask_words(ctx->Kp, 16 / sizeof(T)));
+        if (!fbar || !cbar || !Dbar || !ubar || !dbar || !mask)
+            return cleanup(), ctx->fail(PDR_ERR_OOM, "adjoint allocation failed");
     }
     // forward from f = 0 (pdr_backward reset the flows), cold roots
     T* theta = reinterpret_cast<T*>(ctx->theta);
@@ -850,7 +853,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
             a.f = seg[t - t0];
             CKB(launch_excess<T>(a, ctx->stream));  // h^(t)
-            CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, ctx->num_sms, ctx->stream));
+            CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, mask, ctx->num_sms, ctx->stream));
         }
     }
     if (grad_u && ctx->m > 0)
