@@ -267,6 +267,7 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.grid_e = ctx->grid_e[p];
     a.n_psi = ctx->n_psi[p];
     a.pf_edges = ctx->pf[p];
+    a.l2_hints = ctx->pf[p] > 0 ? 1 : 0;
     a.psi_out = nullptr;
     a.st = ctx->st;
     a.trace = ctx->trace;

@@ -112,6 +112,7 @@ struct SweepArgs {
     int64_t n_psi;      // number of edge partials
     int64_t pf_edges;   // edge QP: L2 prefetch of the rows of edge e + pf_edges while
                         // edge e is solved (about one wave of resident edges ahead; 0: off)
+    int l2_hints;       // 1: the working set exceeds L2; the edge QP streams flow rows evict-first
     // Alg. 3 / Alg. 4 state (double-buffered like the flows) and parameters
     const T* beta_in;   // [m] learning rates beta_ij of iteration t
     T* beta_out;        // [m] learning rates of iteration t+1

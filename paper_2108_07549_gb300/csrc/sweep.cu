@@ -558,6 +558,8 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
     }
     const int vpr = a.Kp / N;
     const bool psi_only = (a.mode == MODE_PSI);
+    const bool hint = a.l2_hints != 0;
+    const uint64_t pol_first = l2_evict_first();
     typename A::V zpsi = A::zero();
     T capmax = T(0);
     for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x - 1) {
@@ -580,7 +582,8 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
             const int v = threadIdx.x + q * B;
             if (v < vpr) {
                 T fx[N];
-                unpack(reinterpret_cast<const VT*>(frow)[v], fx);
+                if (hint) unpack(ld_hint(reinterpret_cast<const VT*>(frow) + v, pol_first), fx);
+                else unpack(reinterpret_cast<const VT*>(frow)[v], fx);
                 if (psi_only) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) c[q][j] = fx[j];
@@ -634,7 +637,10 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
                     const T x = c[q][j] - theta;
                     o[j] = x > T(0) ? x : T(0);
                 }
-                if (v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
+                if (v < vpr) {
+                    if (hint) st_hint(reinterpret_cast<VT*>(orow) + v, pack4(o), pol_first);
+                    else reinterpret_cast<VT*>(orow)[v] = pack4(o);
+                }
             }
             psi = T(2) * theta;  // sum f' - u at the root
         } else {

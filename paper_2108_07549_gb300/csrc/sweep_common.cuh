@@ -51,6 +51,44 @@ __device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes, int ti
         asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
 }
 
+// L2 eviction priority for working sets larger than L2: the flow rows stream
+// through the edge kernel once (evict first), so that they do not push out
+// the height rows, which every edge at a vertex gathers.  The policy comes
+// from createpolicy; loads go through the read-only path.  (Marking the
+// heights evict-last instead left such lines behind after a solve and slowed
+// the kernels that ran next.)
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float4 ld_hint(const float4* p, uint64_t pol)
+{
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol)
+{
+    double2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // Sum over the G lanes of an aligned lane group (xor offsets below G stay
 // inside the group).  Every lane of the warp must call it.  IEEE addition is
 // commutative, so every lane of the group ends with the same value.
