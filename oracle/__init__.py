@@ -122,6 +122,12 @@ def _load():
             lib.orc_residuals_at.restype = None
             lib.orc_solve_eso.argtypes = [P, C.POINTER(_Options), vp, C.POINTER(_Report), vp, C.c_int64]
             lib.orc_solve_eso.restype = C.c_int32
+            lib.orc_edge_ck.argtypes = [C.c_int32, vp, vp, vp, C.c_double, vp, C.POINTER(C.c_double), vp, vp]
+            lib.orc_edge_ck.restype = C.c_int32
+            lib.orc_ck_all.argtypes = [P, vp, vp, vp, vp]
+            lib.orc_ck_all.restype = C.c_int64
+            lib.orc_solve_ck.argtypes = [P, C.POINTER(_Options), vp, C.POINTER(_Report), vp, C.c_int64]
+            lib.orc_solve_ck.restype = C.c_int32
             G = C.POINTER(_GDParams)
             lib.orc_gd_edge.argtypes = [G, C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp,
                                         C.POINTER(C.c_double), C.c_int64, vp, C.POINTER(C.c_double)]
@@ -244,6 +250,36 @@ class Problem:
         _, h = self.excess(f)
         return self.qp_all(h, f)[0]
 
+    def ck_all(self, h, f):
+        """(f_next, g, fallbacks): the capacity-kept step of Program (6) on every edge from heights h."""
+        f = self._f(f)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        f_next = np.empty_like(f)
+        g = np.empty(self.m)
+        fb = _load().orc_ck_all(C.byref(self._c), _ptr(h), _ptr(f), _ptr(f_next), _ptr(g))
+        return f_next, g, int(fb)
+
+    def ck_sweep(self, f):
+        """One capacity-kept iteration without the stop test: f^(t) -> f^(t+1)."""
+        _, h = self.excess(f)
+        return self.ck_all(h, f)[0]
+
+    def solve_ck(self, max_sweeps=100000, eps_obj=1e-6, resid_tol=0.0, f0=None, trace=False):
+        """Alg. 1 with the capacity-kept step (Program (6)) from f0 (default 0).
+        Returns (f, report dict[, ztrace])."""
+        f = np.zeros((self.m, self.K)) if f0 is None else self._f(f0).copy()
+        opt = _Options(int(max_sweeps), float(eps_obj), float(resid_tol))
+        rep = _Report()
+        zt = np.full(int(max_sweeps) + 1, np.nan) if trace else None
+        rc = _load().orc_solve_ck(C.byref(self._c), C.byref(opt), _ptr(f), C.byref(rep),
+                                  _ptr(zt) if trace else None, int(max_sweeps) + 1 if trace else 0)
+        if rc != 0:
+            raise MemoryError("oracle solve failed to allocate")
+        out = {k: getattr(rep, k) for k, _ in _Report._fields_}
+        if trace:
+            return f, out, zt[: out["sweeps"] + 1]
+        return f, out
+
     def residuals(self, f, tol=1e-6):
         """eq. (1) residuals, Farkas margin and verdict at flows f (dict)."""
         f = self._f(f)
@@ -336,6 +372,20 @@ def gd_edge(params: dict, hi, hj, psi, u, f, v, beta, t):
     acc = _load().orc_gd_edge(C.byref(g), K, _ptr(hi), _ptr(hj), float(psi), float(u), _ptr(f), _ptr(v),
                               C.byref(b), int(t), _ptr(df), C.byref(dz))
     return f, v, b.value, bool(acc), dz.value
+
+
+def edge_ck(hi, hj, f, u):
+    """The capacity-kept step of Program (6) on one edge: returns (f_new, g, used_fallback)."""
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    hj = np.ascontiguousarray(hj, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    K = int(f.shape[0])
+    out = np.empty(K)
+    c = np.empty(max(K, 1))
+    pos = np.empty(max(K, 1))
+    g = C.c_double()
+    fb = _load().orc_edge_ck(K, _ptr(hi), _ptr(hj), _ptr(f), float(u), _ptr(out), C.byref(g), _ptr(c), _ptr(pos))
+    return out, g.value, bool(fb)
 
 
 def edge_qp(hi, hj, f, u):

@@ -333,6 +333,96 @@ int64_t orc_qp_all(const orc_problem *P, const double *h, const double *f, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Capacity kept: Program (6) ("Further Discussion on Optimality Condition") */
+/* ------------------------------------------------------------------------ */
+
+/* Program (6) keeps the capacity constraint sum_k f_ij,k <= u_ij and
+ * minimises only the height part of the objective, sum_i,k of the integral
+ * of h_ik, i.e. 1/2 sum_i,k delta_i h_ik^2 for h = Delta/delta.  The paper
+ * gives its KKT conditions (a pipe pressure gamma_ij >= 0 per edge) but no
+ * algorithm.  Reading: Alg. 1 with the capacity kept in the local step.
+ * Every edge replaces its flows by the minimiser of sum_k (f'_k - c_k)^2
+ * over {f' >= 0, sum_k f'_k <= u_ij}, with Alg. 2's c_k = f_k + (h_ik -
+ * h_jk)/2; that is eq. (10) with its congestion term replaced by the kept
+ * constraint, and it is the Euclidean projection of c onto that set:
+ *   f'_k = max(0, c_k - g),  g = 0 if sum_k max(0, c_k) <= u, else the
+ *   g > 0 with sum_k max(0, c_k - g) = u.
+ * As in Alg. 2, the positive c_k are sorted in descending order and g is
+ * the candidate g_p = (sum_{q <= p} c_(q) - u) / p that lies in
+ * [c_(p+1), c_(p)] (c_(mp+1) = 0).  A fixed point satisfies the KKT
+ * conditions (i)-(iii) of that section with pipe pressure 2g.
+ * Returns 1 when rounding made every interval test fail and g was taken as
+ * the largest candidate with c_(p) - g_p >= 0. */
+int32_t orc_edge_ck(int32_t K, const double *hi, const double *hj, const double *f, double u, double *f_new,
+                    double *g_out, double *c, double *pos)
+{
+    for (int32_t k = 0; k < K; ++k) c[k] = 0.5 * ((hi[k] + f[k]) - (hj[k] - f[k]));
+    double s = 0.0;
+    for (int32_t k = 0; k < K; ++k)
+        if (c[k] > 0.0) s += c[k];
+    double g = 0.0;
+    int32_t fallback = 0;
+    if (s > u) {
+        int32_t mp = 0;
+        for (int32_t k = 0; k < K; ++k)
+            if (c[k] > 0.0) pos[mp++] = c[k];
+        qsort(pos, (size_t)mp, sizeof(double), cmp_desc);
+        double sum_c = 0.0;
+        int32_t found = 0;
+        for (int32_t p = 1; p <= mp; ++p) {
+            sum_c += pos[p - 1];
+            const double cand = (sum_c - u) / (double)p;
+            const double lower = (p < mp) ? pos[p] : 0.0;
+            if (lower <= cand && cand <= pos[p - 1]) {
+                g = cand;
+                found = 1;
+                break;
+            }
+        }
+        if (!found) {
+            fallback = 1;
+            sum_c = 0.0;
+            for (int32_t p = 1; p <= mp; ++p) {
+                sum_c += pos[p - 1];
+                const double cand = (sum_c - u) / (double)p;
+                if (pos[p - 1] - cand >= 0.0) g = cand;
+            }
+        }
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        const double v = c[k] - g;
+        f_new[k] = v > 0.0 ? v : 0.0;
+    }
+    if (g_out) *g_out = g;
+    return fallback;
+}
+
+/* The capacity-kept step for every edge from the same heights h^(t)
+ * (Jacobi, as orc_qp_all).  g_new, if not NULL, receives each edge's g.
+ * Returns the number of edges that needed the fallback. */
+int64_t orc_ck_all(const orc_problem *P, const double *h, const double *f, double *f_new, double *g_new)
+{
+    const int64_t m = P->m;
+    const int32_t K = P->K;
+    int64_t fallbacks = 0;
+#pragma omp parallel reduction(+ : fallbacks)
+    {
+        double *c = (double *)malloc(sizeof(double) * (size_t)K);
+        double *pos = (double *)malloc(sizeof(double) * (size_t)K);
+#pragma omp for schedule(static)
+        for (int64_t e = 0; e < m; ++e) {
+            double g;
+            fallbacks += orc_edge_ck(K, h + (int64_t)P->src[e] * K, h + (int64_t)P->col[e] * K, f + e * K, P->u[e],
+                                     f_new + e * K, &g, c, pos);
+            if (g_new) g_new[e] = g;
+        }
+        free(c);
+        free(pos);
+    }
+    return fallbacks;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Residuals of eq. (1), certificate and verdict                             */
 /* ------------------------------------------------------------------------ */
 
@@ -455,10 +545,14 @@ typedef struct {
 } orc_report;
 
 /* Runs Alg. 1 from the flows in f (the paper starts at f = 0) and leaves
- * f^(t) in f.  ztrace, if not NULL, receives z^(0..) up to ztrace_len entries.
+ * f^(t) in f; the local step is Alg. 2 (capacity_kept = 0) or the
+ * capacity-kept projection of Program (6) (capacity_kept = 1).  The
+ * objective is z = 1/2 sum psi^2 + 1/2 sum delta h^2 in both cases (with the
+ * capacity kept, psi = 0 after the first step and z is Program (6)'s).
+ * ztrace, if not NULL, receives z^(0..) up to ztrace_len entries.
  * Returns 0, or -1 on allocation failure. */
-int32_t orc_solve_eso(const orc_problem *P, const orc_options *opt, double *f, orc_report *rep, double *ztrace,
-                      int64_t ztrace_len)
+static int32_t solve_alg1(const orc_problem *P, const orc_options *opt, double *f, orc_report *rep, double *ztrace,
+                          int64_t ztrace_len, int capacity_kept)
 {
     const int32_t n = P->n, K = P->K;
     const int64_t m = P->m;
@@ -508,7 +602,7 @@ int32_t orc_solve_eso(const orc_problem *P, const orc_options *opt, double *f, o
         }
         z_prev = z;
         /* update flows by solving every edge subproblem */
-        rep->qp_fallbacks += orc_qp_all(P, h, f, f_next, NULL);
+        rep->qp_fallbacks += capacity_kept ? orc_ck_all(P, h, f, f_next, NULL) : orc_qp_all(P, h, f, f_next, NULL);
         memcpy(f, f_next, sizeof(double) * (size_t)m * (size_t)K);
         ++t;
     }
@@ -520,6 +614,19 @@ int32_t orc_solve_eso(const orc_problem *P, const orc_options *opt, double *f, o
     free(psi);
     free(f_next);
     return 0;
+}
+
+int32_t orc_solve_eso(const orc_problem *P, const orc_options *opt, double *f, orc_report *rep, double *ztrace,
+                      int64_t ztrace_len)
+{
+    return solve_alg1(P, opt, f, rep, ztrace, ztrace_len, 0);
+}
+
+/* Alg. 1 with the capacity-kept step (Program (6)); see orc_edge_ck. */
+int32_t orc_solve_ck(const orc_problem *P, const orc_options *opt, double *f, orc_report *rep, double *ztrace,
+                     int64_t ztrace_len)
+{
+    return solve_alg1(P, opt, f, rep, ztrace, ztrace_len, 1);
 }
 
 /* ------------------------------------------------------------------------ */
