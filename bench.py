@@ -55,7 +55,7 @@ WORKLOADS = {
     "batch256": "batch256: 256 random out-degree-4 digraphs, n~U[100,5000], K~U[10,1000], d~U{1..10}, u=1.2x "
                 "routing load (20% at 0.7x), seed 0",
 }
-ALGOS = {"eso": 0, "agd": 1, "gdm": 2}
+ALGOS = {"eso": 0, "agd": 1, "gdm": 2, "ck": 3}  # ck: Alg. 1 with the capacity kept (Program (6))
 WORKLOAD = WORKLOADS["knn2500_k500"]
 L2_RESIDENT_BYTES = 96 << 20  # working sets up to this stay in GB300's L2 across sweeps (measured)
 FLUSH_BYTES = 256 << 20
@@ -680,7 +680,7 @@ def main():
         bytes_qp = update_bytes(args.algo, inst)
         bytes_ex = 4 * K * (m + n) + 4 * 2 * m + 8 * n  # f once, h out; incidence lists
         share_qp = t_qp / (t_qp + t_ex)
-        upd = {"eso": "edge_qp", "agd": "agd_step", "gdm": "gdm_step"}[args.algo]
+        upd = {"eso": "edge_qp", "agd": "agd_step", "gdm": "gdm_step", "ck": "edge_qp_ck"}[args.algo]
         dom, t_dom, b_dom = (upd, t_qp, bytes_qp) if t_qp >= t_ex else ("excess_height", t_ex, bytes_ex)
         t_dom_c = t_qp_c if dom == upd else t_ex_c
         peak, peak_src = load_peaks()

@@ -72,7 +72,14 @@ typedef enum {
 typedef enum {
     PDR_ALGO_ESO = 0, /* Alg. 1 with the exact edge solver of Alg. 2 (PDR-ESO) */
     PDR_ALGO_AGD = 1, /* Alg. 3: projected gradient step with adaptive learning rate (PDR-AGD) */
-    PDR_ALGO_GDM = 2  /* Alg. 4: Alg. 3 with momentum (PDR-GDM) */
+    PDR_ALGO_GDM = 2, /* Alg. 4: Alg. 3 with momentum (PDR-GDM) */
+    PDR_ALGO_CK = 3   /* Alg. 1 with the capacity kept (Program (6), Section "Further Discussion on
+                         Optimality Condition"): every edge projects Alg. 2's c_k = f_k + (h_ik - h_jk)/2
+                         onto {f >= 0, sum_k f_k <= u_e}, i.e. f'_k = max(0, c_k - g) with g = 0 if
+                         sum_k max(0, c_k) <= u_e, else sum_k f'_k = u_e.  The paper gives the program's
+                         optimality conditions but no algorithm; this is Alg. 1's local step with the
+                         capacity term kept as a constraint (a projected gradient step of size 1/2).
+                         The flows never exceed the capacities; the objective is 1/2 sum delta h^2. */
 } pdr_algo;
 
 typedef enum {

@@ -49,6 +49,10 @@ void fill_defaults(pdr_options* o)
     o->edge_variant = -1;
 }
 
+// Alg. 3 / Alg. 4: the gradient-step kernels with learning rates; Alg. 1
+// and its capacity-kept form run the edge-QP kernels.
+bool is_gd(const pdr_options& o) { return o.algo == PDR_ALGO_AGD || o.algo == PDR_ALGO_GDM; }
+
 bool options_ok(const pdr_options* o, std::string* why)
 {
     if (o->precision < PDR_PREC_FP32 || o->precision > PDR_PREC_FP32_FP64TAIL) {
@@ -71,8 +75,8 @@ bool options_ok(const pdr_options* o, std::string* why)
         *why = "trace_len must be >= 0";
         return false;
     }
-    if (o->algo < PDR_ALGO_ESO || o->algo > PDR_ALGO_GDM) {
-        *why = "algo must be 0 (ESO), 1 (AGD) or 2 (GDM)";
+    if (o->algo < PDR_ALGO_ESO || o->algo > PDR_ALGO_CK) {
+        *why = "algo must be 0 (ESO), 1 (AGD), 2 (GDM) or 3 (capacity kept)";
         return false;
     }
     const double g[] = {o->beta_init, o->beta_min, o->beta_max, o->alpha_inc, o->alpha_dec, o->gamma};
@@ -252,6 +256,7 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.v_in = Prec<T>::v(ctx, b);
     a.v_out = Prec<T>::v(ctx, b ^ 1);
     a.momentum = ctx->opt.algo == PDR_ALGO_GDM ? 1 : 0;
+    a.ck = ctx->opt.algo == PDR_ALGO_CK ? 1 : 0;
     a.beta_min = (T)ctx->g_beta_min;
     a.beta_max = (T)ctx->g_beta_max;
     a.alpha_inc = (T)ctx->g_alpha_inc;
@@ -329,7 +334,7 @@ template <typename T>
 cudaError_t launch_update(pdr_ctx* ctx, const SweepArgs<T>& a, cudaStream_t stream)
 {
     const int cfg = ctx->cfg[Prec<T>::id];
-    return ctx->opt.algo == PDR_ALGO_ESO ? launch_edge<T>(a, cfg, stream) : launch_gd<T>(a, cfg, stream);
+    return is_gd(ctx->opt) ? launch_gd<T>(a, cfg, stream) : launch_edge<T>(a, cfg, stream);
 }
 
 // Velocity buffers of the working precision (Alg. 4 only).
@@ -552,7 +557,7 @@ pdr_status widen_to_fp64(pdr_ctx* ctx)
     pdr_status s = ensure_fp64(ctx);
     if (s != PDR_OK) return s;
     CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
-    if (ctx->opt.algo != PDR_ALGO_ESO && ctx->m > 0) {
+    if (is_gd(ctx->opt) && ctx->m > 0) {
         // learning rates (and velocities) follow the flows into FP64
         CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta, ctx->m,
                                      ctx->stream));
@@ -574,7 +579,7 @@ constexpr int64_t kPersistChunk = 1024;  // sweeps per persistent launch (even)
 // The persistent engine applies to Alg. 1 with a lane-group variant.
 bool persistent_ok(const pdr_ctx* ctx, int p)
 {
-    return ctx->opt.use_graph == 2 && ctx->opt.algo == PDR_ALGO_ESO && ctx->pgrid[p] >= 2;
+    return ctx->opt.use_graph == 2 && !is_gd(ctx->opt) && ctx->pgrid[p] >= 2;
 }
 
 // Alg. 1 by the persistent kernel: launches of kPersistChunk sweeps until the
@@ -1292,7 +1297,8 @@ pdr_status pdr_flow_rows(pdr_ctx* ctx, int32_t which, const int64_t* edges, int6
 pdr_status pdr_gd_state(pdr_ctx* ctx, double* beta, double* v)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
-    if (ctx->opt.algo == PDR_ALGO_ESO) return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 (no learning rates)");
+    if (!is_gd(ctx->opt))
+        return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 or its capacity-kept form (no learning rates)");
     const int b = ctx->cur;
     if (beta && ctx->m > 0) {
         if (ctx->cur_prec) {
@@ -1323,7 +1329,8 @@ pdr_status pdr_gd_state(pdr_ctx* ctx, double* beta, double* v)
 pdr_status pdr_set_gd_state(pdr_ctx* ctx, const double* beta, const double* v)
 {
     if (!ctx || (!beta && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "beta is NULL") : PDR_ERR_INVALID_ARG;
-    if (ctx->opt.algo == PDR_ALGO_ESO) return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 (no learning rates)");
+    if (!is_gd(ctx->opt))
+        return ctx->fail(PDR_ERR_INVALID_ARG, "the context runs Alg. 1 or its capacity-kept form (no learning rates)");
     for (int64_t e = 0; e < ctx->m; ++e)
         if (!(beta[e] > 0.0) || !std::isfinite(beta[e]))
             return ctx->fail(PDR_ERR_INVALID_ARG, "beta must be finite and > 0 at edge " + std::to_string(e));
@@ -1629,7 +1636,7 @@ pdr_status autotune(pdr_ctx* ctx, int32_t* best_cfg, double* best_us)
     for (int c = 0; c < num_edge_configs(); ++c) {
         if (edge_capacity<T>(c) < ctx->Kp) continue;
         if (edge_config_pipelined(c)) {
-            if (!pipe && ctx->opt.algo == PDR_ALGO_ESO) cand.push_back(c);
+            if (!pipe && !is_gd(ctx->opt)) cand.push_back(c);
             pipe = true;
         } else if ((int)cand.size() < 3) {
             cand.push_back(c);

@@ -119,6 +119,7 @@ struct SweepArgs {
     const T* v_in;      // [m][Kp] velocities of iteration t (Alg. 4)
     T* v_out;           // [m][Kp] velocities of iteration t+1 (Alg. 4)
     int momentum;       // 0: Alg. 3, 1: Alg. 4
+    int ck;             // edge QP: 1 = capacity kept (Program (6)): f' = P(c) onto {f >= 0, sum f <= u}
     T beta_min, beta_max, alpha_inc, alpha_dec, gamma;
     T* psi_out;         // optional [m] congestion output of the edge kernel
     DevState* st;

@@ -202,15 +202,17 @@ __device__ __forceinline__ void above(const T (&c)[V][N], T w, T& S, int& n, T& 
 }
 
 // Case decision and root from the sums above a threshold w >= 0 that is known
-// to lie at or below the root (w = 0, or g(w) >= 0 certified).
+// to lie at or below the root (w = 0, or g(w) >= 0 certified).  den = 2 for
+// Alg. 2 (the congestion term of eq. (10) gives theta = (S_A - u)/(2 + |A|));
+// den = 0 with the capacity kept (Program (6): sum_A (c - theta) = u).
 template <typename T>
-__device__ __forceinline__ void start_root(T S, int n, T mn, T ue, T& theta, int& nA, bool& done)
+__device__ __forceinline__ void start_root(T S, int n, T mn, T ue, int den, T& theta, int& nA, bool& done)
 {
     if (S <= ue) {  // Case 1 of Alg. 2: nothing to shed
         theta = T(0);
         done = true;
-    } else {  // Case 2
-        theta = (S - ue) / T(2 + n);
+    } else {  // Case 2 (S > u >= 0, so n >= 1)
+        theta = (S - ue) / T(den + n);
         nA = n;
         done = mn > theta;
     }
@@ -219,17 +221,17 @@ __device__ __forceinline__ void start_root(T S, int n, T mn, T ue, T& theta, int
 // theta = psi'/2 for the row c (all lanes of the warp call it; `valid` is
 // uniform over the lane group).  w0 is the warm start (>= 0).
 template <typename T, int G, int V, int N>
-__device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool valid, int Kp)
+__device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool valid, int Kp, int den)
 {
     T S, mn, theta = T(0);
     int n, nA = 0;
     bool done = !valid, cold = false;
     above<T, G, V, N>(c, w0, S, n, mn);
     if (valid) {
-        if (w0 <= T(0)) start_root(S, n, mn, ue, theta, nA, done);
-        else if (S - T(n) * w0 - ue - T(2) * w0 >= T(0)) {
-            // g(w0) = sum max(0, c - w0) - u - 2 w0 >= 0: w0 <= root, Case 2
-            theta = (S - ue) / T(2 + n);
+        if (w0 <= T(0)) start_root(S, n, mn, ue, den, theta, nA, done);
+        else if (n > 0 && S - T(n) * w0 - ue - T(den) * w0 >= T(0)) {
+            // g(w0) = sum max(0, c - w0) - u - den w0 >= 0: w0 <= root, Case 2
+            theta = (S - ue) / T(den + n);
             nA = n;
             done = mn > theta;
         } else {
@@ -240,17 +242,17 @@ __device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool 
         T S0, m0;
         int n0;
         above<T, G, V, N>(c, T(0), S0, n0, m0);
-        if (cold) start_root(S0, n0, m0, ue, theta, nA, done);
+        if (cold) start_root(S0, n0, m0, ue, den, theta, nA, done);
     }
     for (int it = 0; __any_sync(kFull, !done); ++it) {
         T S2, m2;
         int n2;
         above<T, G, V, N>(c, theta, S2, n2, m2);
         if (!done) {
-            if (n2 >= nA || n2 == 0) done = true;  // no element left (rounding only): keep theta
+            if (n2 >= nA || n2 == 0) done = true;  // no element left: keep theta
             else {
                 nA = n2;
-                theta = (S2 - ue) / T(2 + n2);
+                theta = (S2 - ue) / T(den + n2);
                 done = m2 > theta;
             }
         }
@@ -336,10 +338,12 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
         if (!psi_only) {
             // warm start slightly below the previous sweep's root
             const T w = valid ? a.theta[e] * T(0.999) : T(0);
-            const T theta = qp_root_group<T, G, V, N>(c, ue, w, valid, a.Kp);
+            const int den = a.ck ? 0 : 2;
+            const T theta = qp_root_group<T, G, V, N>(c, ue, w, valid, a.Kp, den);
             if (valid && gl == 0) a.theta[e] = theta;
-            // f' = max(0, c - theta); at the root sum f' - u = 2 theta, so the
-            // congestion of the new flows is psi' = 2 theta (0 in Case 1)
+            // f' = max(0, c - theta); at the root sum f' - u = den theta, so the
+            // congestion of the new flows is psi' = 2 theta for Alg. 2 and 0 with
+            // the capacity kept (and 0 in Case 1)
 #pragma unroll
             for (int q = 0; q < V; ++q) {
                 const int v = gl + q * G;
@@ -351,7 +355,7 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
                 }
                 if (valid && v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
             }
-            psi = T(2) * theta;
+            psi = T(den) * theta;
         } else {
             // congestion of the stored flows
             T rs = T(0);
@@ -458,7 +462,8 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
         if (en < a.m) pipe_load<T, V>(a, en, lane, vpr, fv, av, bv);
         T psi;
         if (!psi_only) {
-            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta[e] * T(0.999), true, a.Kp);
+            const int den = a.ck ? 0 : 2;
+            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta[e] * T(0.999), true, a.Kp, den);
             if (lane == 0) a.theta[e] = theta;
             T* orow = a.f_out + e * a.Kp;
 #pragma unroll
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
                 }
                 if (v < vpr) reinterpret_cast<VT*>(orow)[v] = pack4(o);
             }
-            psi = T(2) * theta;  // sum f' - u at the root
+            psi = T(den) * theta;  // sum f' - u at the root
         } else {
             T rs = T(0);
 #pragma unroll
@@ -603,24 +608,25 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
         if (!psi_only) {
             // the lane-group search with block-wide sums, counts and minima
             const T w0 = a.theta[e] * T(0.999);
+            const int den = a.ck ? 0 : 2;
             T S, mn, theta = T(0);
             int n, nA = 0;
             bool done = false;
             block_above<T, V, N>(c, w0, S, n, mn, sa_buf, sb_buf, sm_buf);
-            if (w0 <= T(0)) start_root(S, n, mn, ue, theta, nA, done);
-            else if (S - T(n) * w0 - ue - T(2) * w0 >= T(0)) {
-                theta = (S - ue) / T(2 + n);
+            if (w0 <= T(0)) start_root(S, n, mn, ue, den, theta, nA, done);
+            else if (n > 0 && S - T(n) * w0 - ue - T(den) * w0 >= T(0)) {
+                theta = (S - ue) / T(den + n);
                 nA = n;
                 done = mn > theta;
             } else {
                 block_above<T, V, N>(c, T(0), S, n, mn, sa_buf, sb_buf, sm_buf);
-                start_root(S, n, mn, ue, theta, nA, done);
+                start_root(S, n, mn, ue, den, theta, nA, done);
             }
             for (int it = 0; !done && it <= a.Kp + 2; ++it) {  // block-uniform
                 block_above<T, V, N>(c, theta, S, n, mn, sa_buf, sb_buf, sm_buf);
                 if (n >= nA || n == 0) break;
                 nA = n;
-                theta = (S - ue) / T(2 + n);
+                theta = (S - ue) / T(den + n);
                 done = mn > theta;
             }
             if (threadIdx.x == 0) a.theta[e] = theta;
@@ -642,7 +648,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
                     else reinterpret_cast<VT*>(orow)[v] = pack4(o);
                 }
             }
-            psi = T(2) * theta;  // sum f' - u at the root
+            psi = T(den) * theta;  // sum f' - u at the root
         } else {
             T rs = T(0);
             int dummy = 0;

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpdr.so")
 
 PREC_FP32, PREC_FP64, PREC_FP32_FP64TAIL = 0, 1, 2
-ALGO_ESO, ALGO_AGD, ALGO_GDM = 0, 1, 2
+ALGO_ESO, ALGO_AGD, ALGO_GDM, ALGO_CK = 0, 1, 2, 3
 VERDICT_UNKNOWN, VERDICT_FEASIBLE, VERDICT_INFEASIBLE = 0, 1, 2
 STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall"}
 VERDICT_NAMES = {0: "unknown", 1: "feasible", 2: "infeasible"}

@@ -92,7 +92,7 @@ def test_create_rejects_bad_options(lib):
     o = pdr.default_options(max_sweeps=-1)
     st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
     assert st == 1 and "max_sweeps" in msg
-    o = pdr.default_options(algo=3)
+    o = pdr.default_options(algo=4)
     st, msg, _ = _create(lib, **BASE, opt=C.byref(o))
     assert st == 1 and "algo" in msg
     o = pdr.default_options(algo=2, gamma=1.5)
