@@ -77,8 +77,8 @@ def parse():
     ap.add_argument("--edge-variant", type=int, default=-1,
                     help="edge-kernel variant (index of the library's variant table; -1 = the library's choice)")
     ap.add_argument("--to-residual", action="store_true",
-                    help="batch256: solve every instance to its verdict (residuals <= 1e-6 or a Farkas "
-                         "certificate, FP32 with the FP64 tail) as one batch and one after another")
+                    help="solve to the verdict (residuals <= 1e-6 or a Farkas certificate, FP32 with the FP64 "
+                         "tail; --sweeps caps the sweeps); batch256: as one batch and one after another")
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--compare-engines", action="store_true",
                     help="time the sweep-loop engines (host loop, CUDA graph, persistent kernel) on instances "
@@ -415,6 +415,29 @@ def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
     print(json.dumps(out), flush=True)
 
 
+def solve_to_residual(args, inst, pdr, torch, stream):
+    """One instance solved to its verdict: FP32 sweeps until they stall, then
+    FP64 sweeps, until cap_rel and cons_rel <= 1e-6 (or the Farkas
+    certificate holds, or the sweep cap).  Reports the time, the sweeps of
+    each phase and the residuals reached."""
+    max_sweeps = args.sweeps if args.sweeps > 0 else 2000000
+    out = {"kind": "time to residual 1e-6", "workload": WORKLOAD, "max_sweeps": max_sweeps,
+           "precision": "FP32 sweeps, FP64 tail, FP64 residuals and certificate", "algos": {}}
+    for name in (["eso", "ck"] if args.algo == "eso" else [args.algo]):
+        opts = dict(precision=pdr.PREC_FP32_FP64TAIL, eps_obj=0.0, resid_tol=1e-6, eps_rel=1e-13,
+                    max_sweeps=max_sweeps, algo=ALGOS[name])
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, **opts) as sv:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = sv.solve()
+                dt = time.perf_counter() - t0
+        out["algos"][name] = {"s": dt, "sweeps": r["sweeps"], "sweeps_fp64": r["sweeps_fp64"],
+                              "cap_rel": r["cap_rel"], "cons_rel": r["cons_rel"], "z": r["z"],
+                              "verdict": r["verdict_name"], "stop": r["stop_name"]}
+    print(json.dumps(out), flush=True)
+
+
 def bench_batch_to_residual(args, insts, pdr, torch, stream):
     """The batched form against the single-instance form at residual <= 1e-6:
     every instance solved to its verdict (FP32 sweeps, then FP64 sweeps once
@@ -579,6 +602,9 @@ def main():
         return
     if args.adjoint:
         bench_adjoint(args, inst, pdr, torch, stream)
+        return
+    if args.to_residual:
+        solve_to_residual(args, inst, pdr, torch, stream)
         return
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
