@@ -309,13 +309,13 @@ pdr_status pdr_set_data(pdr_ctx *ctx, const double *u, const double *d);
  * sweeps from f = 0 (no stop rule), and, if grad_u / grad_d are not NULL, its
  * gradient with respect to the capacities (grad_u[m]) and demands
  * (grad_d[K]) by reverse mode through the T sweeps (the derivatives of
- * eq. (3), (2), eq. "cpgrad" and of Alg. 2's active-set solution; at a kink
- * of max(0, .) or of an active set, the derivative of the active set the
- * forward took).  Flows are checkpointed every ckpt_every sweeps, so memory
+ * eq. (3), (2), eq. "cpgrad" and of Alg. 2's active-set solution, or of the
+ * capacity-kept projection for PDR_ALGO_CK; at a kink of max(0, .) or of an
+ * active set, the derivative of the active set the forward took).  Flows are checkpointed every ckpt_every sweeps, so memory
  * is about (T/ckpt_every + ckpt_every) flow arrays.  Runs in the context's
  * working precision (FP32 or FP64; gradients accumulate in FP64) and leaves
  * f^(T) as the current flows.  Errors: PDR_ERR_INVALID_ARG (T < 0,
- * ckpt_every < 1, or a context that does not run Alg. 1), PDR_ERR_OOM,
+ * ckpt_every < 1, or a context that runs Alg. 3 or Alg. 4), PDR_ERR_OOM,
  * PDR_ERR_CUDA. */
 pdr_status pdr_backward(pdr_ctx *ctx, int64_t T, int32_t ckpt_every, double *L, double *grad_u, double *grad_d);
 

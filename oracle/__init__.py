@@ -138,6 +138,10 @@ def _load():
             lib.orc_adjoint_eso.restype = C.c_int32
             lib.orc_unrolled_objective.argtypes = [P, C.c_int64]
             lib.orc_unrolled_objective.restype = C.c_double
+            lib.orc_adjoint_ck.argtypes = [P, C.c_int64, C.POINTER(C.c_double), vp, vp]
+            lib.orc_adjoint_ck.restype = C.c_int32
+            lib.orc_unrolled_objective_ck.argtypes = [P, C.c_int64]
+            lib.orc_unrolled_objective_ck.restype = C.c_double
             lib.orc_set_threads.argtypes = [C.c_int32]
             lib.orc_set_threads.restype = None
             lib.orc_max_threads.argtypes = []
@@ -334,6 +338,19 @@ class Problem:
     def unrolled_objective(self, T: int) -> float:
         """z(f^(T)) after T sweeps of Alg. 1 from f = 0 (with this problem's u and d)."""
         return float(_load().orc_unrolled_objective(C.byref(self._c), int(T)))
+
+    def adjoint_ck(self, T: int):
+        """(L, dL/du, dL/dd) for L = z(f^(T)) after T capacity-kept sweeps (Program (6)) from f = 0."""
+        L = C.c_double()
+        gu = np.empty(self.m)
+        gd = np.empty(self.K)
+        if _load().orc_adjoint_ck(C.byref(self._c), int(T), C.byref(L), _ptr(gu), _ptr(gd)) != 0:
+            raise MemoryError("oracle adjoint failed to allocate")
+        return L.value, gu, gd
+
+    def unrolled_objective_ck(self, T: int) -> float:
+        """z(f^(T)) after T capacity-kept sweeps from f = 0."""
+        return float(_load().orc_unrolled_objective_ck(C.byref(self._c), int(T)))
 
     def solve_eso(self, max_sweeps=100000, eps_obj=1e-6, resid_tol=0.0, f0=None, trace=False):
         """Alg. 1 with Alg. 2 from f0 (default 0).  Returns (f, report dict[, ztrace])."""

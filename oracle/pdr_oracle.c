@@ -782,7 +782,8 @@ int32_t orc_solve_gd(const orc_problem *P, const orc_options *opt, const orc_gd_
  *  - c_k = f_k + (h_ik - h_jk)/2, h = Delta/delta, Delta linear in f and d.
  * Stores every f^(t) (memory T*m*K doubles: for small instances).
  * Returns 0, or -1 on allocation failure. */
-int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *grad_u, double *grad_d)
+static int32_t adjoint_alg1(const orc_problem *P, int64_t T, double *L_out, double *grad_u, double *grad_d,
+                            int capacity_kept)
 {
     const int32_t n = P->n, K = P->K;
     const int64_t m = P->m, mk = m * (int64_t)K, nk = (int64_t)n * K;
@@ -803,7 +804,8 @@ int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *
     /* forward: f^(t+1) from f^(t) */
     for (int64_t t = 0; t < T; ++t) {
         orc_excess(P, fs + t * mk, Delta, h);
-        orc_qp_all(P, h, fs + t * mk, fs + (t + 1) * mk, NULL);
+        if (capacity_kept) orc_ck_all(P, h, fs + t * mk, fs + (t + 1) * mk, NULL);
+        else orc_qp_all(P, h, fs + t * mk, fs + (t + 1) * mk, NULL);
     }
     /* L = z(f^(T)) and its seeds */
     orc_excess(P, fs + T * mk, Delta, h);
@@ -823,11 +825,17 @@ int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *
         /* Alg. 2 backward, edge by edge: fbar holds dL/df^(t+1) */
         for (int64_t e = 0; e < m; ++e) {
             const double *hi = h + (int64_t)P->src[e] * K, *hj = h + (int64_t)P->col[e] * K;
-            double r, theta2;
-            orc_edge_qp(K, hi, hj, f + e * K, P->u[e], fn, &r, &theta2, c, pos); /* psi' = 2 theta */
-            /* orc_edge_qp leaves c_k = 1/2((h_ik + f_k) - (h_jk - f_k)) in c */
-            double theta = theta2 / 2.0;
-            int32_t congested = theta2 > 0.0;
+            /* the root theta of the step (Alg. 2: psi'/2; capacity kept: g); both
+             * leave c_k = 1/2((h_ik + f_k) - (h_jk - f_k)) in c */
+            double theta;
+            if (capacity_kept) {
+                orc_edge_ck(K, hi, hj, f + e * K, P->u[e], fn, &theta, c, pos);
+            } else {
+                double r, psi_new;
+                orc_edge_qp(K, hi, hj, f + e * K, P->u[e], fn, &r, &psi_new, c, pos);
+                theta = psi_new / 2.0;
+            }
+            int32_t congested = theta > 0.0;
             double Sbar = 0.0;
             int32_t nA = 0;
             for (int32_t k = 0; k < K; ++k) {
@@ -837,7 +845,10 @@ int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *
                     ++nA;
                 }
             }
-            double corr = congested ? Sbar / (2.0 + (double)nA) : 0.0;
+            /* Alg. 2: theta = (S_A - u)/(2 + |A|); capacity kept: (S_A - u)/|A|.
+             * With the capacity kept and u = 0 the root is max_k c_k and no
+             * element is active: f' = 0 near c, so nothing flows back. */
+            double corr = (congested && nA > 0) ? Sbar / ((capacity_kept ? 0.0 : 2.0) + (double)nA) : 0.0;
             for (int32_t k = 0; k < K; ++k) {
                 int32_t act = congested ? (c[k] > theta) : (c[k] > 0.0);
                 cbar[e * K + k] = act ? fbar[e * K + k] - corr : 0.0;
@@ -864,8 +875,20 @@ int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *
     return 0;
 }
 
-/* L(u, d) = z(f^(T)) alone (the forward of orc_adjoint_eso), for finite differences. */
-double orc_unrolled_objective(const orc_problem *P, int64_t T)
+int32_t orc_adjoint_eso(const orc_problem *P, int64_t T, double *L_out, double *grad_u, double *grad_d)
+{
+    return adjoint_alg1(P, T, L_out, grad_u, grad_d, 0);
+}
+
+/* The same through T capacity-kept sweeps (Program (6)): the step's
+ * Jacobian on the active set is I - 1 1^T / |A| and df'/du = 1/|A|. */
+int32_t orc_adjoint_ck(const orc_problem *P, int64_t T, double *L_out, double *grad_u, double *grad_d)
+{
+    return adjoint_alg1(P, T, L_out, grad_u, grad_d, 1);
+}
+
+/* L(u, d) = z(f^(T)) alone (the forward of the adjoints), for finite differences. */
+static double unrolled_objective(const orc_problem *P, int64_t T, int capacity_kept)
 {
     const int64_t mk = P->m * (int64_t)P->K, nk = (int64_t)P->n * P->K;
     double *f = (double *)calloc((size_t)mk + 1, sizeof(double));
@@ -875,7 +898,8 @@ double orc_unrolled_objective(const orc_problem *P, int64_t T)
     double *psi = (double *)malloc(sizeof(double) * (size_t)P->m + 8);
     for (int64_t t = 0; t < T; ++t) {
         orc_excess(P, f, Delta, h);
-        orc_qp_all(P, h, f, g, NULL);
+        if (capacity_kept) orc_ck_all(P, h, f, g, NULL);
+        else orc_qp_all(P, h, f, g, NULL);
         double *x = f;
         f = g;
         g = x;
@@ -886,3 +910,7 @@ double orc_unrolled_objective(const orc_problem *P, int64_t T)
     free(f); free(g); free(Delta); free(h); free(psi);
     return z;
 }
+
+double orc_unrolled_objective(const orc_problem *P, int64_t T) { return unrolled_objective(P, T, 0); }
+
+double orc_unrolled_objective_ck(const orc_problem *P, int64_t T) { return unrolled_objective(P, T, 1); }

@@ -1,4 +1,6 @@
-// adjoint.cu -- reverse mode through T unrolled sweeps of Alg. 1.
+// adjoint.cu -- reverse mode through T unrolled sweeps of Alg. 1 (with
+// Alg. 2's step, or the capacity-kept step of Program (6), where the
+// Jacobian is the same with 2 + |A| replaced by |A|).
 //
 // L(u, d) = z(f^(T)) with f^(0) = 0 and f^(t+1) = one sweep (eq. (3), (2),
 // then Alg. 2 on every edge).  With fbar = dL/df^(t+1) the backward step of
@@ -122,7 +124,9 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
         __syncwarp();  // the ballots written above are read by every lane below
         sb = group_sum<32>(sb);
         na = group_sum<32>(na);
-        const T corr = congested ? sb / T(2 + na) : T(0);
+        // Alg. 2: theta = (S_A - u)/(2 + |A|); capacity kept: (S_A - u)/|A|.  With
+        // the capacity kept and u = 0 no element is active and nothing flows back.
+        const T corr = (congested && na > 0) ? sb / T((a.ck ? 0 : 2) + na) : T(0);
         VT* out = reinterpret_cast<VT*>(cbar + e * a.Kp);
         for (int q = 0; q < nq; ++q) {
             const int v = q * 32 + lane;

@@ -1201,8 +1201,9 @@ pdr_status pdr_backward(pdr_ctx* ctx, int64_t T, int32_t ckpt_every, double* L, 
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
     if (T < 0 || ckpt_every < 1) return ctx->fail(PDR_ERR_INVALID_ARG, "T must be >= 0 and ckpt_every >= 1");
-    if (ctx->opt.algo != PDR_ALGO_ESO)
-        return ctx->fail(PDR_ERR_INVALID_ARG, "the differentiated form runs Alg. 1 (algo = PDR_ALGO_ESO)");
+    if (is_gd(ctx->opt))
+        return ctx->fail(PDR_ERR_INVALID_ARG,
+                         "the differentiated form runs Alg. 1 (algo = PDR_ALGO_ESO or PDR_ALGO_CK)");
     pdr_status s = pdr_reset(ctx);  // f = 0 in the starting precision
     if (s != PDR_OK) return s;
     return ctx->cur_prec ? backward_T<double>(ctx, T, ckpt_every, L, grad_u, grad_d)

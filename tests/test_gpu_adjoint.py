@@ -100,6 +100,25 @@ def test_set_data_and_errors(pdr):
             s.backward(3, 1)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_capacity_kept_reverse_mode_matches_oracle(pdr, prec):
+    """pdr_backward through capacity-kept sweeps (Program (6)) against the
+    oracle's reverse mode: FP64 to 1e-9, FP32 to 1e-4 in norm."""
+    p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
+    for inst in cases():
+        Lr, gur, gdr = oracle.Problem.from_instance(inst).adjoint_ck(20)
+        with pdr.Solver.from_instance(inst, precision=p, algo=pdr.ALGO_CK) as s:
+            L, gu, gd = s.backward(20, 6)
+        if prec == "fp64":
+            assert abs(L - Lr) <= 1e-12 * Lr
+            np.testing.assert_allclose(gd, gdr, rtol=1e-9, atol=1e-12 * np.abs(gdr).max())
+            np.testing.assert_allclose(gu, gur, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(gur).max()))
+        else:
+            assert abs(L - Lr) <= 1e-5 * Lr
+            g, gr = np.concatenate([gu, gd]), np.concatenate([gur, gdr])
+            assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), (inst.name, np.linalg.norm(g - gr))
+
+
 def test_torch_autograd_function(pdr):
     import torch
 

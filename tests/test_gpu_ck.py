@@ -113,7 +113,7 @@ def test_full_size_sweep_parity_knn2500(pdr, knn2500):
 
 def test_engines_and_batch(pdr):
     """The persistent engine gives the graph engine's flows bit for bit; a batch
-    reaches the single solves' verdicts; the differentiated form refuses."""
+    reaches the single solves' verdicts; there are no learning rates."""
     inst = small_instances()[3]
     opts = dict(precision=pdr.PREC_FP32, algo=pdr.ALGO_CK, eps_obj=0.0, resid_tol=0.0, max_sweeps=1030)
     flows = []
@@ -131,7 +131,5 @@ def test_engines_and_batch(pdr):
         with pdr.Solver.from_instance(x, **bopts) as s:
             assert s.solve()["verdict"] == r["verdict"], x.name
     with pdr.Solver.from_instance(inst, algo=pdr.ALGO_CK) as s:
-        with pytest.raises(pdr.PdrError):
-            s.backward(3, 1)
         with pytest.raises(pdr.PdrError):
             s.gd_state()

@@ -26,23 +26,25 @@ def cases():
             I.make_instance("dg25_k7", I.random_digraph(25, 3, rng), 7, ("uniform_int", 1, 9), 0.9, rng)]
 
 
-def objective_at(inst, T, which, idx, delta):
+def objective_at(inst, T, which, idx, delta, ck=False):
     if which == "u":
         u = inst.u.copy()
         u[idx] += delta
-        return problem(inst, u=u).unrolled_objective(T)
-    d = inst.d.copy()
-    d[idx] += delta
-    return problem(inst, d=d).unrolled_objective(T)
+        P = problem(inst, u=u)
+    else:
+        d = inst.d.copy()
+        d[idx] += delta
+        P = problem(inst, d=d)
+    return P.unrolled_objective_ck(T) if ck else P.unrolled_objective(T)
 
 
-def check_derivative(inst, T, which, idx, g):
+def check_derivative(inst, T, which, idx, g, ck=False):
     """At a smooth point g must equal the central difference; where L has a
     kink exactly at the point (max(0, .) or an active-set boundary of Alg. 2
     hit exactly, which integer data make common), the one-sided derivatives
     differ and g must equal one of them.  Returns 1 if checked."""
     h = 1e-5
-    L = [objective_at(inst, T, which, idx, q * h) for q in (-2, -1, 0, 1, 2)]
+    L = [objective_at(inst, T, which, idx, q * h, ck) for q in (-2, -1, 0, 1, 2)]
     # second-order one-sided differences: exact for quadratics, O(h^2) otherwise
     right = (-3 * L[2] + 4 * L[3] - L[4]) / (2 * h)
     left = (3 * L[2] - 4 * L[1] + L[0]) / (2 * h)
@@ -94,3 +96,25 @@ def test_forward_of_adjoint_is_the_solver():
     f, rep = P.solve_eso(max_sweeps=25, eps_obj=0.0)
     assert rep["sweeps"] == 25 and abs(rep["z"] - L) <= 1e-14 * L
     assert abs(P.unrolled_objective(25) - L) <= 1e-14 * L
+
+
+@pytest.mark.parametrize("T", [1, 6, 20])
+def test_capacity_kept_adjoint_matches_finite_differences(T):
+    """The same checks through T sweeps of the capacity-kept step (Program (6))."""
+    checked = 0
+    for inst in cases():
+        L, gu, gd = problem(inst).adjoint_ck(T)
+        assert abs(L - problem(inst).unrolled_objective_ck(T)) <= 1e-14 * L
+        for k in range(inst.K):
+            checked += check_derivative(inst, T, "d", k, gd[k], ck=True)
+        for e in np.nonzero(inst.u > 0)[0][:12]:
+            checked += check_derivative(inst, T, "u", e, gu[e], ck=True)
+    assert checked >= 40
+
+
+def test_capacity_kept_adjoint_euler_identity():
+    """The capacity-kept step is positively homogeneous of degree 1 in (f, u, d)
+    as well, so u . dL/du + d . dL/dd = 2 L."""
+    for inst in cases():
+        L, gu, gd = problem(inst).adjoint_ck(25)
+        assert abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) <= 1e-10 * max(1.0, L)
