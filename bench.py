@@ -308,6 +308,23 @@ def compare_algos(args, inst, pdr, torch, stream):
             "excess_kernel_us_cold": t_ex * 1e3, "excess_gbs": b_ex / (t_ex / 1e3) / 1e9,
             "excess_frac": b_ex / (t_ex / 1e3) / 1e9 / peak,
         }
+    # the FP64 oracle of each algorithm on a bounded sample: one sweep from f = 0
+    import oracle
+
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem.from_instance(inst)
+    for name in ALGOS:
+        t0 = time.perf_counter()
+        if name == "eso":
+            P.solve_eso(max_sweeps=1, eps_obj=0.0)
+        elif name == "ck":
+            P.solve_ck(max_sweeps=1, eps_obj=0.0)
+        else:
+            P.solve_gd(oracle.gd_params(name == "gdm", inst.K), max_sweeps=1, eps_obj=0.0)
+        dt = time.perf_counter() - t0
+        out["algos"][name]["cpu_baseline"] = {"value": inst.m * inst.K / dt, "unit": UNIT, "cores": threads,
+                                              "kind": "oracle", "sample": f"1 FP64 sweep from f = 0, {dt:.2f} s"}
+    oracle.set_threads(1)
     print(json.dumps(out), flush=True)
 
 
@@ -412,7 +429,37 @@ def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
             out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
     out["gradient_over_forward"] = out["forward_and_gradient_ms"] / out["forward_only_ms"]
     out["forward_updates_per_s"] = inst.m * inst.K * T / (out["forward_only_ms"] / 1e3)
+    # the gradient's extra work per sweep: the segment's forward sweep again
+    # (excess 4K(m+n), edge QP 4K(2m+n)) and the four backward kernels
+    # (Jacobian step: f, h, dL/df' in, dL/dc out = 4K(3m+n); vertex gather:
+    # dL/dc in, dL/dDelta out = 4K(m+n); adjoint step: dL/dc, dL/dDelta in,
+    # dL/df out = 4K(2m+n)), each array counted once
+    m, n, K = inst.m, inst.n, inst.K
+    extra_bytes = T * 4 * K * (9 * m + 5 * n)
+    extra_ms = out["forward_and_gradient_ms"] - out["forward_only_ms"]
+    peak, peak_src = load_peaks()
+    out["gradient_roofline"] = {"bound": "hbm", "algorithmic_bytes": extra_bytes, "ms": extra_ms,
+                                "achieved": extra_bytes / (extra_ms / 1e3) / 1e9,
+                                "peak": peak, "unit": "GB/s", "peak_source": peak_src,
+                                "frac": extra_bytes / (extra_ms / 1e3) / 1e9 / peak}
+    out["cpu_baseline"] = adjoint_cpu_baseline(inst)
     print(json.dumps(out), flush=True)
+
+
+def adjoint_cpu_baseline(inst, T=1):
+    """The FP64 oracle's reverse mode (unoptimised) on a bounded sample: T
+    sweeps forward and back on the same instance."""
+    import oracle
+
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem.from_instance(inst)
+    t0 = time.perf_counter()
+    P.adjoint_eso(T)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return {"value": inst.m * inst.K * T / dt, "unit": "edge·commodity updates/s (forward + gradient)",
+            "cores": threads, "kind": "oracle",
+            "sample": f"reverse mode through {T} FP64 sweep(s) of Alg. 1 on the same instance, {dt:.1f} s"}
 
 
 def solve_to_residual(args, inst, pdr, torch, stream):
@@ -529,6 +576,18 @@ def bench_batch(args, insts, pdr, torch, stream):
             sv.close()
     tb, ts = sorted(bt)[len(bt) // 2], sorted(st)[len(st) // 2]
     vals, counts = np.unique(cfg, return_counts=True)
+    # the oracle on a bounded sample: 5 FP64 sweeps of the first 8 instances
+    import oracle
+
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    upd = 0
+    for x in insts[:8]:
+        oracle.Problem.from_instance(x).solve_eso(max_sweeps=5, eps_obj=0.0)
+        upd += x.m * x.K * 5
+    cpu = {"value": upd / (time.perf_counter() - t0), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "5 FP64 sweeps of Alg. 1 on each of the first 8 instances"}
+    oracle.set_threads(1)
     print(json.dumps({
         "kind": "batched form", "workload": WORKLOAD, "instances": len(insts), "sweeps_per_instance": S,
         "updates_per_solve": total, "dtype": "f32",
@@ -537,6 +596,7 @@ def bench_batch(args, insts, pdr, torch, stream):
         "speedup": ts / tb,
         "autotuner_variants": {str(int(v)): int(c) for v, c in zip(vals, counts)},
         "verdicts_after_S": {v: verdicts.count(v) for v in sorted(set(verdicts))},
+        "cpu_baseline": cpu,
     }), flush=True)
 
 
