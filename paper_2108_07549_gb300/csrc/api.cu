@@ -153,6 +153,7 @@ struct pdr_ctx {
     cudaGraphConditionalHandle cond[2] = {0, 0};
     bool graph_tried[2] = {false, false};
     bool graph_ok[2] = {false, false};
+    bool graph_pdl[2] = {false, false};  // the graph's kernels use programmatic dependent launch
 
     pdr_result last{};
     std::string err;
@@ -331,10 +332,10 @@ void resolve_gd_params(pdr_ctx* ctx)
 
 // The flow update of one sweep: the edge QP (Alg. 2) or the gradient step.
 template <typename T>
-cudaError_t launch_update(pdr_ctx* ctx, const SweepArgs<T>& a, cudaStream_t stream)
+cudaError_t launch_update(pdr_ctx* ctx, const SweepArgs<T>& a, cudaStream_t stream, bool pdl = false)
 {
     const int cfg = ctx->cfg[Prec<T>::id];
-    return is_gd(ctx->opt) ? launch_gd<T>(a, cfg, stream) : launch_edge<T>(a, cfg, stream);
+    return is_gd(ctx->opt) ? launch_gd<T>(a, cfg, stream) : launch_edge<T>(a, cfg, stream, pdl);
 }
 
 // Velocity buffers of the working precision (Alg. 4 only).
@@ -497,11 +498,15 @@ pdr_status read_state(pdr_ctx* ctx)
     return PDR_OK;
 }
 
+// The sweep loop as one graph: a conditional WHILE node whose body holds
+// kUnroll sweeps (excess kernel, then update kernel).  For Alg. 1 the body's
+// kernels are captured with programmatic dependent launch (each may be
+// scheduled while its predecessor drains); if the runtime refuses that, the
+// body is captured again with plain launches.
 template <typename T>
-pdr_status build_graph(pdr_ctx* ctx)
+bool try_build_graph(pdr_ctx* ctx, bool pdl)
 {
     const int p = Prec<T>::id;
-    ctx->graph_tried[p] = true;
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h;
     cudaGraphNode_t node;
@@ -523,8 +528,9 @@ pdr_status build_graph(pdr_ctx* ctx)
         cudaError_t e1 = cudaSuccess;
         for (int q = 0; q < kUnroll && e1 == cudaSuccess; ++q) {
             SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 1, h, q & 1, 0);
-            e1 = launch_excess<T>(a, ctx->cap_stream);
-            if (e1 == cudaSuccess) e1 = launch_update<T>(ctx, a, ctx->cap_stream);
+            // the first kernel of the body follows the conditional node: plain
+            e1 = launch_excess<T>(a, ctx->cap_stream, pdl && q > 0);
+            if (e1 == cudaSuccess) e1 = launch_update<T>(ctx, a, ctx->cap_stream, pdl);
         }
         cudaError_t e3 = cudaStreamEndCapture(ctx->cap_stream, &captured);
         if (e1 != cudaSuccess || e3 != cudaSuccess) goto fail;
@@ -534,12 +540,23 @@ pdr_status build_graph(pdr_ctx* ctx)
     ctx->exec[p] = exec;
     ctx->cond[p] = h;
     ctx->graph_ok[p] = true;
-    return PDR_OK;
+    ctx->graph_pdl[p] = pdl;
+    return true;
 fail:
     cudaGetLastError();
     if (g) cudaGraphDestroy(g);
+    return false;
+}
+
+template <typename T>
+pdr_status build_graph(pdr_ctx* ctx)
+{
+    const int p = Prec<T>::id;
+    ctx->graph_tried[p] = true;
     ctx->graph_ok[p] = false;
-    return PDR_OK;  // the host loop takes over
+    if (!is_gd(ctx->opt) && try_build_graph<T>(ctx, true)) return PDR_OK;
+    try_build_graph<T>(ctx, false);
+    return PDR_OK;  // if both failed, the host loop takes over
 }
 
 // The FP32 phase of PDR_PREC_FP32_FP64TAIL hands over to FP64 when it stopped

@@ -131,14 +131,16 @@ struct SweepArgs {
 };
 
 // Launchers (sweep.cu).  Each returns the launch error.
+// pdl: programmatic dependent launch (the kernel waits in griddepcontrol.wait
+// for the previous kernel), used in the captured sweep loop.
 template <typename T>
-cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream);
+cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream, bool pdl = false);
 // Objective reduction and stop decision on their own (one block); the edge
 // kernel does the same work in its extra block during a sweep.
 template <typename T>
 cudaError_t launch_finalize(const SweepArgs<T>& a, cudaStream_t stream);
 template <typename T>
-cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream);
+cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream, bool pdl = false);
 template <typename T>
 int edge_config(int Kp);  // picks the edge-kernel variant for a row length
 template <typename T>

@@ -153,6 +153,8 @@ __device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, in
 template <typename T>
 __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
 {
+    pdl_wait();     // the previous sweep's edge kernel has finished (no-op without PDL)
+    pdl_trigger();  // one wave: the edge kernel's blocks may queue behind this one's
     volatile DevState* vst = a.st;
     if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
     excess_body<T>(a, blockIdx.x, gridDim.x);
@@ -384,6 +386,7 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
 template <typename T, int G, int V>
 __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
 {
+    pdl_wait();  // the excess kernel has finished (no-op without PDL)
     volatile DevState* vst = a.st;
     if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
@@ -423,6 +426,7 @@ __device__ __forceinline__ void pipe_load(const SweepArgs<T>& a, int64_t e, int 
 template <typename T, int V>
 __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
 {
+    pdl_wait();  // the excess kernel has finished (no-op without PDL)
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
@@ -549,6 +553,7 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
 template <typename T, int B, int V>
 __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2) : 1))) edge_block_kernel(SweepArgs<T> a)
 {
+    pdl_wait();  // the excess kernel has finished (no-op without PDL)
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
     using A = Acc<T>;
@@ -886,11 +891,35 @@ int excess_resident_blocks()
 template int excess_resident_blocks<float>();
 template int excess_resident_blocks<double>();
 
+// A launch with or without programmatic dependent launch (PDL): with it,
+// the kernel may be scheduled while the previous kernel on the stream (or
+// in the graph) is still running; its griddepcontrol.wait then holds it
+// until that kernel has finished and its writes are visible.
 template <typename T>
-cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream)
+cudaError_t launch_one(void (*kernel)(SweepArgs<T>), int grid, int block, cudaStream_t stream, bool pdl,
+                       const SweepArgs<T>& a)
 {
-    excess_kernel<T><<<a.grid_v, kThreads, 0, stream>>>(a);
-    return cudaGetLastError();
+    if (!pdl) {
+        kernel<<<grid, block, 0, stream>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+template <typename T>
+cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream, bool pdl)
+{
+    return launch_one<T>(excess_kernel<T>, a.grid_v, kThreads, stream, pdl, a);
 }
 
 template <typename T>
@@ -901,30 +930,29 @@ cudaError_t launch_finalize(const SweepArgs<T>& a, cudaStream_t stream)
 }
 
 template <typename T>
-cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
+cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream, bool pdl)
 {
     const int g = a.grid_e + 1;  // edge blocks plus the decision block
     switch (cfg) {
-    case 0: edge_group_kernel<T, 4, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 1: edge_group_kernel<T, 8, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 2: edge_group_kernel<T, 16, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 3: edge_group_kernel<T, 32, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 4: edge_group_kernel<T, 32, 2><<<g, kThreads, 0, stream>>>(a); break;
-    case 5: edge_group_kernel<T, 32, 4><<<g, kThreads, 0, stream>>>(a); break;
-    case 6: edge_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
-    case 7: edge_block_kernel<T, 256, 2><<<g, 256, 0, stream>>>(a); break;
-    case 8: edge_block_kernel<T, 512, 2><<<g, 512, 0, stream>>>(a); break;
-    case 9: edge_block_kernel<T, 512, 3><<<g, 512, 0, stream>>>(a); break;
-    case 10: edge_block_kernel<T, 512, 4><<<g, 512, 0, stream>>>(a); break;
-    case 11: edge_block_kernel<T, 512, 5><<<g, 512, 0, stream>>>(a); break;
-    case 12: edge_block_kernel<T, 512, 8><<<g, 512, 0, stream>>>(a); break;
-    case 13: edge_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
-    case 14: edge_pipe_kernel<T, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 15: edge_pipe_kernel<T, 2><<<g, kThreads, 0, stream>>>(a); break;
-    case 16: edge_pipe_kernel<T, 4><<<g, kThreads, 0, stream>>>(a); break;
+    case 0: return launch_one<T>(edge_group_kernel<T, 4, 1>, g, kThreads, stream, pdl, a);
+    case 1: return launch_one<T>(edge_group_kernel<T, 8, 1>, g, kThreads, stream, pdl, a);
+    case 2: return launch_one<T>(edge_group_kernel<T, 16, 1>, g, kThreads, stream, pdl, a);
+    case 3: return launch_one<T>(edge_group_kernel<T, 32, 1>, g, kThreads, stream, pdl, a);
+    case 4: return launch_one<T>(edge_group_kernel<T, 32, 2>, g, kThreads, stream, pdl, a);
+    case 5: return launch_one<T>(edge_group_kernel<T, 32, 4>, g, kThreads, stream, pdl, a);
+    case 6: return launch_one<T>(edge_group_kernel<T, 32, 8>, g, kThreads, stream, pdl, a);
+    case 7: return launch_one<T>(edge_block_kernel<T, 256, 2>, g, 256, stream, pdl, a);
+    case 8: return launch_one<T>(edge_block_kernel<T, 512, 2>, g, 512, stream, pdl, a);
+    case 9: return launch_one<T>(edge_block_kernel<T, 512, 3>, g, 512, stream, pdl, a);
+    case 10: return launch_one<T>(edge_block_kernel<T, 512, 4>, g, 512, stream, pdl, a);
+    case 11: return launch_one<T>(edge_block_kernel<T, 512, 5>, g, 512, stream, pdl, a);
+    case 12: return launch_one<T>(edge_block_kernel<T, 512, 8>, g, 512, stream, pdl, a);
+    case 13: return launch_one<T>(edge_block_kernel<T, 1024, 8>, g, 1024, stream, pdl, a);
+    case 14: return launch_one<T>(edge_pipe_kernel<T, 1>, g, kThreads, stream, pdl, a);
+    case 15: return launch_one<T>(edge_pipe_kernel<T, 2>, g, kThreads, stream, pdl, a);
+    case 16: return launch_one<T>(edge_pipe_kernel<T, 4>, g, kThreads, stream, pdl, a);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1048,11 +1076,11 @@ template int edge_capacity<float>(int);
 template int edge_capacity<double>(int);
 template int64_t edge_parts<double>(int, int);
 template int edge_grid<double>(int, int64_t, int);
-template cudaError_t launch_excess<float>(const SweepArgs<float>&, cudaStream_t);
-template cudaError_t launch_excess<double>(const SweepArgs<double>&, cudaStream_t);
-template cudaError_t launch_edge<float>(const SweepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_excess<float>(const SweepArgs<float>&, cudaStream_t, bool);
+template cudaError_t launch_excess<double>(const SweepArgs<double>&, cudaStream_t, bool);
+template cudaError_t launch_edge<float>(const SweepArgs<float>&, int, cudaStream_t, bool);
 template cudaError_t launch_finalize<float>(const SweepArgs<float>&, cudaStream_t);
 template cudaError_t launch_finalize<double>(const SweepArgs<double>&, cudaStream_t);
-template cudaError_t launch_edge<double>(const SweepArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_edge<double>(const SweepArgs<double>&, int, cudaStream_t, bool);
 
 }  // namespace pdr

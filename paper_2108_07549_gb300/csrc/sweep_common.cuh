@@ -41,6 +41,12 @@ __device__ __forceinline__ void unpack(const double2& v, double* x)
 __device__ __forceinline__ float4 pack4(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
 __device__ __forceinline__ double2 pack4(const double* x) { return make_double2(x[0], x[1]); }
 
+// Programmatic dependent launch: wait until the kernels this grid depends on
+// have completed and their writes are visible, and allow the dependent grid
+// to be scheduled.  Both are no-ops for a grid launched without PDL.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // L2 prefetch of the `bytes` bytes at p, one 128-byte line per thread and
 // round (thread `tid` of `nthreads`).  Only addresses inside the array are
 // passed; a prefetch never blocks the thread.
