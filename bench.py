@@ -701,7 +701,7 @@ def main():
         barrier()
     ms_step = replicas.slowest(sum(times) / len(times), world, device="cuda")
     value = replicas.job_throughput(m * K * S, ms_step / 1e3, world)
-    # S + 1 objective evaluations (the last one stops); the graph body holds 8
+    # S + 1 objective evaluations (the last one stops); the graph body holds 32
     # sweeps (two kernels each), the host loop launches chunks of 256 sweeps;
     # plus residuals (3), solve state init (1), reset (psi refresh + state init)
     if args.engine == "persistent" and not args.host_loop:
@@ -709,7 +709,7 @@ def main():
         # congestion refresh at the end, residuals, state init, reset
         launches_per_step = 2 * (-(-(S + 1) // 1024)) + 1 + 3 + 1 + 2
     else:
-        chunk = 256 if args.host_loop else 8
+        chunk = 256 if args.host_loop else 32
         launches_per_step = 2 * chunk * (-(-(S + 1) // chunk)) + 3 + 1 + 2
 
     # ---------------------------------------------------------------- end to end through the C ABI

@@ -28,7 +28,8 @@ thread_local std::string g_create_error;
 
 int round_up4(int k) { return (k + 3) / 4 * 4; }
 
-constexpr int kUnroll = 8;  // sweeps per iteration of the graph's while loop (even)
+constexpr int kUnroll = 32;     // sweeps per iteration of the graph's while loop (even)
+constexpr int kHostChunk = 256; // sweeps between stop-flag reads of the host loop (even)
 // Working sets above this stream from HBM every sweep (GB300: 129 MB of L2;
 // measured L2-resident streaming holds up to ~90 MB and collapses by 120 MB).
 constexpr double kL2Bytes = 96.0 * 1024 * 1024;
@@ -668,7 +669,7 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
         // host loop fallback: chunks of an even number of sweeps, then a look
         // at the stop flag (a chunk that does not stop leaves f in buffer 0)
         for (;;) {
-            for (int q = 0; q < 32 * kUnroll; ++q) {
+            for (int q = 0; q < kHostChunk; ++q) {
                 SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, q & 1, 0);
                 CK(launch_excess<T>(a, ctx->stream));
                 CK(launch_update<T>(ctx, a, ctx->stream));
