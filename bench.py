@@ -83,6 +83,10 @@ def parse():
     ap.add_argument("--compare-engines", action="store_true",
                     help="time the sweep-loop engines (host loop, CUDA graph, persistent kernel) on instances "
                          "from m = 80 to the bench workload and print one JSON line")
+    ap.add_argument("--excess-variant", type=int, default=-1,
+                    help="excess kernel form: -1 library default, 0 per-thread gathers, 1..3 bulk copies")
+    ap.add_argument("--compare-excess", action="store_true",
+                    help="time the excess kernel forms (alone, warm and cold L2) and the sweep loop with each")
     ap.add_argument("--compare-variants", action="store_true",
                     help="time every edge-kernel variant that holds the rows (Alg. 1) and print one JSON line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
@@ -364,6 +368,43 @@ def compare_variants(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+def compare_excess(args, inst, pdr, torch, stream):
+    """Alg. 1 in FP32 with each excess-kernel form: time per sweep inside the
+    graph loop (CUDA events around a fixed number of sweeps from f = 0, the
+    median of three) and the excess kernel alone, in the L2 state of the loop
+    (warm) and with L2 flushed before every launch (cold)."""
+    peak, peak_src = load_peaks()
+    S = args.sweeps
+    b_ex = 4 * inst.K * (inst.m + inst.n) + 8 * inst.m + 8 * inst.n
+    out = {"kind": "excess-kernel form comparison", "workload": WORKLOAD, "sweeps": S, "dtype": "f32",
+           "algorithmic_bytes": b_ex, "peak_gbs": peak, "peak_source": peak_src, "forms": {}}
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for form in (0, 1, 2, 3):
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
+                                          resid_tol=0.0, max_sweeps=S, excess_variant=form) as sv:
+                sv.solve()
+                times = []
+                for q in range(3):
+                    sv.reset()
+                    flush.fill_(q & 0xFF)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = sv.solve()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = sorted(times)[1]
+                t_w = sv.time_kernel("excess", 20, 0)
+                t_c = sv.time_kernel("excess", 10, FLUSH_BYTES)
+        out["forms"][str(form)] = {
+            "us_per_sweep": ms / S * 1e3, "updates_per_s": inst.m * inst.K * S / (ms / 1e3), "z_after": r["z"],
+            "excess_us_warm": t_w * 1e3, "excess_us_cold": t_c * 1e3,
+            "frac_warm": b_ex / (t_w / 1e3) / 1e9 / peak, "frac_cold": b_ex / (t_c / 1e3) / 1e9 / peak,
+        }
+    print(json.dumps(out), flush=True)
+
+
 def compare_engines(args, inst, pdr, torch, stream):
     """Alg. 1 in FP32 with each sweep-loop engine on instances of growing size
     (the last one the bench workload): microseconds per sweep of a solve of a
@@ -641,7 +682,8 @@ def main():
     if args.profile_sweeps > 0:
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32,
-                                          algo=ALGOS[args.algo], edge_variant=args.edge_variant) as sv:
+                                          algo=ALGOS[args.algo], edge_variant=args.edge_variant,
+                                          excess_variant=args.excess_variant) as sv:
                 sv.sweeps(args.profile_sweeps)
         torch.cuda.synchronize()
         return
@@ -650,6 +692,9 @@ def main():
         return
     if args.compare_variants:
         compare_variants(args, inst, pdr, torch, stream)
+        return
+    if args.compare_excess:
+        compare_excess(args, inst, pdr, torch, stream)
         return
     if args.compare_engines:
         compare_engines(args, inst, pdr, torch, stream)
@@ -669,7 +714,7 @@ def main():
     S = args.sweeps
     opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S,
                 use_graph=0 if args.host_loop else (2 if args.engine == "persistent" else 1), algo=ALGOS[args.algo],
-                edge_variant=args.edge_variant)
+                edge_variant=args.edge_variant, excess_variant=args.excess_variant)
     m, K = inst.m, inst.K
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -793,7 +838,8 @@ def main():
             return
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
-                                          resid_tol=1e-6, max_sweeps=1000000, edge_variant=args.edge_variant) as sv:
+                                          resid_tol=1e-6, max_sweeps=1000000, edge_variant=args.edge_variant,
+                                          excess_variant=args.excess_variant) as sv:
                 rr = sv.solve()
         line["time_to_eps"] = {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"],
                                "ms": rr["ms_total"], "z": rr["z"], "cap_rel": rr["cap_rel"],

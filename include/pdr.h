@@ -119,6 +119,16 @@ typedef struct {
      * (pdr_edge_variant_capacity) must hold K in every precision the solve
      * uses, else PDR_ERR_INVALID_ARG. */
     int32_t edge_variant;
+    /* Kernel form of the excess pass (eq. (2), (3); a tuning choice, every form
+     * gives bit-identical heights).  -1 (default): the library's choice
+     * (form 2 where it can be resident, else 0).
+     * 0: one thread per (vertex, 4 values) gathers the incident flow rows.
+     * 1..3: per block, one warp brings the incident row segments (2 KB) of a
+     * contiguous range of vertices into shared memory with bulk copies
+     * (cp.async.bulk) through a ring of stages, and four warps add them:
+     * 1 = 4 stages of 8 segments, 2 = 2 stages of 8, 3 = 4 stages of 4.  A
+     * form that cannot be resident on the device gives PDR_ERR_INVALID_ARG. */
+    int32_t excess_variant;
 } pdr_options;
 
 typedef struct {

@@ -48,6 +48,7 @@ void fill_defaults(pdr_options* o)
     o->beta_init = o->beta_min = o->beta_max = o->alpha_inc = o->alpha_dec = 0.0;
     o->gamma = -1.0;
     o->edge_variant = -1;
+    o->excess_variant = -1;
 }
 
 // Alg. 3 / Alg. 4: the gradient-step kernels with learning rates; Alg. 1
@@ -78,6 +79,10 @@ bool options_ok(const pdr_options* o, std::string* why)
     }
     if (o->algo < PDR_ALGO_ESO || o->algo > PDR_ALGO_CK) {
         *why = "algo must be 0 (ESO), 1 (AGD), 2 (GDM) or 3 (capacity kept)";
+        return false;
+    }
+    if (o->excess_variant < -1 || o->excess_variant > 3) {
+        *why = "excess_variant must be -1 (default), 0 (gathers) or 1..3 (bulk copies)";
         return false;
     }
     const double g[] = {o->beta_init, o->beta_min, o->beta_max, o->alpha_inc, o->alpha_dec, o->gamma};
@@ -134,6 +139,10 @@ struct pdr_ctx {
     // partials typed by the working precision: 8 bytes per entry covers both
     double *part_cons = nullptr, *part_capb = nullptr, *part_psi = nullptr, *part_cap = nullptr;
     int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
+    // excess kernel form (0: gathers, 1..3: bulk copies); grid and vertex split of each bulk form
+    int xform = 0;
+    int xgrid[4] = {0, 0, 0, 0};
+    int32_t* xv_start[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t n_psi[2] = {1, 1};
     int pgrid[2] = {0, 0};         // persistent kernel grid per precision (0: not available)
     int64_t pf[2] = {0, 0};        // edge-kernel L2 prefetch distance per precision (edges)
@@ -270,7 +279,9 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.part_capb = reinterpret_cast<T*>(ctx->part_capb);
     a.part_psi = ctx->part_psi;
     a.part_cap = reinterpret_cast<T*>(ctx->part_cap);
-    a.grid_v = ctx->grid_v[p];
+    a.excess_form = ctx->xform;
+    a.xv_start = ctx->xv_start[ctx->xform];
+    a.grid_v = ctx->xform ? ctx->xgrid[ctx->xform] : ctx->grid_v[p];
     a.grid_e = ctx->grid_e[p];
     a.n_psi = ctx->n_psi[p];
     a.pf_edges = ctx->pf[p];
@@ -496,6 +507,7 @@ pdr_status read_state(pdr_ctx* ctx)
 {
     CK(cudaMemcpyAsync(ctx->hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->hst->fault) return ctx->fail(PDR_ERR_CUDA, "excess kernel: a shared-memory barrier wait timed out");
     return PDR_OK;
 }
 
@@ -600,6 +612,21 @@ bool persistent_ok(const pdr_ctx* ctx, int p)
     return ctx->opt.use_graph == 2 && !is_gd(ctx->opt) && ctx->pgrid[p] >= 2;
 }
 
+// Excess kernel form from the options: -1 takes the default, 0..3 that
+// form; a bulk-copy form that cannot be resident on this device is refused.
+// The default is bulk-copy form 2 (two stages of eight row segments, six
+// blocks per SM on GB300), the fastest form measured on the grid, k-NN and
+// random-digraph workloads; the gathers where it cannot be resident.
+constexpr int kDefaultExcessForm = 2;
+pdr_status select_excess_form(pdr_ctx* ctx, const pdr_options& o)
+{
+    const int v = o.excess_variant >= 0 ? o.excess_variant : (ctx->xgrid[kDefaultExcessForm] > 0 ? kDefaultExcessForm : 0);
+    if (v > 0 && ctx->xgrid[v] <= 0)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "excess_variant " + std::to_string(v) + " cannot run on this device");
+    ctx->xform = v;
+    return PDR_OK;
+}
+
 // Alg. 1 by the persistent kernel: launches of kPersistChunk sweeps until the
 // stop rules fire; the flows start in buffer 0.  *ran = false if the first
 // cooperative launch was refused (the caller then uses the graph engine).
@@ -609,6 +636,7 @@ pdr_status run_persistent(pdr_ctx* ctx, bool* ran)
     const int p = Prec<T>::id;
     const int grid = ctx->pgrid[p];
     SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, 0, 0);
+    a.excess_form = 0;  // the persistent kernel runs the gather form of the excess pass
     a.grid_v = grid;
     a.grid_e = grid - 1;
     a.n_psi = (int64_t)(grid - 1) * (kThreads / 32);
@@ -916,7 +944,7 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
                    ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta,
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
-                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar};
+                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3]};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (ctx->hst) cudaFreeHost(ctx->hst);
@@ -977,6 +1005,16 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms, excess_resident_blocks<float>());
     ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms, excess_resident_blocks<double>());
     ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms, 8);
+    for (int f = 1; f <= 3; ++f) {
+        const int r32 = excess_bulk_resident_blocks<float>(f), r64 = excess_bulk_resident_blocks<double>(f);
+        const int64_t r = r32 < r64 ? r32 : r64;
+        const int64_t g = r * ctx->num_sms < n ? r * ctx->num_sms : n;
+        ctx->xgrid[f] = r > 0 ? (int)(g < 1 ? 1 : g) : 0;
+    }
+    {
+        const pdr_status xs = select_excess_form(ctx, o);
+        if (xs != PDR_OK) return give_up(xs);
+    }
     {
         int64_t we = (m * 32 + 255) / 256;
         int64_t cap = (int64_t)ctx->num_sms * 8;
@@ -1014,6 +1052,10 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_dem_d, double, Kp);
     ALLOC(ctx->inv_dem_f, float, Kp);
     int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
+    for (int f = 1; f <= 3; ++f) {
+        if (ctx->xgrid[f] > gv) gv = ctx->xgrid[f];
+        if (ctx->xgrid[f] > 0) ALLOC(ctx->xv_start[f], int32_t, ctx->xgrid[f] + 1);
+    }
     int64_t np = ctx->n_psi[0] > ctx->n_psi[1] ? ctx->n_psi[0] : ctx->n_psi[1];
     if (np < m + 8) np = m + 8;  // any standalone variant writes at most m + 8 edge partials
     // the persistent kernel: at most 8 blocks of 256 threads per SM, one
@@ -1081,6 +1123,8 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     CKC(cudaMemcpyAsync(ctx->inv_dem_f, idf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
     CKC(build_adjacency(n, m, ctx->row_ptr, ctx->col, ctx->src, ctx->in_ptr, ctx->in_eid, ctx->inc_ptr, ctx->inc,
                         ctx->deg, ctx->work, ctx->stream));
+    for (int f = 1; f <= 3; ++f)
+        if (ctx->xgrid[f] > 0) CKC(launch_excess_split(ctx->inc_ptr, n, ctx->xgrid[f], ctx->xv_start[f], ctx->stream));
     // degree-0 commodity endpoints make the instance infeasible outright
     {
         std::vector<int32_t> hdeg(n);
@@ -1142,6 +1186,11 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
                             o.beta_min != ctx->opt.beta_min || o.beta_max != ctx->opt.beta_max ||
                             o.alpha_inc != ctx->opt.alpha_inc || o.alpha_dec != ctx->opt.alpha_dec ||
                             o.gamma != ctx->opt.gamma;
+    if (o.excess_variant != ctx->opt.excess_variant) {
+        const pdr_status xs = select_excess_form(ctx, o);
+        if (xs != PDR_OK) return xs;
+        destroy_graphs(ctx);
+    }
     if (gd_changed || o.use_graph != ctx->opt.use_graph) destroy_graphs(ctx);  // captured arguments change
     const int want = start_prec(o);
     if (want != ctx->cur_prec && o.precision != PDR_PREC_FP32_FP64TAIL) {

@@ -58,7 +58,8 @@ struct DevState {
     int stop;             // 1 once a stop rule fired
     int reason;           // STOP_* code
     int stop_on_rise;     // 1: z^(t) >= z^(t-1) stops (the FP32 rounding floor)
-    int pad;
+    int fault;            // 1: a kernel's wait on a shared-memory barrier ran out of its
+                          // limit (the sweep is invalid; the solve stops with an error)
     long long t_sweep;    // t of the sweep in flight (written by the excess kernel, read by
                           // the gradient-step kernels while the decision block advances t)
 };
@@ -109,6 +110,9 @@ struct SweepArgs {
     void* part_psi;     // [n_psi] per edge warp/block: sum psi^2 (float2 pair or double)
     T* part_cap;        // [n_psi] per edge warp/block: max psi/scale
     int32_t grid_v, grid_e;
+    int excess_form;    // excess kernel: 0 = per-thread gathers, 1..3 = bulk-copy pipeline
+                        // (stages x row segments per block: 4 x 8, 2 x 8, 4 x 4)
+    const int32_t* xv_start;  // [grid_v + 1] bulk-copy form: first vertex of each block
     int64_t n_psi;      // number of edge partials
     int64_t pf_edges;   // edge QP: L2 prefetch of the rows of edge e + pf_edges while
                         // edge e is solved (about one wave of resident edges ahead; 0: off)
@@ -166,6 +170,15 @@ cudaError_t launch_persistent(const SweepArgs<T>& a, int cfg, int grid, int64_t 
                               int psi_prologue, cudaStream_t stream);
 template <typename T>
 int excess_resident_blocks();  // excess blocks resident per SM (occupancy)
+// Bulk-copy excess form (1..3): blocks resident per SM (0 if it cannot run);
+// sets the kernel's shared-memory limit on first use.
+template <typename T>
+int excess_bulk_resident_blocks(int form);
+// Splits vertices 0..n-1 into `grid` contiguous ranges of about equal
+// incidence count (plus a per-vertex term): xv_start[b] = first vertex of block b,
+// xv_start[grid] = n.
+cudaError_t launch_excess_split(const int64_t* inc_ptr, int32_t n, int grid, int32_t* xv_start,
+                                cudaStream_t stream);
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream);
 
 // Gradient-step kernels of Alg. 3 / Alg. 4 (gd.cu); same grid, partials and

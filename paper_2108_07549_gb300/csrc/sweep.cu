@@ -37,6 +37,10 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(SweepArgs<T> a)
 
 // ------------------------------------------------------------------ excess and heights
 
+template <typename T>
+__device__ __forceinline__ void excess_tail(const SweepArgs<T>& a, int block, int nblocks,
+                                            typename Acc<T>::V zacc, T cons);
+
 // Body of one excess pass run by block `block` of `nblocks` (the standalone
 // kernel passes its own grid; the persistent kernel its whole grid).
 template <typename T>
@@ -130,7 +134,17 @@ __device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, in
         }
         zacc = A::add(zacc, zt);
     }
-    // this block's fixed slice of the edge kernel's psi partials
+    excess_tail<T>(a, block, nblocks, zacc, cons);
+}
+
+// End of an excess pass in every block: add this block's fixed slice of the
+// edge kernel's psi partials and write the block's three partials.  Every
+// thread of the block calls it.
+template <typename T>
+__device__ __forceinline__ void excess_tail(const SweepArgs<T>& a, int block, int nblocks,
+                                            typename Acc<T>::V zacc, T cons)
+{
+    using A = Acc<T>;
     T capb = T(0);
     {
         const int64_t lo = (int64_t)block * a.n_psi / nblocks;
@@ -158,6 +172,294 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     volatile DevState* vst = a.st;
     if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
     excess_body<T>(a, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------------------ excess by bulk copies
+//
+// The same pass as excess_body, with the incident flow rows brought into
+// shared memory by cp.async.bulk instead of per-thread gathers: the sums
+// run in the same order, so the heights are bit-identical.  Block b owns
+// the vertices xv_start[b] .. xv_start[b+1]-1 (contiguous, about equal
+// incidence count).  A vertex row is cut into 2 KB segments (512 FP32 or 256
+// FP64 values); a unit is one (vertex, segment) and a batch is up to R
+// incident rows of a unit.  One producer warp walks the units segment by
+// segment (all of the block's vertices for segment 0, then segment 1, ...),
+// reads inc_ptr and 1/delta 32 vertices at a time and the incidence list
+// through a window of 64 entries held in its lanes (the lists of a block's
+// vertices are contiguous), and issues one bulk copy per row into a ring of
+// S stages; four consumer warps (one 16-byte vector per thread) add the
+// rows in list order and write the unit's heights after its last batch,
+// with the commodity data of their values (s, t, d, 1/d) held in registers
+// for the whole segment.  Full and empty mbarriers order the ring.  Every wait has
+// a time limit; a block whose wait runs out sets DevState::fault and stop,
+// waits (with the same limit) for the copies it issued, and leaves.
+
+constexpr int kXCons = 128;                    // consumer threads: one 16-byte vector each
+constexpr int kXThreads = kXCons + 32;         // plus the producer warp
+constexpr int kXSegBytes = kXCons * 16;        // bytes of one row segment
+constexpr long long kXWaitCycles = 4ll << 30;  // about 2 s at the SM clock
+constexpr int kXFirst = 1, kXLast = 2, kXEnd = 4;
+
+struct XDesc {
+    int32_t i, c, nrows, flags;
+    uint32_t sign;  // bit r: row r of the batch is an in-edge (added), else an out-edge
+    int32_t deg;    // delta_i
+    double idg;     // 1/delta_i in the working precision (exact in double)
+};
+
+template <int S, int R>
+constexpr size_t excess_bulk_smem()
+{
+    return (size_t)S * R * kXSegBytes + (size_t)S * (2 * sizeof(uint64_t) + sizeof(XDesc));
+}
+
+// S stages of R row segments
+template <typename T, int S, int R>
+__global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
+{
+    using VT = typename VecOf<T>::type;
+    using A = Acc<T>;
+    constexpr int N = VecOf<T>::N;
+    constexpr int W = kXSegBytes / (int)sizeof(T);  // values per segment
+    extern __shared__ __align__(128) unsigned char xsm[];
+    unsigned char* ring = xsm;
+    uint64_t* full = reinterpret_cast<uint64_t*>(xsm + (size_t)S * R * kXSegBytes);
+    uint64_t* empty = full + S;
+    XDesc* desc = reinterpret_cast<XDesc*>(empty + S);
+
+    const int block = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x >= kXCons;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kXCons / 32);
+        }
+        mbar_init_fence();
+    }
+    // The adjacency and the commodity data do not change during a solve:
+    // read the first of them before waiting for the previous kernel.
+    // Producer lane l: inc_ptr and 1/delta of vertex vlo + l (and of
+    // vlo + 32 + l), incidence entries wb0 + l and wb0 + 32 + l.
+    // Consumer: the commodity data of its values in segment 0.
+    const int32_t vlo = a.xv_start[block], vhi = a.xv_start[block + 1];
+    const int nseg = (a.Kp + W - 1) / W;
+    const int64_t ninc = 2 * a.m;
+    const int64_t vlim = (int64_t)a.n;
+    int64_t ip0 = 0, ipn0 = 0, wb0 = 0;
+    T dg0 = T(0), dgn0 = T(0);
+    int32_t cur0 = 0, nxt0 = 0;
+    T dk[N], idk[N];
+    int32_t sk[N], tk[N];
+    const int tid = threadIdx.x;
+    bool mine = tid * N < a.Kp;  // consumer: this thread's values exist in segment 0
+    if (producer) {
+        ip0 = vlo + lane <= vlim ? a.inc_ptr[vlo + lane] : 0;
+        ipn0 = vlo + 32 + lane <= vlim ? a.inc_ptr[vlo + 32 + lane] : 0;
+        dg0 = vlo + lane < vlim ? a.inv_deg[vlo + lane] : T(0);
+        dgn0 = vlo + 32 + lane < vlim ? a.inv_deg[vlo + 32 + lane] : T(0);
+        wb0 = __shfl_sync(kFull, ip0, 0);
+        cur0 = wb0 + lane < ninc ? a.inc[wb0 + lane] : 0;
+        nxt0 = wb0 + 32 + lane < ninc ? a.inc[wb0 + 32 + lane] : 0;
+    } else if (mine) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            sk[q] = a.s[tid * N + q];
+            tk[q] = a.t[tid * N + q];
+            dk[q] = a.dem[tid * N + q];
+            idk[q] = a.inv_dem[tid * N + q];
+        }
+    }
+
+    pdl_wait();
+    pdl_trigger();  // one wave
+    volatile DevState* vst = a.st;
+    __shared__ int skip;  // one read of the stop flag for the whole block
+    if (threadIdx.x == 0) skip = a.mode == MODE_SOLVE && vst->stop;
+    __syncthreads();
+    if (skip) return;
+    if (block == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
+
+    typename A::V zacc = A::zero();
+    T cons = T(0);
+    bool ok = true;
+    if (producer) {
+        // producer warp; every branch below is warp-uniform
+        uint32_t j = 0;
+        // units in segment-major order: every vertex of the range for segment 0, then 1, ...
+        for (int c = 0; c < nseg && ok; ++c) {
+            const int width = min(W, a.Kp - c * W);
+            const uint32_t bytes = (uint32_t)width * (uint32_t)sizeof(T);
+            int64_t ip = ip0, ipn = ipn0, wb = wb0;
+            T dg = dg0, dgn = dgn0;
+            int32_t cur = cur0, nxt = nxt0;
+            int32_t vb = vlo;
+            for (int32_t i = vlo; i < vhi && ok; ++i) {
+                if (i - vb == 32) {  // next 32 vertices
+                    vb += 32;
+                    ip = ipn;
+                    dg = dgn;
+                    ipn = (int64_t)vb + 32 + lane <= vlim ? a.inc_ptr[vb + 32 + lane] : 0;
+                    dgn = (int64_t)vb + 32 + lane < vlim ? a.inv_deg[vb + 32 + lane] : T(0);
+                }
+                const int o = i - vb;
+                const int64_t q0 = __shfl_sync(kFull, ip, o);
+                const int64_t q1a = __shfl_sync(kFull, ip, (o + 1) & 31), q1b = __shfl_sync(kFull, ipn, 0);
+                const int64_t q1 = o < 31 ? q1a : q1b;
+                const T idg = __shfl_sync(kFull, dg, o);
+                if (q0 >= wb + 64) {  // keep wb <= q0 < wb + 32
+                    wb = q0;
+                    cur = wb + lane < ninc ? a.inc[wb + lane] : 0;
+                    nxt = wb + 32 + lane < ninc ? a.inc[wb + 32 + lane] : 0;
+                } else if (q0 >= wb + 32) {
+                    cur = nxt;
+                    wb += 32;
+                    nxt = wb + 32 + lane < ninc ? a.inc[wb + 32 + lane] : 0;
+                }
+                for (int64_t r0 = q0;; r0 += R) {
+                    const int nr = (int)(q1 - r0 < R ? q1 - r0 : R);  // 0: isolated vertex
+                    const int slot = (int)(j % S);
+                    const uint32_t ph = (j / S) & 1u;
+                    if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, kXWaitCycles))) {
+                        ok = false;
+                        break;
+                    }
+                    const int64_t r = r0 + lane, off = r - wb;  // off >= 0
+                    const int32_t from_cur = __shfl_sync(kFull, cur, (int)(off & 31));
+                    const int32_t from_nxt = __shfl_sync(kFull, nxt, (int)(off & 31));
+                    int32_t ev = 0;
+                    if (lane < nr) ev = off < 32 ? from_cur : (off < 64 ? from_nxt : a.inc[r]);
+                    const uint32_t sign = __ballot_sync(kFull, lane < nr && ev >= 0);
+                    if (lane == 0) {
+                        XDesc& d = desc[slot];
+                        d.i = i;
+                        d.c = c;
+                        d.nrows = nr;
+                        d.sign = sign;
+                        d.deg = (int32_t)(q1 - q0);
+                        d.flags = (r0 == q0 ? kXFirst : 0) | (r0 + R >= q1 ? kXLast : 0);
+                        d.idg = (double)idg;
+                        mbar_arrive_expect_tx(&full[slot], (uint32_t)nr * bytes);
+                    }
+                    __syncwarp();
+                    if (lane < nr) {
+                        const int64_t e = ev >= 0 ? ev : ~ev;
+                        bulk_g2s(ring + ((size_t)slot * R + lane) * kXSegBytes, a.f + e * a.Kp + (int64_t)c * W,
+                                 bytes, &full[slot]);
+                    }
+                    ++j;
+                    if (r0 + R >= q1) break;
+                }
+            }
+        }
+        if (ok) {  // end marker
+            const int slot = (int)(j % S);
+            const uint32_t ph = (j / S) & 1u;
+            if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, kXWaitCycles))) {
+                ok = false;
+            } else if (lane == 0) {
+                desc[slot].flags = kXEnd;
+                desc[slot].nrows = 0;
+                mbar_arrive(&full[slot]);
+            }
+        }
+        if (!ok) {
+            // wait (limited) for the copies of the last S batches, then leave
+            for (uint32_t q = j > (uint32_t)S ? j - S : 0; q < j; ++q) mbar_wait(&full[q % S], (q / S) & 1u, kXWaitCycles);
+        }
+    } else {
+        // consumers: thread tid holds values tid*N .. tid*N+N-1 of the segment;
+        // the commodity data of those values is reloaded when the segment changes
+        T acc[N];
+        int cs = 0;
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = T(0);
+        for (uint32_t j = 0;; ++j) {
+            const int slot = (int)(j % S);
+            const uint32_t ph = (j / S) & 1u;
+            if (!__all_sync(kFull, mbar_wait(&full[slot], ph, kXWaitCycles))) {
+                ok = false;
+                break;
+            }
+            const XDesc d = desc[slot];
+            if (d.flags & kXEnd) break;
+            if (d.c != cs) {
+                cs = d.c;
+                const int k0 = cs * W + tid * N;
+                mine = k0 < a.Kp && tid * N < W;
+                if (mine) {
+#pragma unroll
+                    for (int q = 0; q < N; ++q) {
+                        sk[q] = a.s[k0 + q];
+                        tk[q] = a.t[k0 + q];
+                        dk[q] = a.dem[k0 + q];
+                        idk[q] = a.inv_dem[k0 + q];
+                    }
+                }
+            }
+            if (d.flags & kXFirst) {
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc[q] = T(0);
+            }
+            if (mine) {
+                const VT* rows = reinterpret_cast<const VT*>(ring + (size_t)slot * R * kXSegBytes) + tid;
+                for (int r = 0; r < d.nrows; ++r) {
+                    T x[N];
+                    unpack(rows[r * (kXSegBytes / 16)], x);
+                    const bool add = (d.sign >> r) & 1u;
+#pragma unroll
+                    for (int q = 0; q < N; ++q) acc[q] = add ? acc[q] + x[q] : acc[q] - x[q];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if ((d.flags & kXLast) && mine) {
+                const int32_t i = d.i;
+#pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    if (sk[q] == i) acc[q] += dk[q];
+                    else if (tk[q] == i) acc[q] -= dk[q];
+                }
+                const T dgt = T(d.deg);
+                const T idg = (T)d.idg;
+                T hv[N];
+#pragma unroll
+                for (int q = 0; q < N; ++q) hv[q] = acc[q] * idg;
+                reinterpret_cast<VT*>(a.h + (int64_t)i * a.Kp + cs * W + tid * N)[0] = pack4(hv);
+                T zt = T(0);
+#pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    zt += dgt * hv[q] * hv[q];
+                    const T rr = fabs(acc[q]) * idk[q];
+                    cons = rr > cons ? rr : cons;
+                }
+                zacc = A::add(zacc, zt);
+            }
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) {
+            a.st->fault = 1;
+            a.st->stop = 1;
+        }
+    }
+    excess_tail<T>(a, block, gridDim.x, zacc, cons);
+}
+
+// xv_start[b] = the first vertex i with inc_ptr[i] + 2 i >= b * (inc_ptr[n] + 2 n) / grid
+__global__ void excess_split_kernel(const int64_t* inc_ptr, int32_t n, int grid, int32_t* xv_start)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > grid) return;
+    const int64_t total = inc_ptr[n] + 2 * (int64_t)n;
+    const int64_t target = total / grid * b + total % grid * b / grid;  // floor(total * b / grid)
+    int32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo) / 2;
+        if (inc_ptr[mid] + 2 * (int64_t)mid >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    xv_start[b] = lo;
 }
 
 // ------------------------------------------------------------------ the root search of Alg. 2
@@ -897,16 +1199,16 @@ template int excess_resident_blocks<double>();
 // until that kernel has finished and its writes are visible.
 template <typename T>
 cudaError_t launch_one(void (*kernel)(SweepArgs<T>), int grid, int block, cudaStream_t stream, bool pdl,
-                       const SweepArgs<T>& a)
+                       const SweepArgs<T>& a, size_t smem = 0)
 {
     if (!pdl) {
-        kernel<<<grid, block, 0, stream>>>(a);
+        kernel<<<grid, block, smem, stream>>>(a);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr{};
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -919,7 +1221,46 @@ cudaError_t launch_one(void (*kernel)(SweepArgs<T>), int grid, int block, cudaSt
 template <typename T>
 cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream, bool pdl)
 {
-    return launch_one<T>(excess_kernel<T>, a.grid_v, kThreads, stream, pdl, a);
+    switch (a.excess_form) {
+    case 1: return launch_one<T>(excess_bulk_kernel<T, 4, 8>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<4, 8>());
+    case 2: return launch_one<T>(excess_bulk_kernel<T, 2, 8>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<2, 8>());
+    case 3: return launch_one<T>(excess_bulk_kernel<T, 4, 4>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<4, 4>());
+    default: return launch_one<T>(excess_kernel<T>, a.grid_v, kThreads, stream, pdl, a);
+    }
+}
+
+template <typename T, int S, int R>
+int bulk_resident()
+{
+    const size_t smem = excess_bulk_smem<S, R>();
+    int blocks = 0;
+    if (cudaFuncSetAttribute(excess_bulk_kernel<T, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, excess_bulk_kernel<T, S, R>, kXThreads, smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
+}
+
+template <typename T>
+int excess_bulk_resident_blocks(int form)
+{
+    switch (form) {
+    case 1: return bulk_resident<T, 4, 8>();
+    case 2: return bulk_resident<T, 2, 8>();
+    case 3: return bulk_resident<T, 4, 4>();
+    default: return 0;
+    }
+}
+template int excess_bulk_resident_blocks<float>(int);
+template int excess_bulk_resident_blocks<double>(int);
+
+cudaError_t launch_excess_split(const int64_t* inc_ptr, int32_t n, int grid, int32_t* xv_start, cudaStream_t stream)
+{
+    excess_split_kernel<<<(grid + 1 + 255) / 256, 256, 0, stream>>>(inc_ptr, n, grid, xv_start);
+    return cudaGetLastError();
 }
 
 template <typename T>

@@ -52,6 +52,7 @@ class Options(C.Structure):
         ("eps_rel", C.c_double), ("max_sweeps", C.c_int64), ("trace_len", C.c_int32), ("algo", C.c_int32),
         ("beta_init", C.c_double), ("beta_min", C.c_double), ("beta_max", C.c_double), ("alpha_inc", C.c_double),
         ("alpha_dec", C.c_double), ("gamma", C.c_double), ("edge_variant", C.c_int32),
+        ("excess_variant", C.c_int32),
     ]
 
 
