@@ -501,8 +501,16 @@ __device__ __forceinline__ void above(const T (&c)[V][N], T w, T& S, int& n, T& 
             }
         }
     S = group_sum<G>(sl);
-    n = group_sum<G>(nl);
-    mn = group_min<G>(ml);
+    if constexpr (G == 32 && sizeof(T) == 4) {
+        // whole-warp groups: one redux each for the count and the minimum
+        // (every counted x exceeds w >= 0, so ml is positive or +inf and its
+        // bit pattern orders as an unsigned integer)
+        n = (int)__reduce_add_sync(kFull, (unsigned)nl);
+        mn = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(ml)));
+    } else {
+        n = group_sum<G>(nl);
+        mn = group_min<G>(ml);
+    }
 }
 
 // Case decision and root from the sums above a threshold w >= 0 that is known
@@ -828,8 +836,13 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
             }
         }
     sl = group_sum<32>(sl);
-    nl = group_sum<32>(nl);
-    ml = group_min<32>(ml);
+    if constexpr (sizeof(T) == 4) {  // as in above(): ml is positive or +inf
+        nl = (int)__reduce_add_sync(kFull, (unsigned)nl);
+        ml = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(ml)));
+    } else {
+        nl = group_sum<32>(nl);
+        ml = group_min<32>(ml);
+    }
     const int wi = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         sa[wi] = sl;
