@@ -207,6 +207,39 @@ pdr_status pdr_set_flows(pdr_ctx *ctx, const double *f);
 /* Copies the current flows to host f[m*K] (double, edge-major). */
 pdr_status pdr_flows(pdr_ctx *ctx, double *f);
 
+/* Checkpoint and resume of a solve (the loop state of Alg. 1, 3 and 4).
+ * The checkpoint is a host byte buffer, opaque, for one library version.  It
+ * holds the current flows in the working precision and the warm starts of
+ * the edge QPs.  For Alg. 3/4 it also holds the learning rates, and for
+ * Alg. 4 the velocities.  It further holds the iteration counter t, the
+ * previous objective z^(t-1) and the objective trace so far.
+ *
+ * pdr_state_size writes the buffer size the next pdr_get_state needs.
+ * pdr_get_state fills buf with `bytes` >= that size; the caller owns buf.
+ * Both synchronise the context's stream.
+ *
+ * pdr_set_state restores a checkpoint into a context.  The context must
+ * come from the same instance sizes (n, m, K) and algorithm.  Its precision
+ * option must admit the checkpoint's working precision: FP32 checkpoints
+ * need FP32 or FP32 with FP64 tail; FP64 checkpoints need FP64 or FP32
+ * with FP64 tail.  The next pdr_solve then continues the interrupted solve
+ * instead of starting at t = 0: it uses the same sweep counter, stop rules
+ * and trace slots.  The flows of every later sweep are bit-identical to the
+ * uninterrupted solve's.  The objective partials are recomputed from the
+ * restored flows, so z agrees to rounding.  A checkpoint taken after a
+ * stopped solve resumes at the sweep that stopped; with a larger
+ * max_sweeps, it goes on from there.  pdr_sweeps also continues the
+ * counter.  pdr_reset and pdr_set_flows cancel a pending resume.
+ *
+ * Errors:
+ * - PDR_ERR_INVALID_ARG: NULL arguments; a buffer too small, truncated or
+ *   of another version; a checkpoint of other sizes, another algorithm or
+ *   an inadmissible precision.
+ * - PDR_ERR_CUDA. */
+pdr_status pdr_state_size(pdr_ctx *ctx, int64_t *bytes);
+pdr_status pdr_get_state(pdr_ctx *ctx, void *buf, int64_t bytes);
+pdr_status pdr_set_state(pdr_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Selected rows of the current state: out[q*K + k] = f_{edges[q],k}
  * (which = 0) or the Alg. 4 velocity v_{edges[q],k} (which = 1), for
  * q < count (double).  For checking large instances edge by edge without

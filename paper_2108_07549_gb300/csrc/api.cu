@@ -127,7 +127,10 @@ struct pdr_ctx {
     float *f32[2] = {nullptr, nullptr}, *h32 = nullptr, *inv_deg_f = nullptr;
     double *f64[2] = {nullptr, nullptr}, *h64 = nullptr, *inv_deg_d = nullptr;
     int cur = 0;  // buffer holding the current flows
-    double* theta = nullptr;  // [m] warm starts, 8 bytes per edge covers both precisions
+    // [m] roots of the edge QPs, double-buffered like the flows: theta[b] holds
+    // the roots of the sweep that produced the flows in buffer b (the warm
+    // starts of the next sweep); 8 bytes per edge covers both precisions
+    double* theta[2] = {nullptr, nullptr};
     // Alg. 3 / Alg. 4 state, double-buffered like the flows
     double* beta_buf[2] = {nullptr, nullptr};  // [m], 8 bytes per edge covers both precisions
     float* v32[2] = {nullptr, nullptr};
@@ -167,6 +170,10 @@ struct pdr_ctx {
 
     pdr_result last{};
     std::string err;
+    // checkpoint / resume: the next pdr_solve continues the restored sweep
+    // counter and objective instead of starting afresh
+    bool resume_pending = false;
+    int64_t t_widen = -1;  // t at which the FP64 tail of the last solve began (-1: none)
 
     pdr_status fail(pdr_status code, const std::string& msg)
     {
@@ -258,8 +265,9 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.inv_scale = ctx->inv_scale;
     a.inv_scale_t = Prec<T>::inv_scale(ctx);
     a.inv_deg = Prec<T>::inv_deg(ctx);
-    a.theta = reinterpret_cast<T*>(ctx->theta);
     const int b = ((base < 0 ? ctx->cur : base) ^ par) & 1;
+    a.theta_in = reinterpret_cast<const T*>(ctx->theta[b]);
+    a.theta = reinterpret_cast<T*>(ctx->theta[b ^ 1]);
     a.f = Prec<T>::f(ctx, b);
     a.f_out = Prec<T>::f(ctx, b ^ 1);
     a.beta_in = reinterpret_cast<const T*>(ctx->beta_buf[b]);
@@ -400,6 +408,8 @@ pdr_status flows_to_buffer0(pdr_ctx* ctx)
                            ctx->stream));
     if (ctx->opt.algo == PDR_ALGO_GDM && bytes && Prec<T>::v(ctx, 1))
         CK(cudaMemcpyAsync(Prec<T>::v(ctx, 0), Prec<T>::v(ctx, 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->m > 0)
+        CK(cudaMemcpyAsync(ctx->theta[0], ctx->theta[1], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->cur = 0;
     return PDR_OK;
 }
@@ -417,7 +427,8 @@ pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr, bool keep_theta = fal
 {
     if (!psi_out && !keep_theta) {
         // new flows: the edge QPs start their root search cold
-        CK(cudaMemsetAsync(ctx->theta, 0, sizeof(double) * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
+        for (int b = 0; b < 2; ++b)
+            CK(cudaMemsetAsync(ctx->theta[b], 0, sizeof(double) * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
     }
     SweepArgs<T> a = make_args<T>(ctx, MODE_PSI);
     a.psi_out = psi_out;
@@ -482,11 +493,12 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
 
 __global__ void set_state_kernel(DevState* st, DevState v) { *st = v; }
 
-pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise)
+pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise, bool keep_zprev = false)
 {
+    if (fresh) ctx->resume_pending = false;
     DevState v{};
     v.z = 0.0;
-    v.z_prev = INFINITY;
+    v.z_prev = keep_zprev ? ctx->hst->z_prev : INFINITY;
     v.dz = 0.0;
     v.eps_obj = ctx->opt.eps_obj;
     v.resid_tol = ctx->opt.resid_tol;
@@ -589,9 +601,10 @@ pdr_status widen_to_fp64(pdr_ctx* ctx)
     CK(launch_convert_f32_to_f64(ctx->f32[ctx->cur], ctx->f64[0], (int64_t)ctx->m * ctx->Kp, ctx->stream));
     if (is_gd(ctx->opt) && ctx->m > 0) {
         // learning rates (and velocities) follow the flows into FP64
-        CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta, ctx->m,
+        // (through a root buffer as scratch: the FP64 phase starts its root searches cold)
+        CK(launch_convert_f32_to_f64(reinterpret_cast<const float*>(ctx->beta_buf[ctx->cur]), ctx->theta[0], ctx->m,
                                      ctx->stream));
-        CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->theta, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice,
+        CK(cudaMemcpyAsync(ctx->beta_buf[0], ctx->theta[0], sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice,
                            ctx->stream));
         if (ctx->opt.algo == PDR_ALGO_GDM) {
             s = ensure_velocity<double>(ctx);
@@ -708,6 +721,10 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     }
     if (s != PDR_OK) return s;
     ctx->cur = (int)((ctx->hst->t - t_start) & 1);
+    // The sweep that stopped also ran its edge QPs (their output is
+    // discarded) and wrote their congestion partials: recompute those of the
+    // returned flows f^(t), keeping the warm starts.
+    if (ctx->hst->stop) return refresh_psi<T>(ctx, nullptr, true);
     return PDR_OK;
 }
 
@@ -867,11 +884,11 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             return cleanup(), ctx->fail(PDR_ERR_OOM, "adjoint allocation failed");
     }
     // forward from f = 0 (pdr_backward reset the flows), cold roots
-    T* theta = reinterpret_cast<T*>(ctx->theta);
     for (int64_t t = 0; t < Tn; ++t) {
-        if (grads && t % C == 0) {
+        if (grads && t % C == 0) {  // the flows and the warm starts sweep t reads
             CKB(cudaMemcpyAsync(ck[t / C], Prec<T>::f(ctx, ctx->cur), sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
-            CKB(cudaMemcpyAsync(thck[t / C], theta, sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+            CKB(cudaMemcpyAsync(thck[t / C], ctx->theta[ctx->cur], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
         }
         SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
         CKB(launch_excess<T>(a, ctx->stream));
@@ -892,14 +909,18 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     for (int64_t sgi = nseg - 1; grads && sgi >= 0; --sgi) {
         const int64_t t0 = sgi * C, t1 = (t0 + C < Tn) ? t0 + C : Tn;
         CKB(cudaMemcpyAsync(seg[0], ck[sgi], sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
-        CKB(cudaMemcpyAsync(theta, thck[sgi], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        CKB(cudaMemcpyAsync(ctx->theta[0], thck[sgi], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
         for (int64_t t = t0; t < t1; ++t) {  // recompute f^(t0+1..t1-1), record each sweep's roots
+            const int rb = (int)((t - t0) & 1);
             SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
             a.f = seg[t - t0];
             a.f_out = seg[t - t0 + 1];
+            a.theta_in = reinterpret_cast<const T*>(ctx->theta[rb]);
+            a.theta = reinterpret_cast<T*>(ctx->theta[rb ^ 1]);
             CKB(launch_excess<T>(a, ctx->stream));
             CKB(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
-            CKB(cudaMemcpyAsync(th[t - t0], theta, sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+            CKB(cudaMemcpyAsync(th[t - t0], ctx->theta[rb ^ 1], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
         }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
@@ -942,7 +963,7 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->deg, ctx->s, ctx->t,
                    ctx->u_d, ctx->dem_d, ctx->inv_scale, ctx->u_f, ctx->dem_f, ctx->inv_dem_f, ctx->inv_dem_d,
                    ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
-                   ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta,
+                   ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta[0], ctx->theta[1],
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
                    ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3]};
     for (void* p : dev)
@@ -1044,7 +1065,8 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_scale_f, float, m);
     ALLOC(ctx->inv_deg_f, float, n);
     ALLOC(ctx->inv_deg_d, double, n);
-    ALLOC(ctx->theta, double, m);
+    ALLOC(ctx->theta[0], double, m);
+    ALLOC(ctx->theta[1], double, m);
     ALLOC(ctx->beta_buf[0], double, m);
     ALLOC(ctx->beta_buf[1], double, m);
     ALLOC(ctx->dem_d, double, Kp);
@@ -1262,6 +1284,169 @@ pdr_status pdr_flows(pdr_ctx* ctx, double* f)
     if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
     return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64[ctx->cur], ctx->m, f)
                          : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
+}
+
+// ------------------------------------------------------------------ checkpoint / resume
+//
+// A checkpoint holds, in the working precision and in this order: a header,
+// the flows (m x Kp), the warm starts (m), the Alg. 3/4 rates (m, Alg. 3/4
+// only), the Alg. 4 velocities (m x Kp, Alg. 4 only) and the objective
+// trace so far.  Restoring it and solving on gives the flows of the
+// uninterrupted solve bit for bit (a sweep depends only on these).
+
+namespace {
+constexpr uint32_t kStateMagic = 0x53524450u;  // "PDRS"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t n, K, Kp, algo, prec, stopped;
+    int64_t m, t, evals, t_widen, ntrace;
+    double z_prev, z;
+};
+
+struct StateLayout {
+    int64_t f, theta, beta, v, trace, total;  // byte counts (total includes the header)
+};
+
+StateLayout state_layout(const pdr_ctx* ctx, int prec, int64_t ntrace)
+{
+    const int64_t sz = prec ? 8 : 4, fm = (int64_t)ctx->m * ctx->Kp;
+    StateLayout L{};
+    L.f = sz * fm;
+    L.theta = sz * ctx->m;
+    L.beta = is_gd(ctx->opt) ? sz * ctx->m : 0;
+    L.v = ctx->opt.algo == PDR_ALGO_GDM ? sz * fm : 0;
+    L.trace = 8 * ntrace;
+    L.total = (int64_t)sizeof(StateHeader) + L.f + L.theta + L.beta + L.v + L.trace;
+    return L;
+}
+
+int64_t trace_kept(const pdr_ctx* ctx)
+{
+    const int64_t e = ctx->hst->evals;
+    return e < ctx->trace_cap ? e : ctx->trace_cap;
+}
+
+void* dev_v(pdr_ctx* ctx, int prec, int b) { return prec ? (void*)ctx->v64[b] : (void*)ctx->v32[b]; }
+void* dev_f(pdr_ctx* ctx, int prec, int b) { return prec ? (void*)ctx->f64[b] : (void*)ctx->f32[b]; }
+}  // namespace
+
+pdr_status pdr_state_size(pdr_ctx* ctx, int64_t* bytes)
+{
+    if (!ctx || !bytes) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "bytes is NULL") : PDR_ERR_INVALID_ARG;
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    *bytes = state_layout(ctx, ctx->cur_prec, trace_kept(ctx)).total;
+    return PDR_OK;
+}
+
+pdr_status pdr_get_state(pdr_ctx* ctx, void* buf, int64_t bytes)
+{
+    if (!ctx || !buf) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "buf is NULL") : PDR_ERR_INVALID_ARG;
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    const int prec = ctx->cur_prec;
+    const int64_t ntrace = trace_kept(ctx);
+    const StateLayout L = state_layout(ctx, prec, ntrace);
+    if (bytes < L.total) return ctx->fail(PDR_ERR_INVALID_ARG, "buffer smaller than pdr_state_size");
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = kStateVersion;
+    h.n = ctx->n;
+    h.K = ctx->K;
+    h.Kp = ctx->Kp;
+    h.algo = ctx->opt.algo;
+    h.prec = prec;
+    h.stopped = ctx->hst->stop;
+    h.m = ctx->m;
+    h.t = ctx->hst->t;
+    h.evals = ctx->hst->evals;
+    h.t_widen = ctx->t_widen;
+    h.ntrace = ntrace;
+    h.z_prev = ctx->hst->z_prev;
+    h.z = ctx->hst->z;
+    char* out = static_cast<char*>(buf);
+    std::memcpy(out, &h, sizeof h);
+    char* q = out + sizeof h;
+    if (L.f) CK(cudaMemcpyAsync(q, dev_f(ctx, prec, ctx->cur), L.f, cudaMemcpyDeviceToHost, ctx->stream));
+    q += L.f;
+    if (L.theta) CK(cudaMemcpyAsync(q, ctx->theta[ctx->cur], L.theta, cudaMemcpyDeviceToHost, ctx->stream));
+    q += L.theta;
+    if (L.beta) CK(cudaMemcpyAsync(q, ctx->beta_buf[ctx->cur], L.beta, cudaMemcpyDeviceToHost, ctx->stream));
+    q += L.beta;
+    if (L.v) {
+        const void* v = dev_v(ctx, prec, ctx->cur);
+        if (v) CK(cudaMemcpyAsync(q, v, L.v, cudaMemcpyDeviceToHost, ctx->stream));
+        else std::memset(q, 0, (size_t)L.v);  // no Alg. 4 sweep has run: v = 0
+    }
+    q += L.v;
+    if (L.trace) CK(cudaMemcpyAsync(q, ctx->trace, L.trace, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PDR_OK;
+}
+
+pdr_status pdr_set_state(pdr_ctx* ctx, const void* buf, int64_t bytes)
+{
+    if (!ctx || !buf) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "buf is NULL") : PDR_ERR_INVALID_ARG;
+    if (bytes < (int64_t)sizeof(StateHeader)) return ctx->fail(PDR_ERR_INVALID_ARG, "buffer too small");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kStateMagic || h.version != kStateVersion)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "not a checkpoint of this library version");
+    if (h.n != ctx->n || h.m != ctx->m || h.K != ctx->K || h.Kp != ctx->Kp)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "checkpoint of an instance of other sizes");
+    if (h.algo != ctx->opt.algo) return ctx->fail(PDR_ERR_INVALID_ARG, "checkpoint of another algorithm");
+    if (h.prec != 0 && h.prec != 1) return ctx->fail(PDR_ERR_INVALID_ARG, "bad precision in checkpoint");
+    if (h.prec == 1 && ctx->opt.precision == PDR_PREC_FP32)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "an FP64 checkpoint needs precision FP64 or FP32 with FP64 tail");
+    if (h.prec == 0 && ctx->opt.precision == PDR_PREC_FP64)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "an FP32 checkpoint needs precision FP32 or FP32 with FP64 tail");
+    if (h.t < 0 || h.evals < 0 || h.ntrace < 0 || h.ntrace > h.evals)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "bad counters in checkpoint");
+    const StateLayout L = state_layout(ctx, h.prec, h.ntrace);
+    if (bytes < L.total) return ctx->fail(PDR_ERR_INVALID_ARG, "checkpoint truncated");
+    ctx->cur_prec = h.prec;
+    pdr_status s = h.prec ? ensure_fp64(ctx) : ensure_fp32(ctx);
+    if (s != PDR_OK) return s;
+    if (L.v) {
+        s = h.prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
+        if (s != PDR_OK) return s;
+    }
+    ctx->cur = 0;
+    const char* q = static_cast<const char*>(buf) + sizeof h;
+    if (L.f) CK(cudaMemcpyAsync(dev_f(ctx, h.prec, 0), q, L.f, cudaMemcpyHostToDevice, ctx->stream));
+    q += L.f;
+    if (L.theta) CK(cudaMemcpyAsync(ctx->theta[0], q, L.theta, cudaMemcpyHostToDevice, ctx->stream));
+    q += L.theta;
+    if (L.beta) CK(cudaMemcpyAsync(ctx->beta_buf[0], q, L.beta, cudaMemcpyHostToDevice, ctx->stream));
+    q += L.beta;
+    if (L.v) CK(cudaMemcpyAsync(dev_v(ctx, h.prec, 0), q, L.v, cudaMemcpyHostToDevice, ctx->stream));
+    q += L.v;
+    const int64_t nt = h.ntrace < ctx->trace_cap ? h.ntrace : ctx->trace_cap;
+    if (nt > 0) CK(cudaMemcpyAsync(ctx->trace, q, 8 * nt, cudaMemcpyHostToDevice, ctx->stream));
+    s = h.prec ? refresh_psi<double>(ctx, nullptr, true) : refresh_psi<float>(ctx, nullptr, true);
+    if (s != PDR_OK) return s;
+    // The device state between sweeps t-1 and t.  A checkpoint taken after a
+    // stop holds f^(t) with sweep t evaluated but not applied: the resumed
+    // solve evaluates it again, in the same trace slot.
+    DevState v{};
+    v.z = h.z;
+    v.z_prev = h.z_prev;
+    v.eps_obj = ctx->opt.eps_obj;
+    v.resid_tol = ctx->opt.resid_tol;
+    v.eps_rel = ctx->opt.eps_rel;
+    v.t = h.t;
+    v.max_sweeps = ctx->opt.max_sweeps;
+    v.trace_len = ctx->trace_cap;
+    v.evals = h.stopped && h.evals > 0 ? h.evals - 1 : h.evals;
+    set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, v);
+    CK(cudaGetLastError());
+    s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    ctx->t_widen = h.t_widen;
+    ctx->resume_pending = true;
+    return PDR_OK;
 }
 
 pdr_status pdr_backward(pdr_ctx* ctx, int64_t T, int32_t ckpt_every, double* L, double* grad_u, double* grad_d)
@@ -1523,14 +1708,17 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     if (!ctx) return PDR_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     const bool tail = ctx->opt.precision == PDR_PREC_FP32_FP64TAIL;
-    pdr_status s = init_state(ctx, true, (tail && ctx->cur_prec == 0) ? 1 : 0);
+    const bool resume = ctx->resume_pending;  // continue a restored checkpoint
+    ctx->resume_pending = false;
+    pdr_status s = init_state(ctx, !resume, (tail && ctx->cur_prec == 0) ? 1 : 0, resume);
     if (s != PDR_OK) return s;
-    int64_t sweeps32 = 0;
-    s = ctx->cur_prec ? run_phase<double>(ctx, 0) : run_phase<float>(ctx, 0);
+    if (!resume) ctx->t_widen = -1;
+    const int64_t t_start = resume ? ctx->hst->t : 0;
+    s = ctx->cur_prec ? run_phase<double>(ctx, t_start) : run_phase<float>(ctx, t_start);
     if (s != PDR_OK) return s;
-    if (ctx->cur_prec == 0) sweeps32 = ctx->hst->t;
     const int r = ctx->hst->reason;
     if (tail && ctx->cur_prec == 0 && needs_fp64_tail(r)) {
+        ctx->t_widen = ctx->hst->t;
         s = widen_to_fp64(ctx);
         if (s != PDR_OK) return s;
         s = init_state(ctx, false, 0);
@@ -1540,7 +1728,7 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     }
     pdr_result res{};
     res.sweeps = ctx->hst->t;
-    res.sweeps_fp64 = ctx->cur_prec ? ctx->hst->t - sweeps32 : 0;
+    res.sweeps_fp64 = ctx->cur_prec ? ctx->hst->t - (ctx->t_widen >= 0 ? ctx->t_widen : 0) : 0;
     res.dz = ctx->hst->dz;
     res.stop_reason = ctx->hst->reason;
     s = residuals_into(ctx, &res);

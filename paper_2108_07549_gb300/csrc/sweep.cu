@@ -649,7 +649,7 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
         T psi;
         if (!psi_only) {
             // warm start slightly below the previous sweep's root
-            const T w = valid ? a.theta[e] * T(0.999) : T(0);
+            const T w = valid ? a.theta_in[e] * T(0.999) : T(0);
             const int den = a.ck ? 0 : 2;
             const T theta = qp_root_group<T, G, V, N>(c, ue, w, valid, a.Kp, den);
             if (valid && gl == 0) a.theta[e] = theta;
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
         T psi;
         if (!psi_only) {
             const int den = a.ck ? 0 : 2;
-            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta[e] * T(0.999), true, a.Kp, den);
+            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta_in[e] * T(0.999), true, a.Kp, den);
             if (lane == 0) a.theta[e] = theta;
             T* orow = a.f_out + e * a.Kp;
 #pragma unroll
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
         T psi;
         if (!psi_only) {
             // the lane-group search with block-wide sums, counts and minima
-            const T w0 = a.theta[e] * T(0.999);
+            const T w0 = a.theta_in[e] * T(0.999);
             const int den = a.ck ? 0 : 2;
             T S, mn, theta = T(0);
             int n, nA = 0;
@@ -1073,6 +1073,8 @@ __global__ void __launch_bounds__(kThreads, (V <= 4 ? 4 : 3))
         if (q & 1) {
             b.f = a.f_out;
             b.f_out = a.f;
+            b.theta_in = a.theta;
+            b.theta = const_cast<T*>(a.theta_in);
         }
         excess_body<T>(b, blockIdx.x, gridDim.x);
         if (!grid_sync(bar)) return;

@@ -35,6 +35,7 @@ EXPORTS = (
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
     "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
+    "pdr_state_size", "pdr_get_state", "pdr_set_state",
 )
 
 
@@ -99,6 +100,9 @@ def load(path: str = LIB_PATH):
         "pdr_reset": ([vp], i32),
         "pdr_set_flows": ([vp, vp], i32),
         "pdr_flows": ([vp, vp], i32),
+        "pdr_state_size": ([vp, P(i64)], i32),
+        "pdr_get_state": ([vp, vp, i64], i32),
+        "pdr_set_state": ([vp, vp, i64], i32),
         "pdr_heights": ([vp, vp], i32),
         "pdr_congestion": ([vp, vp], i32),
         "pdr_objective": ([vp, P(dbl)], i32),
@@ -282,6 +286,19 @@ class Solver:
         f = np.empty((self.m, self.K), dtype=np.float64)
         self._check(self._lib.pdr_flows(self._h, _ptr(f)))
         return f
+
+    def get_state(self) -> bytes:
+        """Checkpoint of the solve (pdr_get_state) as bytes."""
+        n = C.c_int64()
+        self._check(self._lib.pdr_state_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(max(n.value, 1))
+        self._check(self._lib.pdr_get_state(self._h, buf, n.value))
+        return buf.raw[: n.value]
+
+    def set_state(self, state: bytes):
+        """Restores a checkpoint (pdr_set_state); the next solve continues it."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._check(self._lib.pdr_set_state(self._h, buf, len(state)))
 
     def flow_rows(self, edges, velocities: bool = False) -> np.ndarray:
         """Rows f[e, :] (or the Alg. 4 velocities v[e, :]) for the given edge ids ([len(edges), K])."""
