@@ -54,7 +54,9 @@ typedef enum {
     PDR_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     PDR_ERR_NUMERIC = 4,     /* a non-finite objective appeared */
     PDR_ERR_NOT_SOLVED = 5,  /* reserved */
-    PDR_ERR_UNSUPPORTED = 6  /* option or size outside what this build supports */
+    PDR_ERR_UNSUPPORTED = 6, /* option or size outside what this build supports */
+    PDR_ERR_TIMEOUT = 7      /* a device-side wait ran out of its time limit; the kernel left, the
+                                solve stopped, and the context stays usable */
 } pdr_status;
 
 typedef enum {
@@ -100,7 +102,7 @@ typedef struct {
                            QPs of every sweep, separated by grid barriers, for 1024 sweeps per
                            launch (PDR_ALGO_ESO with a lane-group edge variant, K <= 1024 in FP32
                            or 512 in FP64; otherwise 1 is used); a barrier that waits more than
-                           about a second ends the solve with PDR_ERR_CUDA */
+                           about a second ends the solve with PDR_ERR_TIMEOUT */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */
@@ -239,6 +241,18 @@ pdr_status pdr_flows(pdr_ctx *ctx, double *f);
 pdr_status pdr_state_size(pdr_ctx *ctx, int64_t *bytes);
 pdr_status pdr_get_state(pdr_ctx *ctx, void *buf, int64_t bytes);
 pdr_status pdr_set_state(pdr_ctx *ctx, const void *buf, int64_t bytes);
+
+/* Test hook for the time limit of the device-side waits.
+ * - Waits: the bulk-copy excess form (pdr_options.excess_variant 1..3)
+ *   waits on shared-memory barriers.
+ * - Default limit: 2^32 SM clock cycles, about 2 s.
+ * - cycles: sets that limit; 1000 <= cycles <= 2^32.
+ * - hold_end = 1: the form's producer never posts the end marker of its
+ *   ring.  Every block's consumers then wait out the limit, with no copy in
+ *   flight, and the call that ran the sweep returns PDR_ERR_TIMEOUT.
+ * - hold_end = 0: normal operation.
+ * Errors: PDR_ERR_INVALID_ARG. */
+pdr_status pdr_debug_wait(pdr_ctx *ctx, int64_t cycles, int32_t hold_end);
 
 /* Selected rows of the current state: out[q*K + k] = f_{edges[q],k}
  * (which = 0) or the Alg. 4 velocity v_{edges[q],k} (which = 1), for

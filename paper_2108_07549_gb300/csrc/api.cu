@@ -173,6 +173,10 @@ struct pdr_ctx {
     // checkpoint / resume: the next pdr_solve continues the restored sweep
     // counter and objective instead of starting afresh
     bool resume_pending = false;
+    // device-side wait limit (cycles) and the end-marker hold of the bulk-copy
+    // excess form; changed only by pdr_debug_wait (tests of the time limit)
+    long long wait_cycles = kWaitCycles;
+    int hold_end = 0;
     int64_t t_widen = -1;  // t at which the FP64 tail of the last solve began (-1: none)
 
     pdr_status fail(pdr_status code, const std::string& msg)
@@ -289,6 +293,8 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.part_cap = reinterpret_cast<T*>(ctx->part_cap);
     a.excess_form = ctx->xform;
     a.xv_start = ctx->xv_start[ctx->xform];
+    a.wait_cycles = ctx->wait_cycles;
+    a.hold_end = ctx->hold_end;
     a.grid_v = ctx->xform ? ctx->xgrid[ctx->xform] : ctx->grid_v[p];
     a.grid_e = ctx->grid_e[p];
     a.n_psi = ctx->n_psi[p];
@@ -519,7 +525,8 @@ pdr_status read_state(pdr_ctx* ctx)
 {
     CK(cudaMemcpyAsync(ctx->hst, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->hst->fault) return ctx->fail(PDR_ERR_CUDA, "excess kernel: a shared-memory barrier wait timed out");
+    if (ctx->hst->fault)
+        return ctx->fail(PDR_ERR_TIMEOUT, "excess kernel: a shared-memory barrier wait ran out of its time limit");
     return PDR_OK;
 }
 
@@ -672,7 +679,7 @@ pdr_status run_persistent(pdr_ctx* ctx, bool* ran)
         CK(cudaMemcpyAsync(&hb, ctx->bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, ctx->stream));
         s = read_state(ctx);  // synchronises the stream
         if (s != PDR_OK) return s;
-        if (hb.failed) return ctx->fail(PDR_ERR_CUDA, "persistent sweep kernel: a grid barrier timed out");
+        if (hb.failed) return ctx->fail(PDR_ERR_TIMEOUT, "persistent sweep kernel: a grid barrier timed out");
         if (ctx->hst->stop) break;
     }
     // the other engines read the congestion partials in the standalone layout
@@ -1446,6 +1453,18 @@ pdr_status pdr_set_state(pdr_ctx* ctx, const void* buf, int64_t bytes)
     if (s != PDR_OK) return s;
     ctx->t_widen = h.t_widen;
     ctx->resume_pending = true;
+    return PDR_OK;
+}
+
+pdr_status pdr_debug_wait(pdr_ctx* ctx, int64_t cycles, int32_t hold_end)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (cycles < 1000 || cycles > kWaitCycles)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "cycles must lie in [1000, 2^32]");
+    if (hold_end != 0 && hold_end != 1) return ctx->fail(PDR_ERR_INVALID_ARG, "hold_end must be 0 or 1");
+    ctx->wait_cycles = cycles;
+    ctx->hold_end = hold_end;
+    destroy_graphs(ctx);  // the graphs captured the old launch arguments
     return PDR_OK;
 }
 

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
     constexpr int N = VecOf<T>::N;
     constexpr int GPW = 32 / G;
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_blo
     __shared__ T sa_buf[32];
     __shared__ int sb_buf[32];
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;

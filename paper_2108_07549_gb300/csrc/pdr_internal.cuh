@@ -22,6 +22,7 @@
 namespace pdr {
 
 constexpr int kThreads = 256;  // block size of every sweep kernel
+constexpr long long kWaitCycles = 4ll << 30;  // default limit of a device-side wait: ~2 s at the SM clock
 
 // Kernel modes.
 enum : int {
@@ -115,6 +116,9 @@ struct SweepArgs {
     int excess_form;    // excess kernel: 0 = per-thread gathers, 1..3 = bulk-copy pipeline
                         // (stages x row segments per block: 4 x 8, 2 x 8, 4 x 4)
     const int32_t* xv_start;  // [grid_v + 1] bulk-copy form: first vertex of each block
+    long long wait_cycles;    // bulk-copy form: time limit of a barrier wait, in SM clock cycles
+    int hold_end;             // bulk-copy form, tests only: the producer never posts its end
+                              // marker, so the consumers' last wait runs out (no copy in flight)
     int64_t n_psi;      // number of edge partials
     int64_t pf_edges;   // edge QP: L2 prefetch of the rows of edge e + pf_edges while
                         // edge e is solved (about one wave of resident edges ahead; 0: off)

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
     pdl_wait();     // the previous sweep's edge kernel has finished (no-op without PDL)
     pdl_trigger();  // one wave: the edge kernel's blocks may queue behind this one's
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     excess_body<T>(a, blockIdx.x, gridDim.x);
 }
 
@@ -197,7 +197,6 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
 constexpr int kXCons = 128;                    // consumer threads: one 16-byte vector each
 constexpr int kXThreads = kXCons + 32;         // plus the producer warp
 constexpr int kXSegBytes = kXCons * 16;        // bytes of one row segment
-constexpr long long kXWaitCycles = 4ll << 30;  // about 2 s at the SM clock
 constexpr int kXFirst = 1, kXLast = 2, kXEnd = 4;
 
 struct XDesc {
@@ -274,10 +273,7 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
     pdl_wait();
     pdl_trigger();  // one wave
     volatile DevState* vst = a.st;
-    __shared__ int skip;  // one read of the stop flag for the whole block
-    if (threadIdx.x == 0) skip = a.mode == MODE_SOLVE && vst->stop;
-    __syncthreads();
-    if (skip) return;
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (block == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
 
     typename A::V zacc = A::zero();
@@ -320,7 +316,7 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
                     const int nr = (int)(q1 - r0 < R ? q1 - r0 : R);  // 0: isolated vertex
                     const int slot = (int)(j % S);
                     const uint32_t ph = (j / S) & 1u;
-                    if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, kXWaitCycles))) {
+                    if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, a.wait_cycles))) {
                         ok = false;
                         break;
                     }
@@ -355,9 +351,9 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
         if (ok) {  // end marker
             const int slot = (int)(j % S);
             const uint32_t ph = (j / S) & 1u;
-            if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, kXWaitCycles))) {
+            if (j >= (uint32_t)S && !__all_sync(kFull, mbar_wait(&empty[slot], ph ^ 1u, a.wait_cycles))) {
                 ok = false;
-            } else if (lane == 0) {
+            } else if (lane == 0 && !a.hold_end) {  // hold_end: a test of the consumers' time limit
                 desc[slot].flags = kXEnd;
                 desc[slot].nrows = 0;
                 mbar_arrive(&full[slot]);
@@ -365,7 +361,7 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
         }
         if (!ok) {
             // wait (limited) for the copies of the last S batches, then leave
-            for (uint32_t q = j > (uint32_t)S ? j - S : 0; q < j; ++q) mbar_wait(&full[q % S], (q / S) & 1u, kXWaitCycles);
+            for (uint32_t q = j > (uint32_t)S ? j - S : 0; q < j; ++q) mbar_wait(&full[q % S], (q / S) & 1u, a.wait_cycles);
         }
     } else {
         // consumers: thread tid holds values tid*N .. tid*N+N-1 of the segment;
@@ -377,7 +373,7 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
         for (uint32_t j = 0;; ++j) {
             const int slot = (int)(j % S);
             const uint32_t ph = (j / S) & 1u;
-            if (!__all_sync(kFull, mbar_wait(&full[slot], ph, kXWaitCycles))) {
+            if (!__all_sync(kFull, mbar_wait(&full[slot], ph, a.wait_cycles))) {
                 ok = false;
                 break;
             }
@@ -440,7 +436,7 @@ __global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) {
             a.st->fault = 1;
-            a.st->stop = 1;
+            stop_from_kernel(a);
         }
     }
     excess_tail<T>(a, block, gridDim.x, zacc, cons);
@@ -698,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
 {
     pdl_wait();  // the excess kernel has finished (no-op without PDL)
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
@@ -741,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
@@ -876,7 +872,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
     __shared__ int sb_buf[32];
     __shared__ T sm_buf[32];
     volatile DevState* vst = a.st;
-    if (a.mode == MODE_SOLVE && vst->stop) return;  // an earlier sweep of this launch stopped
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;

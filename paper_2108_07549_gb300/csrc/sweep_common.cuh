@@ -285,6 +285,36 @@ __device__ void block_acc_max2(typename Acc<T>::V& z, T& m1, T& m2)
 
 // ------------------------------------------------------------------ objective and stop rules
 
+// True if an earlier sweep of this solve has stopped; the kernel then does
+// nothing.  Thread 0 reads the flag once for the whole block, so every
+// thread takes the same branch even while the decision block of the same
+// launch raises the flag.  In a one-instance graph, block 0 of such a kernel
+// also clears the while loop's condition.  The call is idempotent, so no
+// path that raises the flag can leave the loop running.
+template <typename T>
+__device__ __forceinline__ bool sweep_stopped(const SweepArgs<T>& a)
+{
+    __shared__ int stopped;
+    if (threadIdx.x == 0) {
+        stopped = a.mode == MODE_SOLVE && reinterpret_cast<volatile DevState*>(a.st)->stop;
+        if (stopped && a.use_cond && !a.active && blockIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+    }
+    __syncthreads();
+    return stopped != 0;
+}
+
+// Ends this instance's solve from a kernel other than the decision block
+// (a wait that ran out), exactly once.  It raises the stop flag and, in a
+// graph, ends the while loop.  A batch's loop ends with its last running
+// instance.
+template <typename T>
+__device__ void stop_from_kernel(const SweepArgs<T>& a)
+{
+    if (atomicExch(&a.st->stop, 1) != 0) return;
+    const bool last = a.active ? atomicSub(a.active, 1u) == 1u : true;
+    if (a.use_cond && last) cudaGraphSetConditional(a.cond, 0);
+}
+
 // Alg. 1: z = 1/2 sum psi^2 + 1/2 sum delta h^2 and the stop test, run by one
 // thread after every partial of this sweep is final.
 template <typename T>

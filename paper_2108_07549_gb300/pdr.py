@@ -24,6 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libpdr.so")
 PREC_FP32, PREC_FP64, PREC_FP32_FP64TAIL = 0, 1, 2
 ALGO_ESO, ALGO_AGD, ALGO_GDM, ALGO_CK = 0, 1, 2, 3
 VERDICT_UNKNOWN, VERDICT_FEASIBLE, VERDICT_INFEASIBLE = 0, 1, 2
+(OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_NOT_SOLVED, ERR_UNSUPPORTED,
+ ERR_TIMEOUT) = range(8)  # pdr_status
 STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall"}
 VERDICT_NAMES = {0: "unknown", 1: "feasible", 2: "infeasible"}
 
@@ -35,7 +37,7 @@ EXPORTS = (
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
     "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
-    "pdr_state_size", "pdr_get_state", "pdr_set_state",
+    "pdr_state_size", "pdr_get_state", "pdr_set_state", "pdr_debug_wait",
 )
 
 
@@ -103,6 +105,7 @@ def load(path: str = LIB_PATH):
         "pdr_state_size": ([vp, P(i64)], i32),
         "pdr_get_state": ([vp, vp, i64], i32),
         "pdr_set_state": ([vp, vp, i64], i32),
+        "pdr_debug_wait": ([vp, i64, i32], i32),
         "pdr_heights": ([vp, vp], i32),
         "pdr_congestion": ([vp, vp], i32),
         "pdr_objective": ([vp, P(dbl)], i32),
@@ -299,6 +302,10 @@ class Solver:
         """Restores a checkpoint (pdr_set_state); the next solve continues it."""
         buf = C.create_string_buffer(bytes(state), len(state))
         self._check(self._lib.pdr_set_state(self._h, buf, len(state)))
+
+    def debug_wait(self, cycles: int = 1 << 32, hold_end: bool = False):
+        """Test hook (pdr_debug_wait): the device wait limit and the end-marker hold."""
+        self._check(self._lib.pdr_debug_wait(self._h, int(cycles), int(bool(hold_end))))
 
     def flow_rows(self, edges, velocities: bool = False) -> np.ndarray:
         """Rows f[e, :] (or the Alg. 4 velocities v[e, :]) for the given edge ids ([len(edges), K])."""
