@@ -312,8 +312,10 @@ pdr_status pdr_sizes(const pdr_ctx *ctx, int32_t *n, int64_t *m, int32_t *K, int
  * the mean duration in milliseconds.  which = 0: edge QP (Alg. 2);
  * which = 1: excess/height (eq. (3), (2)).  If flush_bytes > 0 a buffer of
  * that size is overwritten before every launch so each starts with a cold
- * L2.  The QP launches advance the flows (they are real sweeps with fixed
- * heights).  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
+ * L2.  Each QP launch repeats the solve's next sweep.  It reads the current
+ * flows and the roots that warm-start that sweep, and writes the other
+ * buffers, so the current flows and warm starts do not change.  Errors:
+ * PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
 pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_t flush_bytes, double *ms);
 
 /* Number of entries in the edge-kernel variant table (pdr_options.edge_variant). */

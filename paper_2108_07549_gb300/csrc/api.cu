@@ -1839,8 +1839,9 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         if (flush) CKT(cudaMemsetAsync(flush, q & 0xff, (size_t)flush_bytes, ctx->stream));
         CKT(cudaEventRecord(e0, ctx->stream));
         if (which == 0) {
-            // reads the current flows, writes the other buffer: every launch
-            // repeats the same sweep
+            // reads the current flows and the roots of the sweep that made
+            // them (the warm starts of the solve's next sweep), writes the
+            // other buffers: every launch repeats that next sweep
             if (f64) CKT(launch_update<double>(ctx, make_args<double>(ctx, MODE_FORCED), ctx->stream));
             else CKT(launch_update<float>(ctx, make_args<float>(ctx, MODE_FORCED), ctx->stream));
         } else {
@@ -1854,7 +1855,9 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
         total += el;
     }
     {
-        pdr_status s = refresh_psi_current(ctx);
+        // restore the congestion partials of the current flows; the roots
+        // that warm-start the next sweep (theta[cur]) were only read
+        pdr_status s = f64 ? refresh_psi<double>(ctx, nullptr, true) : refresh_psi<float>(ctx, nullptr, true);
         if (s != PDR_OK) {
             cleanup();
             return s;
