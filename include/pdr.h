@@ -314,9 +314,20 @@ pdr_status pdr_sizes(const pdr_ctx *ctx, int32_t *n, int64_t *m, int32_t *K, int
  * that size is overwritten before every launch so each starts with a cold
  * L2.  Each QP launch repeats the solve's next sweep.  It reads the current
  * flows and the roots that warm-start that sweep, and writes the other
- * buffers, so the current flows and warm starts do not change.  Errors:
+ * buffers.  The device state is put back afterwards, so the current flows,
+ * warm starts and iteration counter do not change.  Errors:
  * PDR_ERR_INVALID_ARG, PDR_ERR_CUDA, PDR_ERR_OOM. */
 pdr_status pdr_time_kernel(pdr_ctx *ctx, int32_t which, int32_t launches, int64_t flush_bytes, double *ms);
+
+/* pdr_sweeps(ctx, count) with CUDA events on the context's stream around
+ * each launch of the excess kernel and of the update kernel (the edge QP
+ * of Alg. 2 or the capacity-kept step, or the gradient step of Alg. 3/4).
+ * The kernels are launched from the host, one after the other.  Writes the
+ * mean duration of each kernel over the `count` sweeps, in milliseconds:
+ * the kernels' average cost along a real run of the solve, with its warm
+ * starts and its L2 state.  The flows advance as with pdr_sweeps.  Errors:
+ * PDR_ERR_INVALID_ARG (NULL, count < 1), PDR_ERR_CUDA. */
+pdr_status pdr_time_sweeps(pdr_ctx *ctx, int64_t count, double *ms_excess, double *ms_update);
 
 /* Number of entries in the edge-kernel variant table (pdr_options.edge_variant). */
 int32_t pdr_num_edge_variants(void);

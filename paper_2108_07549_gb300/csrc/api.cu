@@ -1722,6 +1722,63 @@ pdr_status pdr_sweeps(pdr_ctx* ctx, int64_t count)
     return read_state(ctx);
 }
 
+// pdr_sweeps with CUDA events around every kernel launch, in chunks of up
+// to kTimeChunk sweeps (one stream synchronisation per chunk).
+pdr_status pdr_time_sweeps(pdr_ctx* ctx, int64_t count, double* ms_excess, double* ms_update)
+{
+    if (!ctx || !ms_excess || !ms_update) return PDR_ERR_INVALID_ARG;
+    if (count < 1) return ctx->fail(PDR_ERR_INVALID_ARG, "count must be >= 1");
+    constexpr int kTimeChunk = 256;
+    pdr_status s = read_state(ctx);
+    if (s != PDR_OK) return s;
+    s = init_state(ctx, false, 0);
+    if (s != PDR_OK) return s;
+    s = ctx->cur_prec ? ensure_velocity<double>(ctx) : ensure_velocity<float>(ctx);
+    if (s != PDR_OK) return s;
+    std::vector<cudaEvent_t> ev(3 * kTimeChunk, nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    double tx = 0.0, tu = 0.0;
+    for (cudaEvent_t& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return cleanup(), ctx->fail(PDR_ERR_CUDA, "cudaEventCreate failed");
+    for (int64_t q0 = 0; q0 < count; q0 += kTimeChunk) {
+        const int64_t nq = count - q0 < kTimeChunk ? count - q0 : kTimeChunk;
+        for (int64_t j = 0; j < nq; ++j) {
+            const int par = (int)((q0 + j) & 1);
+            cudaError_t e = cudaEventRecord(ev[3 * j], ctx->stream);
+            if (ctx->cur_prec) {
+                SweepArgs<double> a = make_args<double>(ctx, MODE_FORCED, 0, 0, par);
+                if (e == cudaSuccess) e = launch_excess<double>(a, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[3 * j + 1], ctx->stream);
+                if (e == cudaSuccess) e = launch_update<double>(ctx, a, ctx->stream);
+            } else {
+                SweepArgs<float> a = make_args<float>(ctx, MODE_FORCED, 0, 0, par);
+                if (e == cudaSuccess) e = launch_excess<float>(a, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[3 * j + 1], ctx->stream);
+                if (e == cudaSuccess) e = launch_update<float>(ctx, a, ctx->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[3 * j + 2], ctx->stream);
+            if (e != cudaSuccess) return cleanup(), ctx->cuda_fail("timed sweep", e);
+        }
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        for (int64_t j = 0; j < nq && e == cudaSuccess; ++j) {
+            float a = 0.f, b = 0.f;
+            e = cudaEventElapsedTime(&a, ev[3 * j], ev[3 * j + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * j + 1], ev[3 * j + 2]);
+            tx += a;
+            tu += b;
+        }
+        if (e != cudaSuccess) return cleanup(), ctx->cuda_fail("timed sweep events", e);
+    }
+    cleanup();
+    ctx->cur ^= (int)(count & 1);
+    *ms_excess = tx / (double)count;
+    *ms_update = tu / (double)count;
+    return read_state(ctx);
+}
+
 pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
@@ -1832,6 +1889,13 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
     CKT(cudaEventCreate(&e0));
     CKT(cudaEventCreate(&e1));
     if (flush_bytes > 0) CKT(cudaMalloc(&flush, (size_t)flush_bytes));
+    // the QP launches run the decision block, which advances the counter:
+    // the device state is put back afterwards
+    {
+        const pdr_status s = read_state(ctx);
+        if (s != PDR_OK) return cleanup(), s;
+    }
+    const DevState saved = *ctx->hst;
     // heights of the current flows for the QP launches
     if (f64) CKT(launch_excess<double>(make_args<double>(ctx, MODE_EVAL), ctx->stream));
     else CKT(launch_excess<float>(make_args<float>(ctx, MODE_EVAL), ctx->stream));
@@ -1863,11 +1927,13 @@ pdr_status pdr_time_kernel(pdr_ctx* ctx, int32_t which, int32_t launches, int64_
             return s;
         }
     }
+    set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, saved);
+    CKT(cudaGetLastError());
     CKT(cudaStreamSynchronize(ctx->stream));
 #undef CKT
     cleanup();
     *ms = total / launches;
-    return PDR_OK;
+    return read_state(ctx);
 }
 
 }  // extern "C"

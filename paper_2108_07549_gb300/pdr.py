@@ -37,7 +37,7 @@ EXPORTS = (
     "pdr_adjacency_static", "pdr_gd_state", "pdr_set_gd_state", "pdr_flow_rows",
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
     "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
-    "pdr_state_size", "pdr_get_state", "pdr_set_state", "pdr_debug_wait",
+    "pdr_state_size", "pdr_get_state", "pdr_set_state", "pdr_debug_wait", "pdr_time_sweeps",
 )
 
 
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "pdr_get_state": ([vp, vp, i64], i32),
         "pdr_set_state": ([vp, vp, i64], i32),
         "pdr_debug_wait": ([vp, i64, i32], i32),
+        "pdr_time_sweeps": ([vp, i64, P(dbl), P(dbl)], i32),
         "pdr_heights": ([vp, vp], i32),
         "pdr_congestion": ([vp, vp], i32),
         "pdr_objective": ([vp, P(dbl)], i32),
@@ -385,6 +386,12 @@ class Solver:
         n, m, K, Kp = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
         self._check(self._lib.pdr_sizes(self._h, C.byref(n), C.byref(m), C.byref(K), C.byref(Kp)))
         return n.value, m.value, K.value, Kp.value
+
+    def time_sweeps(self, count: int):
+        """pdr_time_sweeps: mean ms of the excess and update kernels over `count` sweeps."""
+        mx, mu = C.c_double(), C.c_double()
+        self._check(self._lib.pdr_time_sweeps(self._h, int(count), C.byref(mx), C.byref(mu)))
+        return mx.value, mu.value
 
     def time_kernel(self, which: str = "qp", launches: int = 20, flush_bytes: int = 0) -> float:
         """Mean duration (ms) of one launch of the edge QP ("qp") or excess ("excess") kernel."""
