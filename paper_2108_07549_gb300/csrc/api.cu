@@ -127,9 +127,11 @@ struct pdr_ctx {
     float *f32[2] = {nullptr, nullptr}, *h32 = nullptr, *inv_deg_f = nullptr;
     double *f64[2] = {nullptr, nullptr}, *h64 = nullptr, *inv_deg_d = nullptr;
     int cur = 0;  // buffer holding the current flows
-    // [m] roots of the edge QPs, double-buffered like the flows: theta[b] holds
-    // the roots of the sweep that produced the flows in buffer b (the warm
-    // starts of the next sweep); 8 bytes per edge covers both precisions
+    // [2m] roots of the edge QPs and warm starts of the next sweep,
+    // double-buffered like the flows: theta[b] holds the roots ([0, m)) of
+    // the sweep that produced the flows in buffer b and the warm starts
+    // ([m, 2m)) of the sweep that reads them; 16 bytes per edge covers both
+    // precisions
     double* theta[2] = {nullptr, nullptr};
     // Alg. 3 / Alg. 4 state, double-buffered like the flows
     double* beta_buf[2] = {nullptr, nullptr};  // [m], 8 bytes per edge covers both precisions
@@ -415,7 +417,8 @@ pdr_status flows_to_buffer0(pdr_ctx* ctx)
     if (ctx->opt.algo == PDR_ALGO_GDM && bytes && Prec<T>::v(ctx, 1))
         CK(cudaMemcpyAsync(Prec<T>::v(ctx, 0), Prec<T>::v(ctx, 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (ctx->m > 0)
-        CK(cudaMemcpyAsync(ctx->theta[0], ctx->theta[1], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->theta[0], ctx->theta[1], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
     ctx->cur = 0;
     return PDR_OK;
 }
@@ -434,7 +437,7 @@ pdr_status refresh_psi(pdr_ctx* ctx, T* psi_out = nullptr, bool keep_theta = fal
     if (!psi_out && !keep_theta) {
         // new flows: the edge QPs start their root search cold
         for (int b = 0; b < 2; ++b)
-            CK(cudaMemsetAsync(ctx->theta[b], 0, sizeof(double) * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
+            CK(cudaMemsetAsync(ctx->theta[b], 0, sizeof(double) * 2 * (ctx->m > 0 ? ctx->m : 1), ctx->stream));
     }
     SweepArgs<T> a = make_args<T>(ctx, MODE_PSI);
     a.psi_out = psi_out;
@@ -865,12 +868,12 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             return st;                                   \
         }                                                \
     } while (0)
-    // checkpoints of the flows and of the warm-start roots at t = 0, C, 2C, ...
+    // checkpoints of the flows and of the roots and warm starts at t = 0, C, 2C, ...
     std::vector<T*> ck(grads ? nseg : 0), thck(grads ? nseg : 0), seg, th;
     for (auto& q : ck)
         if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
     for (auto& q : thck)
-        if (!(q = (T*)grab(sizeof(T) * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
+        if (!(q = (T*)grab(sizeof(T) * 2 * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
     T *fbar = nullptr, *cbar = nullptr, *Dbar = nullptr;
     double *ubar = nullptr, *dbar = nullptr;
     uint32_t* mask = nullptr;
@@ -894,7 +897,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     for (int64_t t = 0; t < Tn; ++t) {
         if (grads && t % C == 0) {  // the flows and the warm starts sweep t reads
             CKB(cudaMemcpyAsync(ck[t / C], Prec<T>::f(ctx, ctx->cur), sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
-            CKB(cudaMemcpyAsync(thck[t / C], ctx->theta[ctx->cur], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice,
+            CKB(cudaMemcpyAsync(thck[t / C], ctx->theta[ctx->cur], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice,
                                 ctx->stream));
         }
         SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
@@ -916,7 +919,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     for (int64_t sgi = nseg - 1; grads && sgi >= 0; --sgi) {
         const int64_t t0 = sgi * C, t1 = (t0 + C < Tn) ? t0 + C : Tn;
         CKB(cudaMemcpyAsync(seg[0], ck[sgi], sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
-        CKB(cudaMemcpyAsync(ctx->theta[0], thck[sgi], sizeof(T) * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
+        CKB(cudaMemcpyAsync(ctx->theta[0], thck[sgi], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
         for (int64_t t = t0; t < t1; ++t) {  // recompute f^(t0+1..t1-1), record each sweep's roots
             const int rb = (int)((t - t0) & 1);
             SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
@@ -1072,8 +1075,8 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_scale_f, float, m);
     ALLOC(ctx->inv_deg_f, float, n);
     ALLOC(ctx->inv_deg_d, double, n);
-    ALLOC(ctx->theta[0], double, m);
-    ALLOC(ctx->theta[1], double, m);
+    ALLOC(ctx->theta[0], double, 2 * (m > 0 ? m : 1));
+    ALLOC(ctx->theta[1], double, 2 * (m > 0 ? m : 1));
     ALLOC(ctx->beta_buf[0], double, m);
     ALLOC(ctx->beta_buf[1], double, m);
     ALLOC(ctx->dem_d, double, Kp);
@@ -1321,7 +1324,7 @@ StateLayout state_layout(const pdr_ctx* ctx, int prec, int64_t ntrace)
     const int64_t sz = prec ? 8 : 4, fm = (int64_t)ctx->m * ctx->Kp;
     StateLayout L{};
     L.f = sz * fm;
-    L.theta = sz * ctx->m;
+    L.theta = 2 * sz * ctx->m;  // roots and warm starts
     L.beta = is_gd(ctx->opt) ? sz * ctx->m : 0;
     L.v = ctx->opt.algo == PDR_ALGO_GDM ? sz * fm : 0;
     L.trace = 8 * ntrace;

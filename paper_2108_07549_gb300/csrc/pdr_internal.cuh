@@ -99,9 +99,10 @@ struct SweepArgs {
     T* f;               // flows read by this sweep, f^(t)
     T* f_out;           // flows written by the edge QP, f^(t+1) (the other buffer)
     T* h;
-    const T* theta_in;  // [m] root psi'/2 of each edge QP in the sweep that made f (0 = none):
-                        // the warm start of this sweep's root search
-    T* theta;           // [m] this sweep's roots (the other buffer, like f_out)
+    const T* theta_in;  // [2m] of the sweep that made f: [0, m) the root psi'/2 of each edge QP
+                        // (0 = none), [m, 2m) the warm start of this sweep's root search
+    T* theta;           // [2m] this sweep's roots and the next sweep's warm starts (the other
+                        // buffer, like f_out)
     // Objective partials.  Edge kernels write one partial per warp (lane-group
     // form) or per block (block form): the sum of psi^2 as an accumulator
     // pair and the largest psi/scale.  Each excess block adds a fixed slice

@@ -569,6 +569,21 @@ __device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool 
     return theta;
 }
 
+// Warm start of the next sweep's root search from this sweep's root theta
+// and the previous one, prev.  A root that rose is expected to stay at or
+// above theta; one that fell is expected to fall by about as much again.
+// Starting the search at the previous root itself leaves out the many
+// entries whose flows have decayed to zero, which sit just above it (c_k =
+// theta + f'_k): one pass decides almost every edge.  A start above the
+// new root is detected by its certificate g(w) < 0 and costs a cold pass.
+template <typename T>
+__device__ __forceinline__ T next_warm_start(T theta, T prev)
+{
+    if (theta > prev) return theta;
+    const T w = T(0.999) * theta + T(2) * (theta - prev);
+    return w > T(0) ? w : T(0);
+}
+
 // ------------------------------------------------------------------ edge QP, lane-group form
 
 // One aligned group of G lanes per edge; each lane keeps V vectors of the
@@ -644,11 +659,14 @@ __device__ __forceinline__ void edge_group_body(const SweepArgs<T>& a, int block
         }
         T psi;
         if (!psi_only) {
-            // warm start slightly below the previous sweep's root
-            const T w = valid ? a.theta_in[e] * T(0.999) : T(0);
+            // warm start left by the previous sweep (roots in [0, m), starts in [m, 2m))
+            const T w = valid ? a.theta_in[a.m + e] : T(0);
             const int den = a.ck ? 0 : 2;
             const T theta = qp_root_group<T, G, V, N>(c, ue, w, valid, a.Kp, den);
-            if (valid && gl == 0) a.theta[e] = theta;
+            if (valid && gl == 0) {
+                a.theta[a.m + e] = next_warm_start(theta, a.theta_in[e]);
+                a.theta[e] = theta;
+            }
             // f' = max(0, c - theta); at the root sum f' - u = den theta, so the
             // congestion of the new flows is psi' = 2 theta for Alg. 2 and 0 with
             // the capacity kept (and 0 in Case 1)
@@ -773,8 +791,11 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
         T psi;
         if (!psi_only) {
             const int den = a.ck ? 0 : 2;
-            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta_in[e] * T(0.999), true, a.Kp, den);
-            if (lane == 0) a.theta[e] = theta;
+            const T theta = qp_root_group<T, 32, V, N>(c, ue, a.theta_in[a.m + e], true, a.Kp, den);
+            if (lane == 0) {
+                a.theta[a.m + e] = next_warm_start(theta, a.theta_in[e]);
+                a.theta[e] = theta;
+            }
             T* orow = a.f_out + e * a.Kp;
 #pragma unroll
             for (int q = 0; q < V; ++q) {
@@ -923,7 +944,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
         T psi;
         if (!psi_only) {
             // the lane-group search with block-wide sums, counts and minima
-            const T w0 = a.theta_in[e] * T(0.999);
+            const T w0 = a.theta_in[a.m + e];
             const int den = a.ck ? 0 : 2;
             T S, mn, theta = T(0);
             int n, nA = 0;
@@ -945,7 +966,10 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
                 theta = (S - ue) / T(den + n);
                 done = mn > theta;
             }
-            if (threadIdx.x == 0) a.theta[e] = theta;
+            if (threadIdx.x == 0) {
+                a.theta[a.m + e] = next_warm_start(theta, a.theta_in[e]);
+                a.theta[e] = theta;
+            }
             if (pf) {  // its height rows, now that its endpoints have arrived
                 prefetch_l2(a.h + (int64_t)ps * a.Kp, (int64_t)a.Kp * sizeof(T), threadIdx.x, B);
                 prefetch_l2(a.h + (int64_t)pc * a.Kp, (int64_t)a.Kp * sizeof(T), threadIdx.x, B);
