@@ -191,14 +191,15 @@ def source_digest():
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the
+    current sources and on this workload."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("source_digest") != source_digest():
+    if rec.get("source_digest") != source_digest() or rec.get("workload") != WORKLOAD.split(":")[0]:
         return None
     k = rec.get("kernels", {}).get(kernel)
     return None if k is None else float(k["dram_bytes_per_launch"])
