@@ -254,6 +254,14 @@ pdr_status pdr_set_state(pdr_ctx *ctx, const void *buf, int64_t bytes);
  * Errors: PDR_ERR_INVALID_ARG. */
 pdr_status pdr_debug_wait(pdr_ctx *ctx, int64_t cycles, int32_t hold_end);
 
+/* Test hook for host-side failure injection: the nth device allocation the
+ * library makes from now on (in pdr_create, pdr_set_options, pdr_batch_create,
+ * ...) fails as if the device were out of memory, and the call that made it
+ * returns PDR_ERR_OOM after releasing what it had allocated.  nth = 0 turns
+ * the injection off; it also ends after the failure.  Process-wide.
+ * Errors: PDR_ERR_INVALID_ARG (nth < 0). */
+pdr_status pdr_debug_fail_alloc(int64_t nth);
+
 /* Selected rows of the current state: out[q*K + k] = f_{edges[q],k}
  * (which = 0) or the Alg. 4 velocity v_{edges[q],k} (which = 1), for
  * q < count (double).  For checking large instances edge by edge without

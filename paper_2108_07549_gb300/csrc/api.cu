@@ -13,6 +13,7 @@
 #include "pdr.h"
 #include "pdr_internal.cuh"
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -201,11 +202,28 @@ struct pdr_ctx {
 
 namespace {
 
+// Host-side failure injection (pdr_debug_fail_alloc): when positive, the
+// device allocation that brings it to 0 fails as if the device were full.
+std::atomic<int64_t> g_fail_alloc{0};
+
+bool injected_alloc_failure()
+{
+    int64_t k = g_fail_alloc.load();
+    while (k > 0)
+        if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 1;
+    return false;
+}
+
 template <typename T>
 T* dalloc(pdr_ctx* ctx, size_t count, pdr_status* st)
 {
     void* p = nullptr;
     if (count == 0) count = 1;
+    if (injected_alloc_failure()) {
+        *st = PDR_ERR_OOM;
+        ctx->err = "cudaMalloc: injected allocation failure";
+        return nullptr;
+    }
     cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
     if (e != cudaSuccess) {
         *st = (e == cudaErrorMemoryAllocation) ? PDR_ERR_OOM : PDR_ERR_CUDA;
@@ -1456,6 +1474,13 @@ pdr_status pdr_set_state(pdr_ctx* ctx, const void* buf, int64_t bytes)
     if (s != PDR_OK) return s;
     ctx->t_widen = h.t_widen;
     ctx->resume_pending = true;
+    return PDR_OK;
+}
+
+pdr_status pdr_debug_fail_alloc(int64_t nth)
+{
+    if (nth < 0) return PDR_ERR_INVALID_ARG;
+    g_fail_alloc.store(nth);
     return PDR_OK;
 }
 

@@ -38,6 +38,7 @@ EXPORTS = (
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
     "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
     "pdr_state_size", "pdr_get_state", "pdr_set_state", "pdr_debug_wait", "pdr_time_sweeps",
+    "pdr_debug_fail_alloc",
 )
 
 
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "pdr_set_state": ([vp, vp, i64], i32),
         "pdr_debug_wait": ([vp, i64, i32], i32),
         "pdr_time_sweeps": ([vp, i64, P(dbl), P(dbl)], i32),
+        "pdr_debug_fail_alloc": ([i64], i32),
         "pdr_heights": ([vp, vp], i32),
         "pdr_congestion": ([vp, vp], i32),
         "pdr_objective": ([vp, P(dbl)], i32),

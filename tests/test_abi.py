@@ -137,6 +137,8 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pdr_set_state(None, None, 0) == 1
     assert lib.pdr_debug_wait(None, 10_000, 0) == 1
     assert lib.pdr_time_sweeps(None, 1, None, None) == 1
+    assert lib.pdr_debug_fail_alloc(-1) == 1
+    assert lib.pdr_debug_fail_alloc(0) == 0
     lib.pdr_destroy(None)
 
 
