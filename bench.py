@@ -205,23 +205,32 @@ def ncu_traffic(kernel: str):
     return None if k is None else float(k["dram_bytes_per_launch"])
 
 
-def cpu_baseline(inst, budget_s=12.0):
-    """The FP64 oracle (Alg. 1 + Alg. 2, unoptimised) on all host cores, on a bounded sample."""
+def cpu_baseline(inst, budget_s=12.0, single_s=4.0):
+    """The FP64 oracle (Alg. 1 + Alg. 2, unoptimised) on all host cores, on a
+    bounded sample, and beside it on one core."""
     import oracle
 
-    threads = oracle.set_threads(os.cpu_count() or 1)
     P = oracle.Problem.from_instance(inst)
-    t0 = time.perf_counter()
-    P.solve_eso(max_sweeps=5, eps_obj=0.0)
-    per = (time.perf_counter() - t0) / 5
-    n_sweeps = max(5, int(budget_s / max(per, 1e-6)))
-    t0 = time.perf_counter()
-    _, rep = P.solve_eso(max_sweeps=n_sweeps, eps_obj=0.0)
-    dt = time.perf_counter() - t0
+
+    def timed(threads, budget):
+        used = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        P.solve_eso(max_sweeps=2, eps_obj=0.0)
+        per = (time.perf_counter() - t0) / 2
+        n_sweeps = max(2, int(budget / max(per, 1e-6)))
+        t0 = time.perf_counter()
+        _, rep = P.solve_eso(max_sweeps=n_sweeps, eps_obj=0.0)
+        dt = time.perf_counter() - t0
+        return used, rep["sweeps"], dt
+
+    threads, sweeps, dt = timed(os.cpu_count() or 1, budget_s)
+    _, sweeps1, dt1 = timed(1, single_s)
     oracle.set_threads(1)
-    return {"value": inst.m * inst.K * rep["sweeps"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{rep['sweeps']} FP64 sweeps of Alg. 1 (sort-based Alg. 2) from f = 0 on the same instance, "
-                      f"{dt:.1f} s"}
+    return {"value": inst.m * inst.K * sweeps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sweeps} FP64 sweeps of Alg. 1 (sort-based Alg. 2) from f = 0 on the same instance, "
+                      f"{dt:.1f} s",
+            "single_core": {"value": inst.m * inst.K * sweeps1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"{sweeps1} FP64 sweeps from f = 0, {dt1:.1f} s"}}
 
 
 # --------------------------------------------------------------------------- reference arm
