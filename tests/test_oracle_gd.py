@@ -6,6 +6,8 @@ accepted edge step lowers the surrogate, so AGD's z never rises), GDM with
 gamma = 0 reducing exactly to AGD, and verdicts on the capacity twins.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -111,3 +113,66 @@ def test_gd_verdicts_on_twins(grid5, grid5_bad, momentum):
     f, v, b, rep = Q.solve_gd(prm_ok, max_sweeps=200000, eps_obj=1e-12)
     res = Q.residuals(f)
     assert res["verdict"] == oracle.VERDICT_INFEASIBLE and abs(res["margin"] - 2 * res["z"]) <= 1e-3 * res["z"]
+
+
+# --------------------------------------------------------------------------- Alg. 4 momentum step by hand
+
+
+def test_gdm_hand_step_accept_with_clamp():
+    """Alg. 4, K = 2, gamma = .9, v = (-2, .3), f = (1, .5), h_i = (1, .2), h_j = 0,
+    psi = 0, u = 10, beta = .5, t = 3 (no periodic increase):
+      phi = (1, .2), df = (.5, .1), psi' = 0, dz = (.25 - .5) + (.01 - .02) = -.26 -> accepted;
+      v' = (.9 * -2 + .5, .9 * .3 + .1) = (-1.3, .37);
+      f' = (max(0, 1 - 1.3), max(0, .5 + .37)) = (0, .87).
+    The velocity keeps its negative entry (only f is projected).  Wrong readings fail:
+    max(0, f + df) + gamma v gives f'_0 = -.3; no projection gives -.3;
+    v' = gamma (v + df) gives f'_1 = .86."""
+    prm = oracle.gd_params(True, 2, gamma=0.9, beta_min=0.05, beta_max=1.0)
+    f, v, b, acc, dz = oracle.gd_edge(prm, [1.0, 0.2], [0.0, 0.0], 0.0, 10.0, [1.0, 0.5], [-2.0, 0.3], 0.5, 3)
+    assert acc and abs(dz - (-0.26)) < 1e-15 and b == 0.5
+    np.testing.assert_allclose(v, [-1.3, 0.37], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(f, [0.0, 0.87], rtol=0, atol=1e-15)
+    assert f[0] == 0.0
+
+
+def test_gdm_hand_step_reject_keeps_velocity():
+    """Alg. 4, K = 2, rejected step: f = (1, .5), v = (-2, .3), h_i = (2, -2), h_j = 0,
+    psi = 0, u = 100, beta = 2, t = 1: phi = (2, -2), df = (max(-1, 4), max(-.5, -4)) = (4, -.5),
+    dz = (16 - 8) + (.25 - 1) = 7.25 > 0 -> f and v unchanged, beta = max(beta_min, 2 * .5) = 1."""
+    prm = oracle.gd_params(True, 2, gamma=0.9, beta_min=0.05, beta_max=4.0)
+    f, v, b, acc, dz = oracle.gd_edge(prm, [2.0, -2.0], [0.0, 0.0], 0.0, 100.0, [1.0, 0.5], [-2.0, 0.3], 2.0, 1)
+    assert not acc and dz == 7.25 and b == 1.0
+    np.testing.assert_array_equal(f, [1.0, 0.5])
+    np.testing.assert_array_equal(v, [-2.0, 0.3])
+
+
+def test_gdm_golden_trace():
+    """tests/golden/two_vertex_k1_gdm.txt: three iterations of Alg. 4 derived by hand in
+    exact dyadic rationals (so the FP64 oracle must reproduce them exactly), including
+    the momentum overshoot that makes z rise."""
+    from fractions import Fraction as Fr
+
+    g = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "two_vertex_k1_gdm.txt")
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            key, val = line.split(":", 1)
+            g[key.strip()] = [float(Fr(x)) for x in val.split()]
+    P = oracle.Problem(2, [int(x) for x in g["row_ptr"]], [int(x) for x in g["col"]], g["u"],
+                       [int(x) for x in g["s"]], [int(x) for x in g["t"]], g["d"])
+    b0, bmin, bmax, ainc, adec, gamma = g["params"]
+    prm = dict(momentum=1, beta_init=b0, beta_min=bmin, beta_max=bmax, alpha_inc=ainc, alpha_dec=adec, gamma=gamma)
+    f = np.zeros((2, 1))
+    v = np.zeros((2, 1))
+    beta = np.full(2, b0)
+    for t in range(3):
+        f, v, beta = P.gd_sweep(prm, f, v, beta, t)
+        np.testing.assert_array_equal(f[:, 0], g[f"f{t + 1}"])
+        np.testing.assert_array_equal(v[:, 0], g[f"v{t + 1}"])
+    np.testing.assert_array_equal(beta, g["beta3"])
+    f3, v3, beta3, rep, zt = P.solve_gd(prm, max_sweeps=3, eps_obj=0.0, trace=True)
+    np.testing.assert_array_equal(zt, g["z"])
+    np.testing.assert_array_equal(f3[:, 0], g["f3"])
+    np.testing.assert_array_equal(v3[:, 0], g["v3"])
+    np.testing.assert_array_equal(beta3, g["beta3"])
