@@ -1,9 +1,10 @@
 """Benchmark of the PDR sweep (Alg. 1 with the exact edge solver of Alg. 2) on one GB300.
 
-Workload: the planar-like k-nearest-neighbour instance -- n = 2,500 random
-points, each joined both ways to its 3 nearest neighbours (m = 15,000 arcs),
-K = 500 random OD pairs with integer demands in [1, 20], capacities 1.2x the
-load of a seeded random hop-shortest-path routing (seed 0).
+Headline workload (the largest single-GPU configuration): the 100 x 100
+bidirectional grid, n = 10,000, m = 39,600 arcs, K = 10,000 random OD pairs
+with lognormal(1, 0.5) demands, capacities 1.1x the load of a seeded random
+hop-shortest-path routing (seed 0).  The FP32 flows alone are 1.58 GB, far
+above L2, so every sweep streams its rows from HBM.
 
 One step = one call of pdr_solve from f = 0 that runs exactly S sweeps (the
 stop rules stay armed but do not fire before S) plus the FP64 residual and
@@ -14,11 +15,18 @@ Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events on
 the solver's stream, with a 256 MiB buffer overwritten between steps so every
 step starts with a cold L2.  ``value`` has the inputs resident in HBM; ``e2e``
 times the same step through the C ABI from pinned host buffers (pdr_create,
-which copies the instance in, pdr_solve, and pdr_flows, which copies the
-flows out).  ``roofline`` times the dominant kernel alone with the L2 state of
-the timed loop (warm when the working set fits in L2, else flushed per
-launch), divides its algorithmic bytes by that time, and also reports the
-cold-L2 figure.
+which copies the instance in, pdr_solve, and pdr_flows, which writes the
+flows into a pinned host buffer).  ``roofline`` takes the dominant kernel's
+mean launch along the S sweeps of one step (CUDA events around each launch)
+and reconciles it with the sweep time inside the graph loop.
+
+Beside the headline the line carries (rank 0, one GPU): the error of one
+FP32 sweep against the FP64 oracle on sampled edges, the L2-resident
+knn2500_k500 instance (reported against L2 traffic, not HBM), time to
+residual 1e-6 and the residuals reached within a fixed budget, the batched
+form against the single-instance form (256 uneven instances, and 256 small
+ones), the differentiated form against the forward alone, and the oracle on
+this host's cores.
 
 Multi-GPU: the sweep does not shard (replicas only): under torchrun every rank
 solves its own replica and ``value`` is the sum of the ranks' updates over the
@@ -56,7 +64,8 @@ WORKLOADS = {
                 "routing load (20% at 0.7x), seed 0",
 }
 ALGOS = {"eso": 0, "agd": 1, "gdm": 2, "ck": 3}  # ck: Alg. 1 with the capacity kept (Program (6))
-WORKLOAD = WORKLOADS["knn2500_k500"]
+DEFAULT_WORKLOAD = "grid100_k10000"
+WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD]
 L2_RESIDENT_BYTES = 96 << 20  # working sets up to this stay in GB300's L2 across sweeps (measured)
 FLUSH_BYTES = 256 << 20
 
@@ -66,8 +75,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 2000; 100 on the large workloads)")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="knn2500_k500")
+    ap.add_argument("--sweeps", type=int, default=0, help="sweeps per step (default 2000 on knn2500_k500, else 200)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--algo", choices=sorted(ALGOS), default="eso",
                     help="eso: Alg. 1 + Alg. 2; agd: Alg. 3; gdm: Alg. 4")
     ap.add_argument("--adjoint", action="store_true",
@@ -90,7 +99,10 @@ def parse():
     ap.add_argument("--compare-variants", action="store_true",
                     help="time every edge-kernel variant that holds the rows (Alg. 1) and print one JSON line")
     ap.add_argument("--impl", choices=["pdr", "reference"], default="pdr")
-    ap.add_argument("--no-extras", action="store_true", help="skip time-to-eps, roofline and cpu baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the roofline, oracle error, CPU baseline and the extra blocks")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and differentiated-form blocks of the default run")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiler driver: run this many host-launched sweeps from f = 0 on the workload and exit")
     ap.add_argument("--engine", choices=["graph", "persistent"], default="graph",
@@ -215,9 +227,11 @@ def cpu_baseline(inst, budget_s=12.0, single_s=4.0):
     def timed(threads, budget):
         used = oracle.set_threads(threads)
         t0 = time.perf_counter()
-        P.solve_eso(max_sweeps=2, eps_obj=0.0)
-        per = (time.perf_counter() - t0) / 2
-        n_sweeps = max(2, int(budget / max(per, 1e-6)))
+        P.solve_eso(max_sweeps=1, eps_obj=0.0)
+        per = time.perf_counter() - t0
+        n_sweeps = int(budget / max(per, 1e-6))
+        if n_sweeps <= 1:  # one sweep already fills the budget: that run is the sample
+            return used, 1, per
         t0 = time.perf_counter()
         _, rep = P.solve_eso(max_sweeps=n_sweeps, eps_obj=0.0)
         dt = time.perf_counter() - t0
@@ -245,11 +259,12 @@ def run_reference(args, inst):
     threads = oracle.set_threads(os.cpu_count() or 1)
     P = oracle.Problem.from_instance(inst)
     t0 = time.perf_counter()
-    P.solve_eso(max_sweeps=3, eps_obj=0.0)
-    per = (time.perf_counter() - t0) / 3
-    # each step: a bounded sample of the workload, about 20 s for the whole run
+    P.solve_eso(max_sweeps=1, eps_obj=0.0)
+    per = time.perf_counter() - t0
+    # each step: a bounded sample of the workload, about 20 s for the whole
+    # run (at least one sweep per step)
     total_steps = args.steps + args.warmup
-    sweeps = max(3, int(20.0 / max(per, 1e-6) / max(total_steps, 1)))
+    sweeps = max(1, int(20.0 / max(per, 1e-6) / max(total_steps, 1)))
     for _ in range(args.warmup):
         P.solve_eso(max_sweeps=sweeps, eps_obj=0.0)
     times = []
@@ -347,16 +362,17 @@ def compare_variants(args, inst, pdr, torch, stream):
     sweep inside the graph loop (CUDA events around a fixed number of sweeps
     from f = 0) and the edge kernel alone with a cold L2."""
     peak, peak_src = load_peaks()
-    out = {"kind": "edge-kernel variant comparison", "workload": WORKLOAD, "sweeps": args.sweeps, "dtype": "f32",
-           "peak_gbs": peak, "peak_source": peak_src, "variants": {}}
+    out = {"kind": "edge-kernel variant comparison", "workload": WORKLOAD, "algo": args.algo, "sweeps": args.sweeps,
+           "dtype": "f32", "peak_gbs": peak, "peak_source": peak_src, "variants": {}}
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    b_up = update_bytes("eso", inst)
+    b_up = update_bytes(args.algo, inst)
     for v, cap, pipe in pdr.edge_variants(pdr.PREC_FP32):
-        if cap < inst.K:
+        if cap < inst.K or (pipe and args.algo != "eso"):
             continue
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
-                                          resid_tol=0.0, max_sweeps=args.sweeps, edge_variant=v) as sv:
+                                          resid_tol=0.0, max_sweeps=args.sweeps, edge_variant=v,
+                                          algo=ALGOS[args.algo]) as sv:
                 sv.solve()
                 times = []
                 for q in range(3):
@@ -651,6 +667,287 @@ def bench_batch(args, insts, pdr, torch, stream):
     }), flush=True)
 
 
+# --------------------------------------------------------------------------- blocks of the default run
+
+
+def timed_solves(pdr, torch, stream, sv, flush, reps):
+    """Device time (ms) of reset + solve, CUDA events on the solver's stream, L2
+    flushed before each; returns every repeat and the last result."""
+    times, r = [], None
+    for q in range(reps):
+        flush.fill_(q & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.reset()
+        r = sv.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, r
+
+
+def error_vs_oracle(pdr, inst, sv, samples=64, seed=123):
+    """Error of the solver's next FP32 sweep against the FP64 oracle on sampled
+    edges: the rows of the sampled edges and of every edge incident to their
+    endpoints are read back, the oracle computes the endpoints' heights
+    (eq. (3), (2)) from them and the edge update (Alg. 2), and the GPU runs the
+    sweep.  Reports the largest error scaled by the row scale
+    sigma_e = max_k(|f| + |h_i| + |h_j|), and the element-relative error over
+    entries with |f'| > 1e-3 * mean(d)."""
+    import numpy as np
+
+    import oracle
+
+    P = oracle.Problem.from_instance(inst)
+    rng = np.random.default_rng(seed)
+    edges = np.sort(rng.choice(inst.m, min(samples, inst.m), replace=False))
+    src = inst.src
+    verts = np.unique(np.concatenate([src[edges], inst.col[edges]]))
+    need = set(edges.tolist())
+    for i in verts:
+        need |= set(P.in_eid[P.in_ptr[i]:P.in_ptr[i + 1]].tolist())
+        need |= set(range(int(inst.row_ptr[i]), int(inst.row_ptr[i + 1])))
+    need = np.array(sorted(need), dtype=np.int64)
+    roe = np.full(inst.m, -1, dtype=np.int64)
+    roe[need] = np.arange(need.shape[0])
+    rows = sv.flow_rows(need)
+    sv.sweeps(1)
+    new = sv.flow_rows(edges)
+    h = {int(i): P.excess_vertex(int(i), roe, rows)[1] for i in verts}
+    floor = 1e-3 * float(np.mean(inst.d))
+    row_scaled, rel = [], []
+    for q, e in enumerate(edges):
+        f = rows[roe[e]]
+        hi, hj = h[int(src[e])], h[int(inst.col[e])]
+        want = oracle.edge_qp(hi, hj, f, inst.u[e])[0]
+        sigma = float(np.max(np.abs(f) + np.abs(hi) + np.abs(hj)))
+        d = np.abs(new[q] - want)
+        row_scaled.append(float(d.max()) / max(sigma, 1e-300))
+        big = np.abs(want) > floor
+        if big.any():
+            rel.append(d[big] / np.abs(want[big]))
+    rel = np.concatenate(rel) if rel else np.zeros(1)
+    return {"edges": int(edges.shape[0]), "entries_compared": int(rel.shape[0]),
+            "max_row_scaled_err": max(row_scaled), "max_elem_rel_err": float(rel.max()),
+            "p999_elem_rel_err": float(np.quantile(rel, 0.999)), "tolerance_row_scaled": 1e-5,
+            "within_tolerance": bool(max(row_scaled) <= 1e-5),
+            "how": "one FP32 sweep from the solver's current flows vs the FP64 oracle's heights (eq. (3), (2)) "
+                   "and Alg. 2 on %d sampled edges; element-relative over |f'| > 1e-3 mean(d)" % edges.shape[0]}
+
+
+def l2_resident_block(pdr, torch, stream, inst, flush, steps=5, S=2000):
+    """knn2500_k500: the whole working set (both flow buffers and the heights,
+    65 MB) stays in L2 across sweeps, so its kernels are reported against the
+    bytes they move through L2, not as a fraction of HBM."""
+    m, n, K = inst.m, inst.n, inst.K
+    opts = dict(precision=pdr.PREC_FP32, eps_obj=1e-6, resid_tol=1e-6, max_sweeps=S)
+    out = {"workload": WORKLOADS["knn2500_k500"], "sweeps_per_step": S, "l2_resident": True}
+    with torch.cuda.stream(stream):
+        with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, **opts) as sv:
+            timed_solves(pdr, torch, stream, sv, flush, 2)
+            times, r = timed_solves(pdr, torch, stream, sv, flush, steps)
+            ms = statistics.median(times)
+            sv.reset()
+            t_ex, t_qp = sv.time_sweeps(S)
+            out["error_vs_oracle"] = error_vs_oracle(pdr, inst, sv)
+        with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
+                                      resid_tol=1e-6, max_sweeps=1000000) as sv:
+            rr = sv.solve()
+    b_qp = update_bytes("eso", inst)
+    b_ex = 4 * K * (m + n) + 8 * m + 8 * n
+    out.update({
+        "updates_per_s": m * K * S / (ms / 1e3), "ms_per_step": ms,
+        "us_per_sweep": ms * 1e3 / S,
+        "kernel_us": {"edge_qp": t_qp * 1e3, "excess_height": t_ex * 1e3},
+        "l2_gbs": {"edge_qp": b_qp / (t_qp / 1e3) / 1e9, "excess_height": b_ex / (t_ex / 1e3) / 1e9},
+        "algorithmic_bytes": {"edge_qp": b_qp, "excess_height": b_ex},
+        "note": "bytes per launch / mean launch along one step: L2 traffic (the 65 MB working set never leaves "
+                "L2), so no fraction of the HBM peak is claimed",
+        "time_to_eps": {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"], "ms": rr["ms_total"],
+                        "z": rr["z"], "cap_rel": rr["cap_rel"], "cons_rel": rr["cons_rel"],
+                        "verdict": rr["verdict_name"]},
+    })
+    return out
+
+
+def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
+    """Time to residual 1e-6 (cap_rel and cons_rel <= 1e-6, or a Farkas
+    certificate) on the 5x5 grid and its infeasible twin (GPU FP64, GPU FP32
+    with the FP64 tail, and the FP64 oracle), and on the headline instance the
+    residuals reached within a fixed budget of FP32 sweeps, with the oracle's
+    residuals at the same early sweep beside the GPU's."""
+    import oracle
+    from paper_2108_07549_gb300 import instances as I
+
+    out = {"target": "cap_rel <= 1e-6 and cons_rel <= 1e-6 (feasible) or Farkas margin > 0 (infeasible)"}
+    g = I.grid5_k10(1.3, seed=0)
+    for label, inst in (("grid5_k10_feasible_1.3x", g), ("grid5_k10_infeasible_0.6x", g.with_factor(0.6))):
+        row = {}
+        for prec, code in (("gpu_fp64", pdr.PREC_FP64), ("gpu_fp32_fp64tail", pdr.PREC_FP32_FP64TAIL)):
+            with torch.cuda.stream(stream):
+                with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=code, eps_obj=0.0,
+                                              resid_tol=1e-6, eps_rel=1e-13, max_sweeps=600000) as sv:
+                    sv.solve()  # warm-up (graph capture)
+                    sv.reset()
+                    r = sv.solve()
+            row[prec] = {"ms": r["ms_total"], "sweeps": r["sweeps"], "sweeps_fp64": r["sweeps_fp64"],
+                         "cap_rel": r["cap_rel"], "cons_rel": r["cons_rel"], "margin": r["margin"],
+                         "verdict": r["verdict_name"], "stop": r["stop_name"]}
+        P = oracle.Problem.from_instance(inst)
+        t0 = time.perf_counter()
+        f, rep = P.solve_eso(max_sweeps=300000, eps_obj=0.0, resid_tol=1e-6)
+        if rep["stop_reason"] != 2:
+            f, rep2 = P.solve_eso(max_sweeps=300000, eps_obj=1e-15, f0=f)
+            rep = dict(rep2, sweeps=rep["sweeps"] + rep2["sweeps"])
+        dt = time.perf_counter() - t0
+        res = P.residuals(f)
+        row["oracle_fp64"] = {"ms": dt * 1e3, "sweeps": rep["sweeps"], "cap_rel": res["cap_rel"],
+                              "cons_rel": res["cons_rel"], "margin": res["margin"],
+                              "verdict": {0: "unknown", 1: "feasible", 2: "infeasible"}[res["verdict"]]}
+        row["same_verdict"] = len({row[k]["verdict"] for k in ("gpu_fp64", "gpu_fp32_fp64tail", "oracle_fp64")}) == 1
+        out[label] = row
+    # the headline instance: residuals within a budget, and beside the oracle at sweep 3
+    P = oracle.Problem.from_instance(big)
+    chk = {}
+    for S in (3, budget_sweeps):
+        with torch.cuda.stream(stream):
+            with pdr.Solver.from_instance(big, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
+                                          resid_tol=1e-6, max_sweeps=S) as sv:
+                r = sv.solve()
+        chk[str(S)] = {"gpu_fp32": {"ms": r["ms_total"], "cap_rel": r["cap_rel"], "cons_rel": r["cons_rel"],
+                                    "z": r["z"], "verdict": r["verdict_name"]}}
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    f3, _ = P.solve_eso(max_sweeps=3, eps_obj=0.0)
+    res = P.residuals(f3)
+    oracle.set_threads(1)
+    chk["3"]["oracle_fp64"] = {"s": time.perf_counter() - t0, "cap_rel": res["cap_rel"], "cons_rel": res["cons_rel"],
+                               "z": res["z"], "threads": threads}
+    g3, o3 = chk["3"]["gpu_fp32"], chk["3"]["oracle_fp64"]
+    chk["3"]["rel_diff"] = {k: abs(g3[k] - o3[k]) / max(abs(o3[k]), 1e-300) for k in ("z", "cap_rel", "cons_rel")}
+    out[big.name.split("@")[0] + "_within_budget"] = {
+        "checkpoints": chk,
+        "note": "PDR is first order: on this instance the 1e-6 residuals lie far beyond a bench budget, so the "
+                "residuals reached after %d FP32 sweeps are reported" % budget_sweeps}
+    return out
+
+
+def batch_forms_block(pdr, torch, stream, big_batch, small_batch, flush):
+    """The batched form against the single-instance form on the same GPU, the
+    same instances and the same S sweeps each (Alg. 1 + Alg. 2, FP32): one
+    batch (one graph launch per solve) against one solve after another.  For
+    the small instances also to residual 1e-6 (FP32 with the FP64 tail)."""
+    out = {}
+    for label, insts, S in (("batch256_uneven", big_batch, 50), ("batch256_small", small_batch, 200)):
+        opts = dict(precision=pdr.PREC_FP32, eps_obj=0.0, resid_tol=0.0, max_sweeps=S)
+        total = sum(x.m * x.K for x in insts) * S
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            B = pdr.Batch(insts, stream=stream.cuda_stream, **opts)
+            t_create = time.perf_counter() - t0
+            B.solve()
+            bt = []
+            for q in range(3):
+                B.reset()
+                flush.fill_(q & 0xFF)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = B.solve()
+                bt.append(time.perf_counter() - t0)
+            assert all(r["sweeps"] == S for r in res)
+            B.close()
+            singles = [pdr.Solver.from_instance(x, stream=stream.cuda_stream, **opts) for x in insts]
+            for sv in singles:
+                sv.solve()
+            st = []
+            for q in range(3):
+                for sv in singles:
+                    sv.reset()
+                flush.fill_(q & 0xFF)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for sv in singles:
+                    sv.solve()
+                st.append(time.perf_counter() - t0)
+            for sv in singles:
+                sv.close()
+        tb, ts = statistics.median(bt), statistics.median(st)
+        out[label] = {"instances": len(insts), "sweeps_per_instance": S, "updates_per_solve": total,
+                      "n_range": [min(x.n for x in insts), max(x.n for x in insts)],
+                      "K_range": [min(x.K for x in insts), max(x.K for x in insts)],
+                      "batch_s": tb, "batch_updates_per_s": total / tb, "create_and_autotune_s": t_create,
+                      "sequential_s": ts, "sequential_updates_per_s": total / ts, "speedup": ts / tb}
+    # the small instances solved to residual 1e-6
+    opts = dict(precision=pdr.PREC_FP32_FP64TAIL, eps_obj=0.0, resid_tol=1e-6, eps_rel=1e-13, max_sweeps=20000)
+    with torch.cuda.stream(stream):
+        B = pdr.Batch(small_batch, stream=stream.cuda_stream, **opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = B.solve()
+        tb = time.perf_counter() - t0
+        B.close()
+        rs, ts = [], 0.0
+        for x in small_batch:
+            with pdr.Solver.from_instance(x, stream=stream.cuda_stream, **opts) as sv:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rs.append(sv.solve())
+                ts += time.perf_counter() - t0
+    want = [x.feasible_by_construction for x in small_batch]
+
+    def summary(res):
+        v = [r["verdict_name"] for r in res]
+        feas = [r for r in res if r["verdict_name"] == "feasible"]
+        return {"verdicts": {k: v.count(k) for k in sorted(set(v))},
+                "sweeps_max": max(r["sweeps"] for r in res),
+                "max_cap_rel_feasible": max((r["cap_rel"] for r in feas), default=None),
+                "max_cons_rel_feasible": max((r["cons_rel"] for r in feas), default=None),
+                "verdicts_as_constructed": sum(1 for r, w in zip(res, want)
+                                               if w is not None and r["verdict_name"] ==
+                                               ("feasible" if w else "infeasible"))}
+
+    out["batch256_small_to_residual"] = {
+        "precision": "FP32 sweeps, FP64 tail, FP64 residuals and certificate", "max_sweeps": 20000,
+        "batch": {"s": tb, **summary(rb)}, "sequential": {"s": ts, **summary(rs)}, "speedup": ts / tb,
+        "same_verdicts": all(a["verdict"] == b["verdict"] for a, b in zip(rb, rs))}
+    return out
+
+
+def adjoint_block(pdr, torch, stream, inst, T=50, ckpt=10):
+    """The differentiated form on digraph20k_k2000: L = z(f^(T)) and its gradient
+    w.r.t. u and d through T sweeps (checkpoints every ckpt) against the T
+    forward sweeps alone (FP32, CUDA events on the solver's stream)."""
+    import numpy as np
+
+    out = {"workload": WORKLOADS["digraph20k_k2000"], "T": T, "ckpt_every": ckpt, "dtype": "f32"}
+    with torch.cuda.stream(stream):
+        with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
+            sv.backward(T, ckpt)  # warm-up
+            for key, grads in (("forward_only", False), ("forward_and_gradient", True)):
+                times = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    L, gu, gd = sv.backward(T, ckpt, grads=grads)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                out[key + "_ms"] = statistics.median(times)
+    out["gradient_over_forward"] = out["forward_and_gradient_ms"] / out["forward_only_ms"]
+    out["forward_updates_per_s"] = inst.m * inst.K * T / (out["forward_only_ms"] / 1e3)
+    out["L"] = L
+    out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
+    m, n, K = inst.m, inst.n, inst.K
+    extra_bytes = T * 4 * K * (9 * m + 5 * n)
+    extra_ms = out["forward_and_gradient_ms"] - out["forward_only_ms"]
+    peak, peak_src = load_peaks()
+    out["gradient_roofline"] = {"bound": "hbm", "algorithmic_bytes": extra_bytes, "ms": extra_ms,
+                                "achieved": extra_bytes / (extra_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                "peak_source": peak_src, "frac": extra_bytes / (extra_ms / 1e3) / 1e9 / peak}
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 
@@ -666,12 +963,24 @@ def main():
             "batch256": lambda: instances.batch256(seed=0, count=args.instances,
                                                    processes=os.cpu_count() or 1)}[args.workload]()
     if args.sweeps <= 0 and not args.to_residual:
-        args.sweeps = 2000 if args.workload == "knn2500_k500" else 100
+        args.sweeps = 2000 if args.workload == "knn2500_k500" else 200
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, inst)
         return
+    plain = not (args.profile_sweeps or args.compare_algos or args.compare_variants or args.compare_excess or
+                 args.compare_engines or args.adjoint or args.to_residual or args.workload == "batch256")
+    extras = plain and not args.no_extras and rank == 0 and world == 1
+    side = {}
+    if extras:
+        # the extra blocks' inputs, generated before any CUDA work (spawn pools)
+        side["knn"] = instances.knn2500_k500(1.2, seed=0)
+        if not args.no_forms:
+            side["batch"] = instances.batch256(seed=0, count=256, processes=os.cpu_count() or 1)
+            side["small"] = instances.batch256(seed=1, count=256, n_range=(100, 500), k_range=(10, 100),
+                                               processes=os.cpu_count() or 1)
+            side["c5"] = instances.digraph20k_k2000(1.05, seed=0)
 
     import numpy as np
     import torch
@@ -741,7 +1050,6 @@ def main():
             r = solver.solve()
         assert r["sweeps"] == S, r
         barrier()
-        times = []
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         with ClockSampler(local) as clocks:
@@ -772,7 +1080,7 @@ def main():
     host = [pin(x) for x in (inst.row_ptr, inst.col, inst.u, inst.s, inst.t, inst.d)]
     out = torch.empty((m, K), dtype=torch.float64).pin_memory().numpy()
     h2d = sum(x.nbytes for x in host)
-    d2h = m * K * 4  # the FP32 flows; pdr_flows widens them to double on the host
+    d2h = m * K * 8  # the flows, widened to double on the device and written into pinned host memory
     e2e_times = []
     with torch.cuda.stream(stream):
         for q in range(max(1, args.warmup) + args.steps):
@@ -787,13 +1095,17 @@ def main():
                 e2e_times.append(t1 - t0)
     e2e_s = replicas.slowest(sum(e2e_times) / len(e2e_times), world, device="cuda")
     e2e_value = replicas.job_throughput(m * K * S, e2e_s, world)
+    working_set = 4 * K * (2 * m + inst.n)  # both flow buffers and the heights, FP32
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sweeps_per_step": S, "precision": "FP32 flows and edge QP, FP64 stop "
-                   "test and certificate", "l2": "256 MiB buffer overwritten between timed steps",
+                   "test and certificate",
+                   "l2": "256 MiB buffer overwritten between timed steps; the working set (%.2f GB) exceeds L2"
+                         % (working_set / 1e9) if working_set > L2_RESIDENT_BYTES else
+                         "256 MiB buffer overwritten between timed steps",
                    "parallelism": "replicas" if world > 1 else "single",
                    "engine": "host loop" if args.host_loop else args.engine},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -803,62 +1115,61 @@ def main():
     }
 
     if not args.no_extras and rank == 0:
-        # each kernel's average launch duration over the work of one timed
-        # step: the same S sweeps from f = 0, host-launched, with CUDA events on
-        # the solver's stream around every launch (the warm starts and the L2
-        # state of the timed loop: its working set stays in L2 across sweeps
-        # when it fits); then, with L2 flushed before every launch, repeats of
-        # the next sweep
+        # each kernel's mean launch along the S sweeps of one step from f = 0,
+        # host-launched with CUDA events on the solver's stream around every
+        # launch, reconciled with the sweep time inside the graph loop (two
+        # solves of S and 2S sweeps)
         with torch.cuda.stream(stream):
             solver.reset()
-            t_ex_w, t_qp_w = solver.time_sweeps(S)
-            t_qp_c = solver.time_kernel("qp", 50, FLUSH_BYTES)
-            t_ex_c = solver.time_kernel("excess", 50, FLUSH_BYTES)
+            t_ex, t_qp = solver.time_sweeps(S)
+            t_qp_c = solver.time_kernel("qp", 10, FLUSH_BYTES)
+            t_ex_c = solver.time_kernel("excess", 10, FLUSH_BYTES)
+            t1, _ = timed_solves(pdr, torch, stream, solver, flush, 3)
+            solver.set_options(max_sweeps=2 * S)
+            t2, _ = timed_solves(pdr, torch, stream, solver, flush, 3)
+            solver.set_options(max_sweeps=S)
+            solver.reset()
+            solver.solve()
+            line["error_vs_oracle"] = error_vs_oracle(pdr, inst, solver)
+        graph_us = (statistics.median(t2) - statistics.median(t1)) * 1e3 / S
         n = inst.n
-        working_set = 4 * inst.K * (2 * m + n)  # both flow buffers and the heights, FP32
-        resident = working_set <= L2_RESIDENT_BYTES
-        t_qp, t_ex = t_qp_w, t_ex_w
         bytes_qp = update_bytes(args.algo, inst)
         bytes_ex = 4 * K * (m + n) + 4 * 2 * m + 8 * n  # f once, h out; incidence lists
-        share_qp = t_qp / (t_qp + t_ex)
         upd = {"eso": "edge_qp", "agd": "agd_step", "gdm": "gdm_step", "ck": "edge_qp_ck"}[args.algo]
         dom, t_dom, b_dom = (upd, t_qp, bytes_qp) if t_qp >= t_ex else ("excess_height", t_ex, bytes_ex)
         t_dom_c = t_qp_c if dom == upd else t_ex_c
         peak, peak_src = load_peaks()
         achieved = b_dom / (t_dom / 1e3) / 1e9
-        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        resident = working_set <= L2_RESIDENT_BYTES
+        line["roofline"] = {"bound": "l2" if resident else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": ncu_traffic(dom), "kernel": dom,
                             "peak_source": f"{peak_src} hbm_gbs (burst copy)",
-                            "timing": "mean over the %d sweeps of one step from f = 0, CUDA events around "
-                                      "each launch" % S,
-                            "l2_state": ("warm: the working set (%.0f MB) stays in L2 across the timed sweeps"
-                                         % (working_set / 1e6)) if resident else
-                                        ("the working set (%.0f MB) exceeds L2: the rows stream from HBM "
-                                         "every sweep" % (working_set / 1e6)),
+                            "timing": "mean launch over the %d sweeps of one step from f = 0, CUDA events around "
+                                      "each launch on the solver's stream" % S,
                             "kernel_us": {upd: t_qp * 1e3, "excess_height": t_ex * 1e3},
+                            "kernel_us_sum_per_sweep": (t_qp + t_ex) * 1e3,
+                            "graph_loop_us_per_sweep": graph_us,
+                            "step_us_per_sweep": ms_step * 1e3 / S,
                             "algorithmic_bytes": {upd: bytes_qp, "excess_height": bytes_ex},
-                            "share_update": share_qp,
+                            "sweep_algorithmic_bytes": bytes_qp + bytes_ex,
+                            "sweep_achieved_gbs": (bytes_qp + bytes_ex) / (graph_us / 1e6) / 1e9,
+                            "share_update": t_qp / (t_qp + t_ex),
+                            "l2_state": ("warm: the working set (%.0f MB) stays in L2" % (working_set / 1e6))
+                                        if resident else
+                                        ("the working set (%.2f GB) exceeds L2: the rows stream from HBM "
+                                         "every sweep" % (working_set / 1e9)),
                             "cold_l2": {"kernel_us": {upd: t_qp_c * 1e3, "excess_height": t_ex_c * 1e3},
-                                        "achieved": b_dom / (t_dom_c / 1e3) / 1e9,
                                         "frac": b_dom / (t_dom_c / 1e3) / 1e9 / peak}}
-        # time to the paper's stop rule (|z^(t) - z^(t-1)| < 1e-6) from f = 0
-        if args.workload != "knn2500_k500":
-            if world == 1:
-                line["cpu_baseline"] = cpu_baseline(inst, budget_s=12.0)
-            solver.close()
-            print(json.dumps(line), flush=True)
-            return
-        with torch.cuda.stream(stream):
-            with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=1e-6,
-                                          resid_tol=1e-6, max_sweeps=1000000, edge_variant=args.edge_variant,
-                                          excess_variant=args.excess_variant) as sv:
-                rr = sv.solve()
-        line["time_to_eps"] = {"rule": "|z^(t)-z^(t-1)| < 1e-6 (Alg. 1)", "sweeps": rr["sweeps"],
-                               "ms": rr["ms_total"], "z": rr["z"], "cap_rel": rr["cap_rel"],
-                               "cons_rel": rr["cons_rel"], "verdict": rr["verdict_name"]}
         if world == 1:  # the host cores are shared by the ranks of a multi-GPU run
             line["cpu_baseline"] = cpu_baseline(inst)
     solver.close()
+    if extras:
+        del out, host
+        line["l2_resident_knn2500_k500"] = l2_resident_block(pdr, torch, stream, side["knn"], flush)
+        line["time_to_residual"] = residual_block(pdr, torch, stream, inst)
+        if not args.no_forms:
+            line["batched_form"] = batch_forms_block(pdr, torch, stream, side["batch"], side["small"], flush)
+            line["differentiated_form"] = adjoint_block(pdr, torch, stream, side["c5"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -90,7 +90,11 @@ typedef enum {
     PDR_STOP_RESIDUAL = 2,   /* cap_rel <= resid_tol and cons_rel <= resid_tol */
     PDR_STOP_RELATIVE = 3,   /* |z^(t) - z^(t-1)| <= eps_rel * z^(t) */
     PDR_STOP_NUMERIC = 4,    /* z is not finite */
-    PDR_STOP_STALL = 5       /* FP32 phase of PDR_PREC_FP32_FP64TAIL: z^(t) >= z^(t-1) */
+    PDR_STOP_STALL = 5,      /* FP32 phase of PDR_PREC_FP32_FP64TAIL: z^(t) >= z^(t-1) */
+    PDR_STOP_PLATEAU = 6     /* FP32 phase of PDR_PREC_FP32_FP64TAIL: over a window of 1024 sweeps
+                                the smallest max(cap_rel, cons_rel), already below 1000 x resid_tol
+                                (1e-3 when resid_tol <= 0), fell by less than 1e-4 of the previous
+                                window's (the FP32 rounding floor) */
 } pdr_stop_reason;
 
 typedef struct {
@@ -206,7 +210,12 @@ pdr_status pdr_reset(pdr_ctx *ctx);
  * supplies f >= 0). */
 pdr_status pdr_set_flows(pdr_ctx *ctx, const double *f);
 
-/* Copies the current flows to host f[m*K] (double, edge-major). */
+/* Copies the current flows to f[m*K] (double, edge-major), caller-owned.
+ * f may be pageable host memory, or any memory the GPU can write (pinned
+ * host memory from cudaMallocHost / cudaHostRegister, device or managed
+ * memory): there a kernel packs and widens the rows into f directly.
+ * Synchronises the context's stream.  Errors: PDR_ERR_INVALID_ARG (f NULL
+ * with m > 0), PDR_ERR_CUDA. */
 pdr_status pdr_flows(pdr_ctx *ctx, double *f);
 
 /* Checkpoint and resume of a solve (the loop state of Alg. 1, 3 and 4).
@@ -253,6 +262,18 @@ pdr_status pdr_set_state(pdr_ctx *ctx, const void *buf, int64_t bytes);
  * - hold_end = 0: normal operation.
  * Errors: PDR_ERR_INVALID_ARG. */
 pdr_status pdr_debug_wait(pdr_ctx *ctx, int64_t cycles, int32_t hold_end);
+
+/* Test hook for the time limit of the persistent engine's grid barrier
+ * (pdr_options.use_graph = 2).  No counterpart in the paper.
+ * - Each wait at the barrier gives up after limit_ns nanoseconds of the
+ *   GPU's global timer (default 2e9, 2 s; 1e5 <= limit_ns <= 2e9), raises a
+ *   flag that ends every other block's wait, and every block leaves the
+ *   kernel; the solve returns PDR_ERR_TIMEOUT and the context stays usable.
+ * - withhold = 1: block 0 leaves the kernel at its first barrier without
+ *   arriving (it has no copy in flight), so the other blocks' waits run out.
+ * - withhold = 0: normal operation.
+ * Errors: PDR_ERR_INVALID_ARG. */
+pdr_status pdr_debug_barrier(pdr_ctx *ctx, int64_t limit_ns, int32_t withhold);
 
 /* Test hook for host-side failure injection: the nth device allocation the
  * library makes from now on (in pdr_create, pdr_set_options, pdr_batch_create,
@@ -342,8 +363,11 @@ int32_t pdr_num_edge_variants(void);
 
 /* Row capacity of variant v: the largest K it holds in `precision`
  * (PDR_PREC_FP32 or PDR_PREC_FP64).  *pipelined (may be NULL) receives 1 for
- * the persistent pipelined forms of Alg. 2, which Alg. 3/4 run in their plain
- * form.  Returns -1 if v or precision is out of range (nothing written). */
+ * the persistent pipelined warp forms of Alg. 2 and 2 for the staged block
+ * forms (one block per SM that keeps the next edge's rows in flight as bulk
+ * copies into shared memory), 0 for the plain forms; Alg. 3/4 run the plain
+ * form of a pipelined or staged variant.  Returns -1 if v or precision is out
+ * of range (nothing written). */
 int32_t pdr_edge_variant_capacity(int32_t v, int32_t precision, int32_t *pipelined);
 
 /* In-adjacency and degrees of a graph that already lives in device memory,
@@ -371,16 +395,22 @@ int32_t pdr_edge_variant_capacity(int32_t v, int32_t precision, int32_t *pipelin
  * Scratch: 4 MiB of device memory per GPU that loads the library, held until
  * the process exits, shared by every call: calls whose GPU work overlaps
  * (other host threads, or other streams of the same device) race on it and
- * must be serialised by the caller.  The first call on each device looks up
- * the scratch's device address (with that device current); make that first
- * call before any stream capture begins.  On failure pdr_last_error(NULL)
- * returns the message.  Errors: PDR_ERR_INVALID_ARG, PDR_ERR_CUDA. */
+ * must be serialised by the caller.  Every call looks up the scratch's
+ * device address on the current device before it launches anything (nothing
+ * is cached across calls, so a cudaDeviceReset between calls is harmless);
+ * make the first call on a device before any stream capture begins.  On
+ * failure pdr_last_error(NULL) returns the message.  Errors:
+ * PDR_ERR_INVALID_ARG, PDR_ERR_CUDA. */
 pdr_status pdr_adjacency_static(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, int64_t *in_ptr,
                                 int32_t *in_eid, int32_t *deg, void *stream);
 
 /* Replaces the capacities u[m] and/or the demands d[K] (NULL keeps them);
- * same domain as pdr_create.  The flows are kept.  Errors:
- * PDR_ERR_INVALID_ARG. */
+ * same domain as pdr_create.  The flows are kept.  u and d may be host
+ * memory, or both device (or managed) memory: then they are checked and
+ * converted on the device (no host copy; the call synchronises the
+ * context's stream to read the check), with the same results.  An array
+ * outside the domain changes nothing.  Errors: PDR_ERR_INVALID_ARG (domain,
+ * or one host and one device array), PDR_ERR_CUDA. */
 pdr_status pdr_set_data(pdr_ctx *ctx, const double *u, const double *d);
 
 /* Differentiated form.  L(u, d) = z(f^(T)), the objective of Alg. 1 after T
@@ -392,9 +422,10 @@ pdr_status pdr_set_data(pdr_ctx *ctx, const double *u, const double *d);
  * active set, the derivative of the active set the forward took).  Flows are checkpointed every ckpt_every sweeps, so memory
  * is about (T/ckpt_every + ckpt_every) flow arrays.  Runs in the context's
  * working precision (FP32 or FP64; gradients accumulate in FP64) and leaves
- * f^(T) as the current flows.  Errors: PDR_ERR_INVALID_ARG (T < 0,
- * ckpt_every < 1, or a context that runs Alg. 3 or Alg. 4), PDR_ERR_OOM,
- * PDR_ERR_CUDA. */
+ * f^(T) as the current flows.  grad_u and grad_d may be host or device
+ * memory (the copy follows unified addressing); L is a host double.
+ * Errors: PDR_ERR_INVALID_ARG (T < 0, ckpt_every < 1, or a context that
+ * runs Alg. 3 or Alg. 4), PDR_ERR_OOM, PDR_ERR_CUDA. */
 pdr_status pdr_backward(pdr_ctx *ctx, int64_t T, int32_t ckpt_every, double *L, double *grad_u, double *grad_d);
 
 /* ------------------------------------------------------------------------ */

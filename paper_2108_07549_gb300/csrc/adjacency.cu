@@ -140,20 +140,15 @@ cudaError_t build_adjacency(int32_t n, int64_t m, const int64_t* row_ptr, const 
 // call makes no cudaMalloc or cudaFree.
 #include "pdr.h"
 
-#include <mutex>
 #include <string>
 
 namespace pdr {
 namespace {
 
 constexpr int64_t kStaticMaxVertices = int64_t(1) << 18;  // 262,144 vertices: 4 MiB of scratch per GPU
-constexpr int kMaxDevices = 64;
 
 // [0, max): in-degree counts; [max, 2 max): fill cursors; [2 max]: input-error word
 __device__ __align__(256) unsigned long long g_static_scratch[2 * kStaticMaxVertices + 1];
-
-std::mutex g_static_mutex;
-void* g_static_addr[kMaxDevices] = {};
 
 // Input checks on the device: row_ptr[0] = 0, non-decreasing, row_ptr[n] = m,
 // 0 <= col[e] < n.  Sets bits of *err instead of trusting the arrays.
@@ -191,28 +186,15 @@ extern "C" pdr_status pdr_adjacency_static(int32_t n, int64_t m, const int64_t* 
         return PDR_ERR_INVALID_ARG;
     }
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        set_thread_error(std::string("pdr_adjacency_static: cudaGetDevice: ") + cudaGetErrorString(e));
+    // The host-side name of the array is not a device address: ask the
+    // runtime for the current device's copy on every call.  The lookup is
+    // cheap, and nothing is cached that a cudaDeviceReset could leave stale.
+    void* base = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&base, g_static_scratch);
+    if (e != cudaSuccess || !base) {
+        set_thread_error(std::string("pdr_adjacency_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         cudaGetLastError();
         return PDR_ERR_CUDA;
-    }
-    void* base = nullptr;
-    {
-        // once per device, with that device current: the host-side name of
-        // the array is not a device address, so ask the runtime for it
-        std::lock_guard<std::mutex> lock(g_static_mutex);
-        if (!g_static_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
-            if (e != cudaSuccess) {
-                g_static_addr[dev] = nullptr;
-                set_thread_error(std::string("pdr_adjacency_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-                cudaGetLastError();
-                return PDR_ERR_CUDA;
-            }
-        }
-        base = g_static_addr[dev];
     }
     unsigned long long* cnt = static_cast<unsigned long long*>(base);
     unsigned long long* cursor = cnt + kStaticMaxVertices;

@@ -159,6 +159,7 @@ struct pdr_ctx {
     int64_t trace_cap = 0;
     // residuals
     double *r_h64 = nullptr, *r_part = nullptr;
+    int* data_err = nullptr;  // error bits of a device-side pdr_set_data
     ResidOut* r_out = nullptr;
     ResidOut* hr_out = nullptr;  // pinned
     int r_grid_v = 1, r_grid_e = 1;
@@ -180,6 +181,9 @@ struct pdr_ctx {
     // excess form; changed only by pdr_debug_wait (tests of the time limit)
     long long wait_cycles = kWaitCycles;
     int hold_end = 0;
+    // persistent engine's grid barrier; changed only by pdr_debug_barrier
+    long long barrier_ns = kBarrierNs;
+    int hold_barrier = 0;
     int64_t t_widen = -1;  // t at which the FP64 tail of the last solve began (-1: none)
 
     pdr_status fail(pdr_status code, const std::string& msg)
@@ -315,6 +319,8 @@ SweepArgs<T> make_args(pdr_ctx* ctx, int mode, int use_cond = 0, cudaGraphCondit
     a.xv_start = ctx->xv_start[ctx->xform];
     a.wait_cycles = ctx->wait_cycles;
     a.hold_end = ctx->hold_end;
+    a.barrier_ns = ctx->barrier_ns;
+    a.hold_barrier = ctx->hold_barrier;
     a.grid_v = ctx->xform ? ctx->xgrid[ctx->xform] : ctx->grid_v[p];
     a.grid_e = ctx->grid_e[p];
     a.n_psi = ctx->n_psi[p];
@@ -498,6 +504,10 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
     } else {
         c32 = edge_config<float>(Kp);
         c64 = edge_config<double>(Kp);
+        if (is_gd(o)) {
+            c32 = gd_preferred_config(c32);
+            c64 = gd_preferred_config(c64);
+        }
     }
     if (c32 < 0 || (o.precision != PDR_PREC_FP32 && c64 < 0))
         return ctx->fail(PDR_ERR_UNSUPPORTED,
@@ -520,6 +530,73 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
 
 __global__ void set_state_kernel(DevState* st, DevState v) { *st = v; }
 
+// pdr_set_data from device arrays, the same arithmetic as the host path.
+// Block 0 thread 0 checks the domain and sums the positive capacities in
+// edge order (the mean positive capacity scales cap_rel, as at create time);
+// nothing is written when a value is out of its domain.
+__global__ void set_data_check_kernel(int64_t m, int K, const double* __restrict__ u, const double* __restrict__ d,
+                                      double* __restrict__ ubar, int* __restrict__ err)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int bad = 0;
+    double usum = 0.0;
+    int64_t upos = 0;
+    if (u)
+        for (int64_t e = 0; e < m; ++e) {
+            const double x = u[e];
+            if (!isfinite(x) || x < 0.0) bad |= 1;
+            if (x > 0.0) {
+                usum += x;
+                ++upos;
+            }
+        }
+    if (d)
+        for (int k = 0; k < K; ++k)
+            if (!isfinite(d[k]) || !(d[k] > 0.0)) bad |= 2;
+    *ubar = upos ? usum / (double)upos : 1.0;
+    *err = bad;
+}
+
+__global__ void set_data_fill_kernel(int64_t m, int K, int Kp, const double* __restrict__ u,
+                                     const double* __restrict__ d, const double* __restrict__ ubar,
+                                     const int* __restrict__ err, double* u_d, float* u_f, double* inv_scale,
+                                     float* inv_scale_f, double* dem_d, float* dem_f, double* inv_dem_d,
+                                     float* inv_dem_f)
+{
+    if (*err) return;
+    const double ub = *ubar;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u && e < m; e += stride) {
+        const double x = u[e];
+        const double inv = 1.0 / (x > ub ? x : ub);
+        u_d[e] = x;
+        u_f[e] = (float)x;
+        inv_scale[e] = inv;
+        inv_scale_f[e] = (float)inv;
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d && k < Kp; k += stride) {
+        const double x = k < K ? d[k] : 0.0;
+        dem_d[k] = x;
+        dem_f[k] = (float)x;
+        inv_dem_d[k] = k < K ? 1.0 / x : 0.0;
+        inv_dem_f[k] = k < K ? (float)(1.0 / x) : 0.0f;
+    }
+}
+
+cudaError_t launch_set_data(int64_t m, int K, int Kp, const double* u, const double* d, double* u_d, float* u_f,
+                            double* inv_scale, float* inv_scale_f, double* dem_d, float* dem_f, double* inv_dem_d,
+                            float* inv_dem_f, int* err, cudaStream_t stream)
+{
+    // the mean positive capacity sits in the slot after the error word
+    double* ubar = reinterpret_cast<double*>(err) + 1;
+    set_data_check_kernel<<<1, 32, 0, stream>>>(m, K, u, d, ubar, err);
+    const int64_t want = ((m > Kp ? m : Kp) + 255) / 256;
+    const int grid = (int)(want < 1 ? 1 : (want < 1024 ? want : 1024));
+    set_data_fill_kernel<<<grid, 256, 0, stream>>>(m, K, Kp, u, d, ubar, err, u_d, u_f, inv_scale, inv_scale_f,
+                                                   dem_d, dem_f, inv_dem_d, inv_dem_f);
+    return cudaGetLastError();
+}
+
 pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise, bool keep_zprev = false)
 {
     if (fresh) ctx->resume_pending = false;
@@ -537,6 +614,12 @@ pdr_status init_state(pdr_ctx* ctx, bool fresh, int stop_on_rise, bool keep_zpre
     v.stop = 0;
     v.reason = 0;
     v.stop_on_rise = stop_on_rise;
+    // the residual-plateau rule runs with the stall rule, in the FP32 phase of
+    // the tail mode, and starts its windows at this phase's first sweep
+    v.plat_window = stop_on_rise ? kPlateauWindow : 0;
+    v.plat_t0 = keep_zprev ? ctx->hst->plat_t0 : v.t;  // a resumed solve keeps its windows
+    v.plat_cur = keep_zprev ? ctx->hst->plat_cur : INFINITY;
+    v.plat_prev = keep_zprev ? ctx->hst->plat_prev : INFINITY;
     set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, v);
     CK(cudaGetLastError());
     return PDR_OK;
@@ -617,7 +700,7 @@ pdr_status build_graph(pdr_ctx* ctx)
 // limit or a non-finite z).
 bool needs_fp64_tail(int reason)
 {
-    return reason == STOP_OBJECTIVE || reason == STOP_RELATIVE || reason == STOP_STALL;
+    return reason == STOP_OBJECTIVE || reason == STOP_RELATIVE || reason == STOP_STALL || reason == STOP_PLATEAU;
 }
 
 // Moves the current FP32 state (flows; Alg. 3/4 rates and velocities) into
@@ -751,8 +834,10 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     ctx->cur = (int)((ctx->hst->t - t_start) & 1);
     // The sweep that stopped also ran its edge QPs (their output is
     // discarded) and wrote their congestion partials: recompute those of the
-    // returned flows f^(t), keeping the warm starts.
-    if (ctx->hst->stop) return refresh_psi<T>(ctx, nullptr, true);
+    // returned flows f^(t), keeping the warm starts.  A stop by the sweep cap
+    // skipped those updates (final_evaluation), so its partials are still
+    // the returned flows'.
+    if (ctx->hst->stop && ctx->hst->reason != STOP_MAX_SWEEPS) return refresh_psi<T>(ctx, nullptr, true);
     return PDR_OK;
 }
 
@@ -760,8 +845,8 @@ template <typename T>
 pdr_status residuals_T(pdr_ctx* ctx)
 {
     SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
-    CK(launch_residuals<T>(a, ctx->u_d, ctx->dem_d, ctx->r_h64, ctx->r_part, ctx->r_grid_v, ctx->r_grid_e, ctx->r_out,
-                           ctx->stream));
+    const ResidIn r{ctx->u_d, ctx->dem_d, ctx->inv_deg_d, ctx->inv_dem_f};
+    CK(launch_residuals<T>(a, r, ctx->r_h64, ctx->r_part, ctx->r_grid_v, ctx->r_grid_e, ctx->r_out, ctx->stream));
     CK(cudaMemcpyAsync(ctx->hr_out, ctx->r_out, sizeof(ResidOut), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return PDR_OK;
@@ -785,6 +870,19 @@ pdr_status residuals_into(pdr_ctx* ctx, pdr_result* r)
     else if (o.cap_rel <= tol && o.cons_rel <= tol) r->verdict = PDR_VERDICT_FEASIBLE;
     else r->verdict = PDR_VERDICT_UNKNOWN;
     return PDR_OK;
+}
+
+// True for memory that only the device may dereference (device or managed
+// allocations); host memory, pinned or not, is read by the host directly.
+bool is_device_memory(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
 // Copies a padded device array [rows x Kp] of T into host double [rows x K].
@@ -957,9 +1055,10 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, mask, ctx->num_sms, ctx->stream));
         }
     }
+    // the gradients go to host or device memory alike (unified addressing)
     if (grad_u && ctx->m > 0)
-        CKB(cudaMemcpyAsync(grad_u, ubar, sizeof(double) * ctx->m, cudaMemcpyDeviceToHost, ctx->stream));
-    if (grad_d) CKB(cudaMemcpyAsync(grad_d, dbar, sizeof(double) * ctx->K, cudaMemcpyDeviceToHost, ctx->stream));
+        CKB(cudaMemcpyAsync(grad_u, ubar, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->stream));
+    if (grad_d) CKB(cudaMemcpyAsync(grad_d, dbar, sizeof(double) * ctx->K, cudaMemcpyDefault, ctx->stream));
     CKB(cudaStreamSynchronize(ctx->stream));
 #undef CKB
     cleanup();
@@ -993,7 +1092,8 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->f32[0], ctx->f32[1], ctx->h32, ctx->f64[0], ctx->f64[1], ctx->h64, ctx->part_h, ctx->part_cons, ctx->part_capb, ctx->part_psi, ctx->part_cap, ctx->st,
                    ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta[0], ctx->theta[1],
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
-                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3]};
+                   ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3],
+                   ctx->data_err};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (ctx->hst) cudaFreeHost(ctx->hst);
@@ -1125,6 +1225,7 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->r_part, double, resid_part_count(ctx->r_grid_v, ctx->r_grid_e));
     ALLOC(ctx->r_out, ResidOut, 1);
     ALLOC(ctx->psi_tmp, double, m);
+    ALLOC(ctx->data_err, int, 4);  // error word, then the mean positive capacity (8-byte aligned)
     CKC(cudaMallocHost(&ctx->hst, sizeof(DevState)));
     CKC(cudaMallocHost(&ctx->hr_out, sizeof(ResidOut)));
     std::memset(ctx->hst, 0, sizeof(DevState));
@@ -1218,7 +1319,8 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
     std::string why;
     if (!options_ok(&o, &why)) return ctx->fail(PDR_ERR_INVALID_ARG, why);
     const bool variant_changed = o.edge_variant != ctx->opt.edge_variant ||
-                                 (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0);
+                                 (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0) ||
+                                 (o.edge_variant < 0 && is_gd(o) != is_gd(ctx->opt));
     if (variant_changed) {
         const pdr_status vs = select_edge_variants(ctx, o);  // writes nothing on failure
         if (vs != PDR_OK) return vs;
@@ -1310,6 +1412,20 @@ pdr_status pdr_set_flows(pdr_ctx* ctx, const double* f)
 pdr_status pdr_flows(pdr_ctx* ctx, double* f)
 {
     if (!ctx || (!f && ctx->m > 0)) return ctx ? ctx->fail(PDR_ERR_INVALID_ARG, "f is NULL") : PDR_ERR_INVALID_ARG;
+    if (ctx->m == 0) return PDR_OK;
+    // A destination the GPU can write (pinned host memory, device or managed
+    // memory) receives the widened rows straight from a kernel; pageable
+    // host memory goes through a host-side staging copy.
+    cudaPointerAttributes attr{};
+    const cudaError_t ae = cudaPointerGetAttributes(&attr, f);
+    if (ae != cudaSuccess) cudaGetLastError();
+    if (ae == cudaSuccess && attr.type != cudaMemoryTypeUnregistered && attr.devicePointer) {
+        double* dst = static_cast<double*>(attr.devicePointer);
+        if (ctx->cur_prec) CK(launch_widen_rows<double>(ctx->f64[ctx->cur], ctx->m, ctx->K, ctx->Kp, dst, ctx->stream));
+        else CK(launch_widen_rows<float>(ctx->f32[ctx->cur], ctx->m, ctx->K, ctx->Kp, dst, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return PDR_OK;
+    }
     return ctx->cur_prec ? copy_rows_out<double>(ctx, ctx->f64[ctx->cur], ctx->m, f)
                          : copy_rows_out<float>(ctx, ctx->f32[ctx->cur], ctx->m, f);
 }
@@ -1324,13 +1440,15 @@ pdr_status pdr_flows(pdr_ctx* ctx, double* f)
 
 namespace {
 constexpr uint32_t kStateMagic = 0x53524450u;  // "PDRS"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 
 struct StateHeader {
     uint32_t magic, version;
     int32_t n, K, Kp, algo, prec, stopped;
     int64_t m, t, evals, t_widen, ntrace;
     double z_prev, z;
+    int64_t plat_t0;            // residual-plateau window of the tail mode's FP32 phase
+    double plat_cur, plat_prev;
 };
 
 struct StateLayout {
@@ -1394,6 +1512,9 @@ pdr_status pdr_get_state(pdr_ctx* ctx, void* buf, int64_t bytes)
     h.ntrace = ntrace;
     h.z_prev = ctx->hst->z_prev;
     h.z = ctx->hst->z;
+    h.plat_t0 = ctx->hst->plat_t0;
+    h.plat_cur = ctx->hst->plat_cur;
+    h.plat_prev = ctx->hst->plat_prev;
     char* out = static_cast<char*>(buf);
     std::memcpy(out, &h, sizeof h);
     char* q = out + sizeof h;
@@ -1468,6 +1589,9 @@ pdr_status pdr_set_state(pdr_ctx* ctx, const void* buf, int64_t bytes)
     v.max_sweeps = ctx->opt.max_sweeps;
     v.trace_len = ctx->trace_cap;
     v.evals = h.stopped && h.evals > 0 ? h.evals - 1 : h.evals;
+    v.plat_t0 = h.plat_t0;
+    v.plat_cur = h.plat_cur;
+    v.plat_prev = h.plat_prev;
     set_state_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, v);
     CK(cudaGetLastError());
     s = read_state(ctx);
@@ -1496,6 +1620,17 @@ pdr_status pdr_debug_wait(pdr_ctx* ctx, int64_t cycles, int32_t hold_end)
     return PDR_OK;
 }
 
+pdr_status pdr_debug_barrier(pdr_ctx* ctx, int64_t limit_ns, int32_t withhold)
+{
+    if (!ctx) return PDR_ERR_INVALID_ARG;
+    if (limit_ns < 100000 || limit_ns > kBarrierNs)
+        return ctx->fail(PDR_ERR_INVALID_ARG, "limit_ns must lie in [1e5, 2e9]");
+    if (withhold != 0 && withhold != 1) return ctx->fail(PDR_ERR_INVALID_ARG, "withhold must be 0 or 1");
+    ctx->barrier_ns = limit_ns;
+    ctx->hold_barrier = withhold;
+    return PDR_OK;
+}
+
 pdr_status pdr_backward(pdr_ctx* ctx, int64_t T, int32_t ckpt_every, double* L, double* grad_u, double* grad_d)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
@@ -1512,6 +1647,20 @@ pdr_status pdr_backward(pdr_ctx* ctx, int64_t T, int32_t ckpt_every, double* L, 
 pdr_status pdr_set_data(pdr_ctx* ctx, const double* u, const double* d)
 {
     if (!ctx) return PDR_ERR_INVALID_ARG;
+    // arrays the host cannot read directly (device or managed memory) are
+    // checked and converted on the device
+    if (is_device_memory(u) || is_device_memory(d)) {
+        if ((u && !is_device_memory(u)) || (d && !is_device_memory(d)))
+            return ctx->fail(PDR_ERR_INVALID_ARG, "u and d must both be host or both be device memory");
+        int bad = 0;
+        CK(launch_set_data(ctx->m, ctx->K, ctx->Kp, u, d, ctx->u_d, ctx->u_f, ctx->inv_scale, ctx->inv_scale_f,
+                           ctx->dem_d, ctx->dem_f, ctx->inv_dem_d, ctx->inv_dem_f, ctx->data_err, ctx->stream));
+        CK(cudaMemcpyAsync(&bad, ctx->data_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (bad & 1) return ctx->fail(PDR_ERR_INVALID_ARG, "capacities must be finite and >= 0 (nothing changed)");
+        if (bad & 2) return ctx->fail(PDR_ERR_INVALID_ARG, "demands must be finite and > 0 (nothing changed)");
+        return refresh_psi_current(ctx);
+    }
     if (u)
         for (int64_t e = 0; e < ctx->m; ++e)
             if (!std::isfinite(u[e]) || u[e] < 0.0)
@@ -1885,7 +2034,7 @@ int32_t pdr_num_edge_variants(void) { return num_edge_configs(); }
 int32_t pdr_edge_variant_capacity(int32_t v, int32_t precision, int32_t* pipelined)
 {
     if (v < 0 || v >= num_edge_configs() || (precision != PDR_PREC_FP32 && precision != PDR_PREC_FP64)) return -1;
-    if (pipelined) *pipelined = edge_config_pipelined(v) ? 1 : 0;
+    if (pipelined) *pipelined = edge_config_pipelined(v) ? 1 : edge_config_staged(v) ? 2 : 0;
     return precision == PDR_PREC_FP32 ? edge_capacity<float>(v) : edge_capacity<double>(v);
 }
 
@@ -1982,11 +2131,18 @@ struct pdr_batch {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<char> graph_mask[2];
     bool graph_tried[2] = {false, false}, graph_ok[2] = {false, false};
+    // one-block-per-instance engine: the instances one block solves at speed
+    std::vector<char> small;              // size test passed (precision-independent part)
+    void* bargs[2] = {nullptr, nullptr};  // device SweepArgs<float> / <double> [count]
+    int* bids = nullptr;                  // device instance ids [count], grouped by variant
+    void* hstage = nullptr;               // pinned staging of the arguments and ids
 };
 
 namespace {
 
 constexpr int kBatchUnroll = 2;  // sweeps per instance per iteration of the batch's while loop
+constexpr int64_t kBlockElems = int64_t(1) << 18;  // m x Kp up to which one block solves an instance
+constexpr int64_t kBlockChunk = 2048;              // sweeps per launch of the one-block-per-instance kernel
 constexpr int kBatchPool = 32;   // capture streams
 
 pdr_status batch_fail(pdr_status code, const std::string& msg)
@@ -2149,25 +2305,166 @@ __global__ void set_counter_kernel(unsigned int* c, unsigned int v) { *c = v; }
 // Alg. 1 in precision T for the instances with run[i] set, from the states
 // their callers initialised (instance i's sweep counter starting at
 // t_start[i]); the others keep their stopped state.
+// Blocks of the cluster that solves an instance on the one-cluster-per-
+// instance engine: enough that each lane group of the cluster handles at
+// most about 16 edges per sweep (the edges of a group run one after the
+// other), a power of two up to 8.
+int batch_cluster_size(const pdr_ctx* c, int p)
+{
+    const int G = edge_group_lanes(c->cfg[p]);
+    const int64_t groups = (int64_t)(kBatchThreads / 32) * (32 / G);
+    const int64_t want = (c->m + groups * 16 - 1) / (groups * 16);
+    int cs = 1;
+    while (cs < want && cs < 8) cs <<= 1;
+    return cs;
+}
+
+// True if instance i runs on the one-block-per-instance engine in precision
+// p: a lane-group variant of at most 4 vectors per lane (the larger ones
+// spill at the block's register budget) and a small instance.
+bool batch_resident(const pdr_batch* b, int32_t i, int p)
+{
+    if (!b->small[i]) return false;
+    const int cfg = b->ctx[i]->cfg[p];
+    return batch_block_config(cfg) && edge_plain_config(cfg) <= 5;
+}
+
+// The instances of `blk` (set up by batch_run) on the one-block-per-instance
+// engine: launches of kBlockChunk sweeps, one per edge-kernel variant on its
+// own stream so that they run side by side, until every instance stopped.
 template <typename T>
-pdr_status batch_run(pdr_batch* b, const std::vector<char>& run, const std::vector<int64_t>& t_start)
+pdr_status batch_block_run(pdr_batch* b, const std::vector<char>& blk, const std::vector<int64_t>& t_start)
 {
     const int p = Prec<T>::id;
+    std::vector<int32_t> live;
+    for (int32_t i = 0; i < b->count; ++i)
+        if (blk[i]) live.push_back(i);
+    SweepArgs<T>* hargs = static_cast<SweepArgs<T>*>(b->hstage);
+    int* hids = reinterpret_cast<int*>(hargs + b->count);
+    SweepArgs<T>* dargs = static_cast<SweepArgs<T>*>(b->bargs[p]);
+    std::vector<cudaEvent_t> ev;
+    auto done = [&](pdr_status st) {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        return st;
+    };
+    auto cuda_err = [&](const char* what, cudaError_t e) {
+        return done(batch_fail(PDR_ERR_CUDA, std::string("batch: ") + what + ": " + cudaGetErrorString(e)));
+    };
+    for (int q = 0; q < 7; ++q) {  // the fork event and one per launch group (more on demand)
+        cudaEvent_t e;
+        const cudaError_t er = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (er != cudaSuccess) return cuda_err("event", er);
+        ev.push_back(e);
+    }
+    bool first = true;
+    while (!live.empty()) {
+        // arguments with the buffer parity of each instance's current flows
+        for (int32_t i : live) {
+            pdr_ctx* c = b->ctx[i];
+            const int par = first ? 0 : (int)((c->hst->t - t_start[i]) & 1);
+            const int csize = batch_cluster_size(c, p);
+            SweepArgs<T> a = make_args<T>(c, MODE_SOLVE, 0, 0, par, 0);
+            a.excess_form = 0;  // the gather form, run by the cluster's blocks
+            a.grid_v = csize;
+            a.grid_e = csize;
+            a.n_psi = csize * (kBatchThreads / 32);
+            a.pf_edges = 0;
+            a.l2_hints = 0;
+            a.active = nullptr;
+            hargs[i] = a;
+        }
+        // one launch per (lane-group variant, cluster size), largest clusters first
+        struct Group {
+            int cfg, csize, off, count;
+        };
+        std::vector<Group> groups;
+        int pos = 0;
+        for (int csize = 8; csize >= 1; csize >>= 1)
+            for (int cfg = 0; cfg <= 5; ++cfg) {
+                const int off = pos;
+                for (int32_t i : live)
+                    if (edge_plain_config(b->ctx[i]->cfg[p]) == cfg && batch_cluster_size(b->ctx[i], p) == csize)
+                        hids[pos++] = i;
+                if (pos > off) groups.push_back({cfg, csize, off, pos - off});
+            }
+        cudaError_t e = cudaMemcpyAsync(dargs, hargs, sizeof(SweepArgs<T>) * b->count, cudaMemcpyHostToDevice,
+                                        b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->bids, hids, sizeof(int) * pos, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], b->stream);
+        for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+            while (ev.size() < g + 2) {
+                cudaEvent_t x;
+                e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+                if (e != cudaSuccess) break;
+                ev.push_back(x);
+            }
+            if (e != cudaSuccess) break;
+            cudaStream_t sg = b->pool[g % b->pool.size()];
+            e = cudaStreamWaitEvent(sg, ev[0], 0);
+            if (e == cudaSuccess)
+                e = launch_batch_block<T>(groups[g].cfg, dargs, b->bids + groups[g].off, groups[g].count, groups[g].csize,
+                                          kBlockChunk, first ? 1 : 0, sg);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + g], sg);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev[1 + g], 0);
+        }
+        for (size_t q = 0; q < live.size() && e == cudaSuccess; ++q) {
+            pdr_ctx* c = b->ctx[live[q]];
+            e = cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_err("one-block-per-instance engine", e);
+        std::vector<int32_t> next;
+        for (int32_t i : live) {
+            if (b->ctx[i]->hst->fault)
+                return done(batch_fail(PDR_ERR_TIMEOUT, "instance " + std::to_string(i) + ": a device wait timed out"));
+            if (!b->ctx[i]->hst->stop) next.push_back(i);
+        }
+        live.swap(next);
+        first = false;
+    }
+    // current flows, and the congestion partials in the standalone kernels' layout
+    for (int32_t i = 0; i < b->count; ++i) {
+        if (!blk[i]) continue;
+        pdr_ctx* c = b->ctx[i];
+        c->cur = (int)((c->hst->t - t_start[i]) & 1);
+        const pdr_status st = refresh_psi<T>(c, nullptr, true);
+        if (st != PDR_OK) return done(st);
+    }
+    return done(PDR_OK);
+}
+
+template <typename T>
+pdr_status batch_run(pdr_batch* b, const std::vector<char>& run_all, const std::vector<int64_t>& t_start)
+{
+    const int p = Prec<T>::id;
+    // small instances go to the one-block-per-instance engine, the others to the graph
+    std::vector<char> blk(b->count, 0), run(run_all);
+    bool any_blk = false;
+    const bool use_graph = b->ctx[0]->opt.use_graph != 0;
+    for (int32_t i = 0; i < b->count; ++i)
+        if (run_all[i] && use_graph && batch_resident(b, i, p)) {
+            blk[i] = 1;
+            run[i] = 0;
+            any_blk = true;
+        }
     unsigned int running = 0;
     for (int32_t i = 0; i < b->count; ++i) {
-        if (!run[i]) continue;
+        if (!run_all[i]) continue;
         pdr_ctx* c = b->ctx[i];
         pdr_status s = ensure_velocity<T>(c);
         if (s != PDR_OK) return s;
         s = flows_to_buffer0<T>(c);
         if (s != PDR_OK) return s;
-        ++running;
+        if (run[i]) ++running;
+    }
+    if (any_blk) {
+        const pdr_status s = batch_block_run<T>(b, blk, t_start);
+        if (s != PDR_OK) return s;
     }
     if (running == 0) return PDR_OK;
     set_counter_kernel<<<1, 1, 0, b->stream>>>(b->active, running);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return batch_fail(PDR_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
-    const bool use_graph = b->ctx[0]->opt.use_graph != 0;
     if (use_graph && (!b->graph_tried[p] || b->graph_mask[p] != run)) {
         batch_destroy_graph(b, p);
         batch_build_graph<T>(b, run);
@@ -2258,6 +2555,21 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance* inst, const pdr_o
     }
     b->tuned_cfg.assign(count, -1);
     b->tuned_us.assign(count, -1.0);
+    b->small.assign(count, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        const pdr_ctx* c = b->ctx[i];
+        b->small[i] = !is_gd(o) && c->m > 0 && c->m * (int64_t)c->Kp <= kBlockElems;
+    }
+    for (int p = 0; p < 2; ++p)
+        if (cudaMalloc(&b->bargs[p], sizeof(SweepArgs<double>) * count) != cudaSuccess) {
+            cudaGetLastError();
+            return give_up(PDR_ERR_OOM, "batch: argument table allocation failed");
+        }
+    if (cudaMalloc(&b->bids, sizeof(int) * count) != cudaSuccess ||
+        cudaMallocHost(&b->hstage, (sizeof(SweepArgs<double>) + sizeof(int)) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return give_up(PDR_ERR_OOM, "batch: argument table allocation failed");
+    }
     for (int32_t i = 0; i < count; ++i) {
         pdr_ctx* c = b->ctx[i];
         if (o.edge_variant >= 0) {  // the caller's variant: no tuning
@@ -2377,6 +2689,10 @@ void pdr_batch_destroy(pdr_batch* b)
     for (cudaStream_t s : b->pool) cudaStreamDestroy(s);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->active) cudaFree(b->active);
+    for (void* q : b->bargs)
+        if (q) cudaFree(q);
+    if (b->bids) cudaFree(b->bids);
+    if (b->hstage) cudaFreeHost(b->hstage);
     cudaGetLastError();
     delete b;
 }

@@ -32,7 +32,7 @@ __device__ __forceinline__ T new_beta(const SweepArgs<T>& a, T beta, bool accept
 }
 
 // One aligned group of G lanes per edge; lane l holds row vectors l + q*G.
-template <typename T, int G, int V>
+template <typename T, int G, int V, bool M>
 __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
     }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
     const bool grow = (vst->t_sweep % 10) == 0;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -121,12 +122,12 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
             else
 #pragma unroll
                 for (int j = 0; j < N; ++j) fx[j] = T(0);
-            if (a.momentum && live) unpack(__ldg(reinterpret_cast<const VT*>(a.v_in + row) + v), vin);
+            if (M && live) unpack(__ldg(reinterpret_cast<const VT*>(a.v_in + row) + v), vin);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 const T st = beta * (d[q][j] - psi);
                 const T df = st > -fx[j] ? st : -fx[j];
-                if (a.momentum) {
+                if constexpr (M) {
                     const T vv = live ? vin[j] : T(0);
                     vo[j] = accept ? a.gamma * vv + df : vv;
                     const T x = fx[j] + vo[j];
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
             }
             if (live) {
                 reinterpret_cast<VT*>(a.f_out + row)[v] = pack4(o);
-                if (a.momentum) reinterpret_cast<VT*>(a.v_out + row)[v] = pack4(vo);
+                if (M) reinterpret_cast<VT*>(a.v_out + row)[v] = pack4(vo);
             }
         }
         rs = group_sum<G>(rs);
@@ -159,20 +160,22 @@ __global__ void __launch_bounds__(kThreads) gd_group_kernel(SweepArgs<T> a)
 }
 
 // One block of B threads per edge (large K); thread l holds row vectors l + q*B.
-template <typename T, int B, int V>
-__global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_block_kernel(SweepArgs<T> a)
+template <typename T, int B, int V, bool M>
+__global__ void __launch_bounds__(B, gd_min_blocks(B, V)) gd_block_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
     __shared__ T sa_buf[32];
     __shared__ int sb_buf[32];
+    __shared__ T sc_buf[32];
     volatile DevState* vst = a.st;
     if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
     }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
     const bool grow = (vst->t_sweep % 10) == 0;
     const int vpr = a.Kp / N;
     typename A::V zpsi = A::zero();
@@ -225,8 +228,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_blo
                 D += df * (df - d[q][j]);
             }
         }
-        block_sum2(s2, dummy, sa_buf, sb_buf);
-        block_sum2(D, dummy, sa_buf, sb_buf);
+        block_sum_pair(s2, D, sa_buf, sc_buf);
         const T over1 = s2 - ue;
         const T psin = over1 > T(0) ? over1 : T(0);
         const T dz = T(0.5) * (psin * psin - psi * psi) + D;
@@ -241,12 +243,12 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_blo
             else
 #pragma unroll
                 for (int j = 0; j < N; ++j) fx[j] = T(0);
-            if (a.momentum && live) unpack(__ldg(reinterpret_cast<const VT*>(a.v_in + row) + v), vin);
+            if (M && live) unpack(__ldg(reinterpret_cast<const VT*>(a.v_in + row) + v), vin);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 const T st = beta * (d[q][j] - psi);
                 const T df = st > -fx[j] ? st : -fx[j];
-                if (a.momentum) {
+                if constexpr (M) {
                     const T vv = live ? vin[j] : T(0);
                     vo[j] = accept ? a.gamma * vv + df : vv;
                     const T x = fx[j] + vo[j];
@@ -258,10 +260,13 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_blo
             }
             if (live) {
                 reinterpret_cast<VT*>(a.f_out + row)[v] = pack4(o);
-                if (a.momentum) reinterpret_cast<VT*>(a.v_out + row)[v] = pack4(vo);
+                if (M) reinterpret_cast<VT*>(a.v_out + row)[v] = pack4(vo);
             }
         }
-        block_sum2(rs, dummy, sa_buf, sb_buf);
+        // Alg. 3 stores f + df (accepted) or f (rejected), whose sums s2 and
+        // fs were formed above in this very order; Alg. 4 re-sums its row
+        if constexpr (M) block_sum2(rs, dummy, sa_buf, sb_buf);
+        else rs = accept ? s2 : fs;
         if (threadIdx.x == 0) {
             a.beta_out[e] = new_beta(a, beta, accept, grow);
             const T over = rs - ue;
@@ -282,28 +287,40 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 5 : (B <= 512 ? 2 : 1))) gd_blo
 // Same variant table as the edge-QP kernels (sweep.cu: kCfg); a pipelined
 // variant runs the plain form of the same capacity (the kernels stride over
 // the edges, so any grid works).
-template <typename T>
-cudaError_t launch_gd(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
+template <typename T, bool M>
+cudaError_t launch_gd_m(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
 {
     const int g = a.grid_e + 1;
     switch (edge_plain_config(cfg)) {
-    case 0: gd_group_kernel<T, 4, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 1: gd_group_kernel<T, 8, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 2: gd_group_kernel<T, 16, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 3: gd_group_kernel<T, 32, 1><<<g, kThreads, 0, stream>>>(a); break;
-    case 4: gd_group_kernel<T, 32, 2><<<g, kThreads, 0, stream>>>(a); break;
-    case 5: gd_group_kernel<T, 32, 4><<<g, kThreads, 0, stream>>>(a); break;
-    case 6: gd_group_kernel<T, 32, 8><<<g, kThreads, 0, stream>>>(a); break;
-    case 7: gd_block_kernel<T, 256, 2><<<g, 256, 0, stream>>>(a); break;
-    case 8: gd_block_kernel<T, 512, 2><<<g, 512, 0, stream>>>(a); break;
-    case 9: gd_block_kernel<T, 512, 3><<<g, 512, 0, stream>>>(a); break;
-    case 10: gd_block_kernel<T, 512, 4><<<g, 512, 0, stream>>>(a); break;
-    case 11: gd_block_kernel<T, 512, 5><<<g, 512, 0, stream>>>(a); break;
-    case 12: gd_block_kernel<T, 512, 8><<<g, 512, 0, stream>>>(a); break;
-    case 13: gd_block_kernel<T, 1024, 8><<<g, 1024, 0, stream>>>(a); break;
+    case 0: gd_group_kernel<T, 4, 1, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 1: gd_group_kernel<T, 8, 1, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 2: gd_group_kernel<T, 16, 1, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 3: gd_group_kernel<T, 32, 1, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 4: gd_group_kernel<T, 32, 2, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 5: gd_group_kernel<T, 32, 4, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 6: gd_group_kernel<T, 32, 8, M><<<g, kThreads, 0, stream>>>(a); break;
+    case 7: gd_block_kernel<T, 128, 4, M><<<g, 128, 0, stream>>>(a); break;
+    case 8: gd_block_kernel<T, 256, 2, M><<<g, 256, 0, stream>>>(a); break;
+    case 9: gd_block_kernel<T, 512, 2, M><<<g, 512, 0, stream>>>(a); break;
+    case 10: gd_block_kernel<T, 512, 3, M><<<g, 512, 0, stream>>>(a); break;
+    case 11: gd_block_kernel<T, 512, 4, M><<<g, 512, 0, stream>>>(a); break;
+    case 12: gd_block_kernel<T, 512, 5, M><<<g, 512, 0, stream>>>(a); break;
+    case 13: gd_block_kernel<T, 256, 10, M><<<g, 256, 0, stream>>>(a); break;
+    case 14: gd_block_kernel<T, 512, 8, M><<<g, 512, 0, stream>>>(a); break;
+    case 15: gd_block_kernel<T, 1024, 8, M><<<g, 1024, 0, stream>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Same variant table as the edge-QP kernels (sweep.cu: kCfg); a pipelined
+// variant runs the plain form of the same capacity (the kernels stride over
+// the edges, so any grid works).  Alg. 3 and Alg. 4 are compiled apart, so
+// that Alg. 3 carries no velocity registers.
+template <typename T>
+cudaError_t launch_gd(const SweepArgs<T>& a, int cfg, cudaStream_t stream)
+{
+    return a.momentum ? launch_gd_m<T, true>(a, cfg, stream) : launch_gd_m<T, false>(a, cfg, stream);
 }
 
 template cudaError_t launch_gd<float>(const SweepArgs<float>&, int, cudaStream_t);

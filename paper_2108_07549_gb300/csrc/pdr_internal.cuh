@@ -22,7 +22,20 @@
 namespace pdr {
 
 constexpr int kThreads = 256;  // block size of every sweep kernel
+constexpr int kBatchThreads = 512;  // block size of the one-block-per-instance batch kernel
+// Resident blocks per SM that the block forms of the edge kernels are
+// compiled for (the register cap that follows from it: 65,536 / (B x that)).
+constexpr int block_min_blocks(int B, int V)
+{
+    return B <= 128 ? 12 : B <= 256 ? (V <= 2 ? 6 : 4) : B <= 512 ? (V <= 5 ? 3 : 2) : (V <= 3 ? 2 : 1);
+}
+// The same for the Alg. 3 / Alg. 4 block forms (more live values per element).
+constexpr int gd_min_blocks(int B, int V)
+{
+    return B <= 128 ? 10 : B <= 256 ? (V <= 2 ? 5 : 3) : B <= 512 ? 2 : 1;
+}
 constexpr long long kWaitCycles = 4ll << 30;  // default limit of a device-side wait: ~2 s at the SM clock
+constexpr long long kBarrierNs = 2000000000ll;  // default limit of a grid-barrier wait: 2 s of the global timer
 
 // Kernel modes.
 enum : int {
@@ -38,7 +51,8 @@ enum : int {
     STOP_RESIDUAL = 2,
     STOP_RELATIVE = 3,
     STOP_NUMERIC = 4,
-    STOP_STALL = 5
+    STOP_STALL = 5,
+    STOP_PLATEAU = 6
 };
 
 // Solver state that lives on the device and is updated by the decision block
@@ -63,10 +77,18 @@ struct DevState {
                           // limit (the sweep is invalid; the solve stops with an error)
     long long t_sweep;    // t of the sweep in flight (written by the excess kernel, read by
                           // the gradient-step kernels while the decision block advances t)
+    // residual plateau (FP32 phase of the tail mode): r = max(cap_rel, cons_rel)
+    long long plat_window;  // sweeps per window (0: off)
+    long long plat_t0;      // t at which the current window began
+    double plat_cur;        // smallest r in the current window
+    double plat_prev;       // smallest r in the previous window (+inf before the first)
 };
+constexpr long long kPlateauWindow = 1024;  // sweeps per window of the plateau rule
+constexpr double kPlateauGain = 1e-4;       // a window must lower the best residual by this fraction
+constexpr double kPlateauCeiling = 1e3;     // ... once it is below this multiple of resid_tol
 
 // Grid barrier of the persistent sweep kernel (device memory, zeroed before
-// each launch).  `failed` is set when a wait ran out of its iteration limit;
+// each launch).  `failed` is set when a wait ran out of its time limit;
 // every block then leaves the kernel and the host reports the error.
 struct GridBarrier {
     unsigned int count;   // blocks arrived at the current barrier
@@ -120,6 +142,9 @@ struct SweepArgs {
     long long wait_cycles;    // bulk-copy form: time limit of a barrier wait, in SM clock cycles
     int hold_end;             // bulk-copy form, tests only: the producer never posts its end
                               // marker, so the consumers' last wait runs out (no copy in flight)
+    long long barrier_ns;     // persistent engine: time limit of a grid-barrier wait, in ns
+    int hold_barrier;         // persistent engine, tests only: block 0 leaves without arriving
+                              // at its first grid barrier, so the other blocks' waits run out
     int64_t n_psi;      // number of edge partials
     int64_t pf_edges;   // edge QP: L2 prefetch of the rows of edge e + pf_edges while
                         // edge e is solved (about one wave of resident edges ahead; 0: off)
@@ -166,12 +191,27 @@ int edge_group_lanes(int cfg);           // lanes per edge of a lane-group varia
 template <typename T>
 int64_t edge_prefetch_distance(int cfg, int num_sms);  // edges solved by one wave of resident blocks
 bool edge_config_pipelined(int cfg);
+bool edge_config_staged(int cfg);       // the bulk-copy staged block forms
 int excess_grid(int32_t n, int Kp, int vec, int num_sms, int resident_blocks);
 // Persistent sweep kernel (sweep.cu): excess and edge QP of every sweep in one
 // cooperative launch, separated by grid barriers; runs up to `sweeps` sweeps
 // of Alg. 1 or until the stop rules fire.  Only the lane-group variants.
 template <typename T>
 int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms);  // 0: not available
+// Batched form, one thread-block cluster of csize blocks (1, 2, 4 or 8) per
+// instance: instances ids[0..count) of args run up to `sweeps` sweeps each
+// with the lane-group variant cfg (true for batch_block_config);
+// psi_prologue: first launch of a solve.
+template <typename T>
+cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
+                               int psi_prologue, cudaStream_t stream);
+bool batch_block_config(int cfg);
+int gd_preferred_config(int cfg);
+
+// Packs and widens m padded rows into dst[rows*K] (double), dst writable by the GPU.
+template <typename T>
+cudaError_t launch_widen_rows(const T* src, int64_t rows, int K, int Kp, double* dst, cudaStream_t stream);
+
 template <typename T>
 cudaError_t launch_persistent(const SweepArgs<T>& a, int cfg, int grid, int64_t sweeps, GridBarrier* bar,
                               int psi_prologue, cudaStream_t stream);
@@ -212,9 +252,18 @@ inline int64_t backward_mask_words(int Kp, int vec) { return (int64_t)((Kp / vec
 struct ResidOut {
     double z, cap_abs, cap_rel, cons_abs, cons_rel, f_min, margin, margin_scale;
 };
+// Instance data of the residual pass, all in FP64 except the FP32 copy of
+// 1/d used to screen candidates for the largest relative imbalance.
+struct ResidIn {
+    const double* u_d;        // [m] capacities
+    const double* dem_d;      // [Kp] demands (0 in the padding)
+    const double* inv_deg_d;  // [n] 1/delta_i (0 for isolated vertices)
+    const float* inv_dem_f;   // [Kp] 1/d_k rounded to FP32 (0 in the padding)
+};
+
 template <typename T>
-cudaError_t launch_residuals(const SweepArgs<T>& a, const double* u_d, const double* dem_d, double* h64,
-                             double* part, int32_t grid_v, int32_t grid_e, ResidOut* out, cudaStream_t stream);
+cudaError_t launch_residuals(const SweepArgs<T>& a, const ResidIn& r, double* h64, double* part, int32_t grid_v,
+                             int32_t grid_e, ResidOut* out, cudaStream_t stream);
 int resid_part_count(int32_t grid_v, int32_t grid_e);
 
 // Message returned by pdr_last_error(NULL) on the calling thread (api.cu).

@@ -3,7 +3,8 @@
 // precision of the flows.
 //
 //  vertex pass  Delta_ik (eq. (3), (3h)) and h_ik = Delta_ik / delta_i
-//               (eq. (2)) in FP64; per block: sum delta h^2, max |Delta|,
+//               (eq. (2)) in FP64 (FP32 flows summed error-free in FP32
+//               pairs first); per block: sum delta h^2, max |Delta|,
 //               max |Delta| / d_k.
 //  edge pass    sum_k f_e,k, psi_e (eq. (41)), the certificate length
 //               l_e = max(0, max_k (h_ik - h_jk)) and min_k f_e,k; per block:
@@ -71,28 +72,129 @@ __device__ void block_reduce(double* v, const int* op, double (*smem)[32])
     __syncthreads();
 }
 
+// Exact error of one addition (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Running sum of FP32 terms kept as an unevaluated pair (hi + lo): every
+// addition is error-free (TwoSum) and only the small error terms are added
+// in FP32, so hi + lo is the exact sum to about 2^-45 of the largest partial
+// sum, well inside FP64 rounding of the quantities formed from it.
+struct PairSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float e;
+        two_sum(hi, x, hi, e);
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Four consecutive elements of a padded row as doubles.
+__device__ __forceinline__ void load4(const double* p, double* x)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+}
+
+// The largest |Delta_ik| and |Delta_ik| / d_k are found in FP64 without an
+// FP64 division per element: an element goes through the exact FP64 path
+// only when its FP32 estimate (relative error below 2^-21) comes within
+// 2^-18 of the FP32 estimate of the best exact value so far, so no element
+// that could be the maximum is skipped.
+constexpr float kSlack = 0.99999619f;  // 1 - 2^-18
+
+// Vertex pass: one warp per vertex, each lane four commodities at a time.
+// Delta_ik = sum over in-edges (ascending id) - sum over out-edges
+// (ascending) + the source/sink term (eq. (3), (3h)); h = Delta / delta_i
+// (eq. (2)).  FP32 flows are summed error-free (PairSum), FP64 flows in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) resid_vertex_kernel(SweepArgs<T> a, const double* __restrict__ dem_d,
-                                                           double* __restrict__ h64, double* __restrict__ part)
+__global__ void __launch_bounds__(256) resid_vertex_kernel(SweepArgs<T> a, ResidIn r, double* __restrict__ h64,
+                                                           double* __restrict__ part)
 {
     __shared__ double smem[5][32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nvec = a.Kp / 4;
     double zsum = 0.0, cabs = 0.0, crel = 0.0;
-    const int64_t total = (int64_t)a.n * a.K;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)(idx / a.K);
-        const int32_t k = (int32_t)(idx - (int64_t)i * a.K);
-        double acc = 0.0;
-        for (int64_t q = a.in_ptr[i]; q < a.in_ptr[i + 1]; ++q) acc += (double)a.f[(int64_t)a.in_eid[q] * a.Kp + k];
-        for (int64_t e = a.row_ptr[i]; e < a.row_ptr[i + 1]; ++e) acc -= (double)a.f[e * a.Kp + k];
-        if (a.s[k] == i) acc += dem_d[k];
-        else if (a.t[k] == i) acc -= dem_d[k];
-        const int dg = a.deg[i];
-        const double h = dg > 0 ? acc / (double)dg : 0.0;
-        h64[(int64_t)i * a.Kp + k] = h;
-        zsum += (double)dg * h * h;
-        cabs = fmax(cabs, fabs(acc));
-        crel = fmax(crel, fabs(acc) / dem_d[k]);
+    float cabs32 = 0.f, crel32 = 0.f;  // FP32 estimates of the elements behind cabs, crel
+    for (int64_t i = warp; i < a.n; i += nwarps) {
+        const int64_t i0 = a.in_ptr[i], i1 = a.in_ptr[i + 1], o0 = a.row_ptr[i], o1 = a.row_ptr[i + 1];
+        const double invdeg = r.inv_deg_d[i];
+        for (int v = lane; v < nvec; v += 32) {
+            const int k0 = 4 * v;
+            double D[4];
+            float D32[4];
+            if constexpr (sizeof(T) == 4) {
+                PairSum acc[4];
+                for (int64_t q = i0; q < i1; ++q) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(a.f + (int64_t)a.in_eid[q] * a.Kp + k0));
+                    acc[0].add(x.x), acc[1].add(x.y), acc[2].add(x.z), acc[3].add(x.w);
+                }
+                for (int64_t e = o0; e < o1; ++e) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(a.f + e * a.Kp + k0));
+                    acc[0].add(-x.x), acc[1].add(-x.y), acc[2].add(-x.z), acc[3].add(-x.w);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    D[j] = acc[j].value();
+                    D32[j] = __fadd_rn(acc[j].hi, acc[j].lo);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) D[j] = 0.0;
+                double x[4];
+                for (int64_t q = i0; q < i1; ++q) {
+                    load4(reinterpret_cast<const double*>(a.f) + (int64_t)a.in_eid[q] * a.Kp + k0, x);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) D[j] += x[j];
+                }
+                for (int64_t e = o0; e < o1; ++e) {
+                    load4(reinterpret_cast<const double*>(a.f) + e * a.Kp + k0, x);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) D[j] -= x[j];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) D32[j] = (float)D[j];
+            }
+            const int4 sv = __ldg(reinterpret_cast<const int4*>(a.s + k0));
+            const int4 tv = __ldg(reinterpret_cast<const int4*>(a.t + k0));
+            const int ss[4] = {sv.x, sv.y, sv.z, sv.w}, tt[4] = {tv.x, tv.y, tv.z, tv.w};
+            double h[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + j;
+                if (k >= a.K) D[j] = 0.0;  // the padding carries no commodity
+                if (ss[j] == (int)i || tt[j] == (int)i) {  // padding has s = t = -1
+                    D[j] += ss[j] == (int)i ? r.dem_d[k] : -r.dem_d[k];
+                    D32[j] = (float)D[j];
+                }
+                h[j] = D[j] * invdeg;
+                zsum = fma(D[j], h[j], zsum);  // delta_i h^2 = Delta h
+                if (D[j] != 0.0) {
+                    const float ad = fabsf(D32[j]);
+                    if (ad >= cabs32 * kSlack) {
+                        cabs = fmax(cabs, fabs(D[j]));
+                        cabs32 = fmaxf(cabs32, ad);
+                    }
+                    const float rel = ad * r.inv_dem_f[k];
+                    if (rel >= crel32 * kSlack) {
+                        crel = fmax(crel, fabs(D[j]) / r.dem_d[k]);
+                        crel32 = fmaxf(crel32, rel);
+                    }
+                }
+            }
+            double2* hp = reinterpret_cast<double2*>(h64 + i * a.Kp + k0);
+            hp[0] = make_double2(h[0], h[1]);
+            hp[1] = make_double2(h[2], h[3]);
+        }
     }
     double v[3] = {zsum, cabs, crel};
     const int op[3] = {0, 1, 1};
@@ -101,37 +203,75 @@ __global__ void __launch_bounds__(256) resid_vertex_kernel(SweepArgs<T> a, const
         for (int q = 0; q < kVParts; ++q) part[(int64_t)blockIdx.x * kVParts + q] = v[q];
 }
 
-// One warp per edge.
+// Edge pass: one warp per edge, each lane four commodities at a time:
+// sum_k f_e,k (error-free pairs for FP32 flows), psi_e (eq. (41)), min_k f_e,k
+// and the certificate length l_e = max(0, max_k (h_ik - h_jk)) in FP64 (only
+// where u_e > 0: an edge without capacity adds nothing to sum_e u_e l_e).
 template <typename T>
-__global__ void __launch_bounds__(256) resid_edge_kernel(SweepArgs<T> a, const double* __restrict__ u_d,
-                                                         const double* __restrict__ h64, double* __restrict__ part)
+__global__ void __launch_bounds__(256) resid_edge_kernel(SweepArgs<T> a, ResidIn r, const double* __restrict__ h64,
+                                                         double* __restrict__ part)
 {
     __shared__ double smem[5][32];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nvec = a.Kp / 4;
     double psi2 = 0.0, capa = 0.0, capr = 0.0, cost = 0.0, fmn = INFINITY;
     for (int64_t e = warp; e < a.m; e += nwarps) {
-        const T* fr = a.f + e * a.Kp;
+        const double ue = r.u_d[e];
+        const bool need_l = ue > 0.0;
         const double* hi = h64 + (int64_t)a.src[e] * a.Kp;
         const double* hj = h64 + (int64_t)a.col[e] * a.Kp;
         double tot = 0.0, l = 0.0, mn = INFINITY;
-        for (int k = lane; k < a.K; k += 32) {
-            const double x = (double)fr[k];
-            tot += x;
-            mn = fmin(mn, x);
-            l = fmax(l, hi[k] - hj[k]);
+        if constexpr (sizeof(T) == 4) {
+            PairSum acc;
+            float mn32 = INFINITY;
+            for (int v = lane; v < nvec; v += 32) {
+                const int k0 = 4 * v;
+                const float4 x = __ldg(reinterpret_cast<const float4*>(a.f + e * a.Kp + k0));
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+                const int nk = a.K - k0 < 4 ? a.K - k0 : 4;  // the padding carries no commodity
+                for (int j = 0; j < nk; ++j) {
+                    acc.add(xs[j]);
+                    mn32 = fminf(mn32, xs[j]);
+                }
+                if (need_l) {
+                    double p[4], q[4];
+                    load4(hi + k0, p);
+                    load4(hj + k0, q);
+                    for (int j = 0; j < nk; ++j) l = fmax(l, p[j] - q[j]);
+                }
+            }
+            tot = (double)acc.hi + (double)acc.lo;
+            mn = (double)mn32;
+        } else {
+            for (int v = lane; v < nvec; v += 32) {
+                const int k0 = 4 * v;
+                double x[4];
+                load4(reinterpret_cast<const double*>(a.f) + e * a.Kp + k0, x);
+                const int nk = a.K - k0 < 4 ? a.K - k0 : 4;  // the padding carries no commodity
+                for (int j = 0; j < nk; ++j) {
+                    tot += x[j];
+                    mn = fmin(mn, x[j]);
+                }
+                if (need_l) {
+                    double p[4], q[4];
+                    load4(hi + k0, p);
+                    load4(hj + k0, q);
+                    for (int j = 0; j < nk; ++j) l = fmax(l, p[j] - q[j]);
+                }
+            }
         }
         tot = wsum(tot);
         l = wmax(l);
         mn = wmin(mn);
         if (lane == 0) {
-            const double over = tot - u_d[e];
+            const double over = tot - ue;
             const double psi = over > 0.0 ? over : 0.0;
             psi2 += psi * psi;
             capa = fmax(capa, psi);
             capr = fmax(capr, psi * a.inv_scale[e]);
-            cost += u_d[e] * l;
+            cost += ue * l;
             fmn = fmin(fmn, mn);
         }
     }
@@ -193,18 +333,18 @@ __global__ void __launch_bounds__(256) resid_final_kernel(SweepArgs<T> a, const 
 int resid_part_count(int32_t grid_v, int32_t grid_e) { return grid_v * kVParts + grid_e * kEParts; }
 
 template <typename T>
-cudaError_t launch_residuals(const SweepArgs<T>& a, const double* u_d, const double* dem_d, double* h64,
-                             double* part, int32_t grid_v, int32_t grid_e, ResidOut* out, cudaStream_t stream)
+cudaError_t launch_residuals(const SweepArgs<T>& a, const ResidIn& r, double* h64, double* part, int32_t grid_v,
+                             int32_t grid_e, ResidOut* out, cudaStream_t stream)
 {
-    resid_vertex_kernel<T><<<grid_v, 256, 0, stream>>>(a, dem_d, h64, part);
-    resid_edge_kernel<T><<<grid_e, 256, 0, stream>>>(a, u_d, h64, part + (int64_t)grid_v * kVParts);
-    resid_final_kernel<T><<<1, 256, 0, stream>>>(a, dem_d, h64, part, grid_v, grid_e, out);
+    resid_vertex_kernel<T><<<grid_v, 256, 0, stream>>>(a, r, h64, part);
+    resid_edge_kernel<T><<<grid_e, 256, 0, stream>>>(a, r, h64, part + (int64_t)grid_v * kVParts);
+    resid_final_kernel<T><<<1, 256, 0, stream>>>(a, r.dem_d, h64, part, grid_v, grid_e, out);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_residuals<float>(const SweepArgs<float>&, const double*, const double*, double*,
-                                             double*, int32_t, int32_t, ResidOut*, cudaStream_t);
-template cudaError_t launch_residuals<double>(const SweepArgs<double>&, const double*, const double*, double*,
-                                              double*, int32_t, int32_t, ResidOut*, cudaStream_t);
+template cudaError_t launch_residuals<float>(const SweepArgs<float>&, const ResidIn&, double*, double*, int32_t,
+                                             int32_t, ResidOut*, cudaStream_t);
+template cudaError_t launch_residuals<double>(const SweepArgs<double>&, const ResidIn&, double*, double*, int32_t,
+                                              int32_t, ResidOut*, cudaStream_t);
 
 }  // namespace pdr

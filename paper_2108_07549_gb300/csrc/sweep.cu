@@ -566,7 +566,11 @@ __device__ __forceinline__ T qp_root_group(const T (&c)[V][N], T ue, T w0, bool 
         }
         if (it > Kp + 2) break;  // unreachable: nA drops every round
     }
-    return theta;
+    // A Case 2 root below 0 can only come from rounding in sums that put
+    // s = sum max(0, c) within rounding of u: that edge is in Case 1 (root 0).
+    // Without the clamp, f' = max(0, c - theta) would lift every c <= 0 --
+    // the zero padding included -- to -theta.
+    return theta > T(0) ? theta : T(0);
 }
 
 // Warm start of the next sweep's root search from this sweep's root theta
@@ -717,6 +721,7 @@ __global__ void __launch_bounds__(kThreads) edge_group_kernel(SweepArgs<T> a)
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
     }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
     edge_group_body<T, G, V, false>(a, blockIdx.x, gridDim.x - 1);
 }
 
@@ -760,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
     }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)(gridDim.x - 1) * blockDim.x) >> 5;
@@ -883,7 +889,7 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
 template <typename T, int B, int V>
-__global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2) : 1))) edge_block_kernel(SweepArgs<T> a)
+__global__ void __launch_bounds__(B, block_min_blocks(B, V)) edge_block_kernel(SweepArgs<T> a)
 {
     pdl_wait();  // the excess kernel has finished (no-op without PDL)
     using VT = typename VecOf<T>::type;
@@ -898,6 +904,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
         if (a.mode != MODE_PSI) reduce_and_finalize(a);
         return;
     }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
     const int vpr = a.Kp / N;
     const bool psi_only = (a.mode == MODE_PSI);
     const bool hint = a.l2_hints != 0;
@@ -966,6 +973,7 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
                 theta = (S - ue) / T(den + n);
                 done = mn > theta;
             }
+            if (theta < T(0)) theta = T(0);  // a root below 0 is rounding at s = u: Case 1 (as qp_root_group)
             if (threadIdx.x == 0) {
                 a.theta[a.m + e] = next_warm_start(theta, a.theta_in[e]);
                 a.theta[e] = theta;
@@ -1023,8 +1031,6 @@ __global__ void __launch_bounds__(B, (B <= 256 ? 6 : (B <= 512 ? (V <= 5 ? 3 : 2
 // decision meanwhile (as the decision block of the standalone edge kernel),
 // and a second barrier after which every block reads the same stop flag.
 
-constexpr long long kBarrierSpins = 1ll << 21;  // ~1-2 s of polling, then give up
-
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
 {
     unsigned int v;
@@ -1037,12 +1043,24 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Sense-by-generation barrier over the whole (co-resident) grid.  Returns
-// false in every thread of a block whose wait timed out or saw another
-// block's timeout.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar)
+// Nanoseconds of the GPU's global timer (the same clock in every SM).
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-by-generation barrier over the whole (co-resident) grid.  A wait
+// gives up after limit_ns nanoseconds of the global timer (elapsed time, not
+// a poll count) and raises bar->failed, which ends every other block's wait
+// too.  Returns false in every thread of a block whose wait timed out or saw
+// another block's timeout.  withhold (test hook, uniform per block): the
+// block leaves without arriving, so the others' waits run out.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, long long limit_ns, bool withhold)
 {
     __shared__ int ok;
+    if (withhold) return false;
     __syncthreads();
     if (threadIdx.x == 0) {
         // the generation is read before arriving, so the last arrival's
@@ -1056,9 +1074,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar)
             __threadfence();
             st_release_u32(&bar->gen, gen + 1u);
         } else {
-            long long spins = 0;
+            const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(&bar->gen) == gen) {
-                if (ld_acquire_u32(&bar->failed) != 0u || ++spins > kBarrierSpins) {
+                if (ld_acquire_u32(&bar->failed) != 0u || (long long)(global_ns() - t0) > limit_ns) {
                     atomicExch(&bar->failed, 1u);
                     good = 0;
                     break;
@@ -1079,13 +1097,14 @@ __global__ void __launch_bounds__(kThreads, (V <= 4 ? 4 : 3))
 {
     volatile DevState* vst = a.st;
     const int nb = gridDim.x - 1;  // edge blocks; block nb decides
+    const bool hold = a.hold_barrier != 0 && blockIdx.x == 0;  // test hook: block 0 never arrives
     // congestion partials of the current flows in this grid's layout (a
     // later launch of the same solve finds them written by its predecessor)
     if (psi_prologue) {
         SweepArgs<T> b = a;
         b.mode = MODE_PSI;
         if ((int)blockIdx.x < nb) edge_group_body<T, G, V, true>(b, blockIdx.x, nb);
-        if (!grid_sync(bar)) return;
+        if (!grid_sync(bar, a.barrier_ns, hold)) return;
     }
     for (int64_t q = 0; q < sweeps; ++q) {
         if (vst->stop) break;  // the same value in every block (read after a barrier)
@@ -1097,10 +1116,241 @@ __global__ void __launch_bounds__(kThreads, (V <= 4 ? 4 : 3))
             b.theta = const_cast<T*>(a.theta_in);
         }
         excess_body<T>(b, blockIdx.x, gridDim.x);
-        if (!grid_sync(bar)) return;
+        if (!grid_sync(bar, a.barrier_ns, hold)) return;
         if ((int)blockIdx.x == nb) reduce_and_finalize(b);
         else edge_group_body<T, G, V, true>(b, blockIdx.x, nb);
-        if (!grid_sync(bar)) return;
+        if (!grid_sync(bar, a.barrier_ns, hold)) return;
+    }
+}
+
+// ------------------------------------------------------------------ edge QP, staged block form
+//
+// Persistent form of edge_block_kernel for long rows: one block per SM walks
+// a stride of edges and keeps the next edge's three rows (f, h_i, h_j) in
+// flight as cp.async.bulk copies into shared memory while it solves the
+// current edge from registers.  Thread 0 issues the next edge's copies as
+// soon as every thread has moved the current rows into registers, so each
+// SM always has one edge's rows on the way from memory, through the root
+// search and the stores of the current edge, with no L2 prefetch
+// guesswork.  The flow rows stream with an L2 evict-first hint.  Per element
+// the arithmetic and its order are edge_block_kernel's, so the flows are
+// bit-identical to it.  Each wait on the copies is limited (a.wait_cycles);
+// one that runs out records the fault, ends the solve, waits (limited) for
+// the copy in flight and leaves.
+template <typename T, int B, int V>
+__global__ void __launch_bounds__(B, 1) edge_staged_kernel(SweepArgs<T> a)
+{
+    pdl_wait();  // the excess kernel has finished (no-op without PDL)
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    using A = Acc<T>;
+    extern __shared__ __align__(128) unsigned char esm[];
+    __shared__ __align__(8) uint64_t full;
+    __shared__ T sa_buf[32];
+    __shared__ int sb_buf[32];
+    __shared__ T sm_buf[32];
+    volatile DevState* vst = a.st;
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
+    if (blockIdx.x == gridDim.x - 1) {  // the decision block
+        if (a.mode != MODE_PSI) reduce_and_finalize(a);
+        return;
+    }
+    if (final_evaluation(a)) return;  // the sweep cap stops this sweep: its output is not used
+    const int nb = gridDim.x - 1;
+    const int vpr = a.Kp / N;
+    const uint32_t row_bytes = (uint32_t)a.Kp * (uint32_t)sizeof(T);
+    const bool psi_only = (a.mode == MODE_PSI);
+    const VT* sf = reinterpret_cast<const VT*>(esm);
+    const VT* shi = sf + vpr;
+    const VT* shj = shi + vpr;
+    const uint64_t pol_first = l2_evict_first();
+    auto stage = [&](int64_t e) {  // thread 0: the rows of edge e into shared memory
+        mbar_arrive_expect_tx(&full, psi_only ? row_bytes : 3u * row_bytes);
+        bulk_g2s_hint(esm, a.f + e * a.Kp, row_bytes, &full, pol_first);
+        if (!psi_only) {
+            bulk_g2s(esm + row_bytes, a.h + (int64_t)a.src[e] * a.Kp, row_bytes, &full);
+            bulk_g2s(esm + 2 * (size_t)row_bytes, a.h + (int64_t)a.col[e] * a.Kp, row_bytes, &full);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&full, 1);
+        mbar_init_fence();
+        if ((int64_t)blockIdx.x < a.m) stage(blockIdx.x);
+    }
+    __syncthreads();
+    typename A::V zpsi = A::zero();
+    T capmax = T(0);
+    uint32_t phase = 0;
+    for (int64_t e = blockIdx.x; e < a.m; e += nb) {
+        const bool landed = mbar_wait(&full, phase, a.wait_cycles);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) {
+                a.st->fault = 1;
+                stop_from_kernel(a);
+            }
+            mbar_wait(&full, phase, a.wait_cycles);  // the copy in flight, then leave
+            return;
+        }
+        phase ^= 1u;
+        const T ue = a.u[e];
+        T c[V][N];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = threadIdx.x + q * B;
+            if (v < vpr) {
+                T fx[N];
+                unpack(sf[v], fx);
+                if (psi_only) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = fx[j];
+                } else {
+                    T ax[N], bx[N];
+                    unpack(shi[v], ax);
+                    unpack(shj[v], bx);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) c[q][j] = fma(T(0.5), ax[j] - bx[j], fx[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) c[q][j] = T(0);
+            }
+        }
+        __syncthreads();  // every row is in registers: the staging buffer is free
+        if (threadIdx.x == 0 && e + nb < a.m) stage(e + nb);
+        T* orow = a.f_out + e * a.Kp;
+        T psi;
+        if (!psi_only) {
+            const T w0 = a.theta_in[a.m + e];
+            const int den = a.ck ? 0 : 2;
+            T S, mn, theta = T(0);
+            int n, nA = 0;
+            bool done = false;
+            block_above<T, V, N>(c, w0, S, n, mn, sa_buf, sb_buf, sm_buf);
+            if (w0 <= T(0)) start_root(S, n, mn, ue, den, theta, nA, done);
+            else if (n > 0 && S - T(n) * w0 - ue - T(den) * w0 >= T(0)) {
+                theta = (S - ue) / T(den + n);
+                nA = n;
+                done = mn > theta;
+            } else {
+                block_above<T, V, N>(c, T(0), S, n, mn, sa_buf, sb_buf, sm_buf);
+                start_root(S, n, mn, ue, den, theta, nA, done);
+            }
+            for (int it = 0; !done && it <= a.Kp + 2; ++it) {  // block-uniform
+                block_above<T, V, N>(c, theta, S, n, mn, sa_buf, sb_buf, sm_buf);
+                if (n >= nA || n == 0) break;
+                nA = n;
+                theta = (S - ue) / T(den + n);
+                done = mn > theta;
+            }
+            if (theta < T(0)) theta = T(0);  // a root below 0 is rounding at s = u: Case 1
+            if (threadIdx.x == 0) {
+                a.theta[a.m + e] = next_warm_start(theta, a.theta_in[e]);
+                a.theta[e] = theta;
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int v = threadIdx.x + q * B;
+                T o[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const T x = c[q][j] - theta;
+                    o[j] = x > T(0) ? x : T(0);
+                }
+                if (v < vpr) st_hint(reinterpret_cast<VT*>(orow) + v, pack4(o), pol_first);
+            }
+            psi = T(den) * theta;  // sum f' - u at the root
+        } else {
+            T rs = T(0);
+            int dummy = 0;
+#pragma unroll
+            for (int q = 0; q < V; ++q)
+#pragma unroll
+                for (int j = 0; j < N; ++j) rs += c[q][j];
+            block_sum2(rs, dummy, sa_buf, sb_buf);
+            psi = rs - ue > T(0) ? rs - ue : T(0);
+        }
+        if (threadIdx.x == 0) {
+            zpsi = A::add(zpsi, psi * psi);
+            const T cp = psi * a.inv_scale_t[e];
+            capmax = cp > capmax ? cp : capmax;
+            if (a.psi_out) a.psi_out[e] = psi;
+        }
+    }
+    // one partial per block, held by thread 0
+    if (threadIdx.x == 0) {
+        reinterpret_cast<typename A::S*>(a.part_psi)[blockIdx.x] = A::store(zpsi);
+        a.part_cap[blockIdx.x] = capmax;
+    }
+}
+
+// ------------------------------------------------------------------ batched form: one cluster per instance
+//
+// For a batch of small instances one launch runs every instance's solve: the
+// csize consecutive blocks of a thread-block cluster own instance
+// ids[blockIdx.x / csize] and run Alg. 1 sweep after sweep -- the excess
+// pass, the objective and stop test, then (unless it stopped) the edge QPs --
+// separated only by cluster barriers (block barriers for csize = 1), until
+// its own stop rule fires or `sweeps` sweeps are done.  A finished instance's
+// blocks leave and free their SM slots, which is the per-instance
+// convergence mask.  Per element the arithmetic and its order are those of
+// the standalone kernels with the same lane-group variant, so the flows equal
+// theirs bit for bit; the objective's partials are grouped per block (z
+// agrees to rounding).  The flows start in the buffer args[i] names and every
+// applied sweep swaps the buffers.
+
+// All threads of the cluster; release/acquire at cluster scope orders the
+// global-memory writes of one phase before the reads of the next.
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T, int G, int V>
+__global__ void __launch_bounds__(kBatchThreads, 2)
+    batch_block_kernel(const SweepArgs<T>* __restrict__ args, const int* __restrict__ ids, int csize,
+                       int64_t sweeps, int psi_prologue)
+{
+    // the instance's arguments live in shared memory (not in every thread's
+    // registers); thread 0 of every block swaps its buffers between sweeps
+    __shared__ SweepArgs<T> sa;
+    __shared__ int stop;
+    const int rank = (int)(blockIdx.x % (unsigned)csize);
+    auto sync = [csize]() {
+        if (csize > 1) cluster_sync_all();
+        else __syncthreads();
+    };
+    if (threadIdx.x == 0) {
+        sa = args[ids[blockIdx.x / (unsigned)csize]];
+        stop = reinterpret_cast<volatile DevState*>(sa.st)->stop;
+        if (psi_prologue) sa.mode = MODE_PSI;
+    }
+    __syncthreads();
+    if (stop) return;  // the same value in every block of the cluster (no block of it has run yet)
+    if (psi_prologue) {  // congestion partials of the starting flows, in this kernel's layout
+        edge_group_body<T, G, V, true>(sa, rank, csize);
+        sync();
+        if (threadIdx.x == 0) sa.mode = MODE_SOLVE;
+        __syncthreads();
+    }
+    for (int64_t q = 0; q < sweeps; ++q) {
+        excess_body<T>(sa, rank, csize);
+        sync();
+        if (rank == 0) reduce_and_finalize(sa);
+        sync();
+        if (threadIdx.x == 0) stop = reinterpret_cast<volatile DevState*>(sa.st)->stop;
+        __syncthreads();
+        if (stop) return;  // f^(t) stays in sa.f
+        edge_group_body<T, G, V, true>(sa, rank, csize);
+        sync();
+        if (threadIdx.x == 0) {  // f^(t+1) becomes the current flows
+            T* f = sa.f;
+            sa.f = sa.f_out;
+            sa.f_out = f;
+            const T* th = sa.theta_in;
+            sa.theta_in = sa.theta;
+            sa.theta = const_cast<T*>(th);
+        }
+        __syncthreads();
     }
 }
 
@@ -1108,6 +1358,18 @@ template <typename T, int G, int V>
 cudaError_t persistent_occupancy(int* blocks)
 {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, persistent_kernel<T, G, V>, kThreads, 0);
+}
+
+// dst[r*K + k] = src[r*Kp + k] as double: the padded rows of a flow array
+// packed and widened into a caller's buffer that the GPU can write.
+template <typename T>
+__global__ void widen_rows_kernel(const T* __restrict__ src, int64_t rows, int K, int Kp, double* __restrict__ dst)
+{
+    const int64_t total = rows * (int64_t)K;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / K;
+        dst[q] = (double)src[r * Kp + (q - r * K)];
+    }
 }
 
 __global__ void convert_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t count)
@@ -1124,16 +1386,24 @@ struct EdgeCfg {
     int P;        // 1 = pipelined persistent warp form (Alg. 2 only)
 };
 constexpr EdgeCfg kCfg[] = {
-    // 0..13 ordered by capacity (elements per row); two 512-thread blocks fit
-    // on an SM, so the block forms keep two edges in flight per SM up to 16,384
-    {4, 0, 1, 0},   {8, 0, 1, 0},   {16, 0, 1, 0},  {32, 0, 1, 0},  {32, 0, 2, 0},
-    {32, 0, 4, 0},  {32, 0, 8, 0},  {0, 256, 2, 0}, {0, 512, 2, 0}, {0, 512, 3, 0},
-    {0, 512, 4, 0}, {0, 512, 5, 0}, {0, 512, 8, 0}, {0, 1024, 8, 0},
-    // 14..16: the pipelined forms of 3..5 (the gradient kernels of Alg. 3/4
+    // 0..15 ordered by capacity (elements per row); of equal capacities the
+    // first is the default (measured fastest for Alg. 2: 128 x 4 on
+    // digraph20k_k2000, 512 x 5 on grid100_k10000); the block forms keep
+    // 2-12 edges in flight per SM (block_min_blocks)
+    {4, 0, 1, 0},   {8, 0, 1, 0},   {16, 0, 1, 0},  {32, 0, 1, 0},   {32, 0, 2, 0},
+    {32, 0, 4, 0},  {32, 0, 8, 0},  {0, 128, 4, 0}, {0, 256, 2, 0},  {0, 512, 2, 0},
+    {0, 512, 3, 0}, {0, 512, 4, 0}, {0, 512, 5, 0}, {0, 256, 10, 0}, {0, 512, 8, 0},
+    {0, 1024, 8, 0},
+    // 16..18: the pipelined forms of 3..5 (the gradient kernels of Alg. 3/4
     // run the plain form of the same capacity); at 8 vectors per lane the
     // prefetched rows no longer fit in registers
     {32, 0, 1, 1},  {32, 0, 2, 1},  {32, 0, 4, 1},
+    // 19..20: the staged forms of 12 and 14 (bulk copies of the next edge's
+    // rows into shared memory: 3 rows of up to 40 / 64 KB)
+    {0, 512, 5, 2}, {0, 512, 8, 2},
 };
+constexpr int kFirstPipelined = 16;
+constexpr int kFirstStaged = 19;
 constexpr int kNumCfg = sizeof(kCfg) / sizeof(kCfg[0]);
 
 template <typename T>
@@ -1153,6 +1423,11 @@ int edge_config(int Kp)
     return -1;
 }
 
+// Alg. 3 / Alg. 4 take the 256 x 10 block form where Alg. 2 takes 512 x 5
+// (equal capacity; the gradient step ran faster with fewer threads per edge
+// on grid100_k10000: 0.57 against 0.51 of the HBM peak).
+int gd_preferred_config(int cfg) { return cfg == 12 ? 13 : cfg; }
+
 template <typename T, int V>
 int pipe_resident()
 {
@@ -1166,10 +1441,36 @@ int pipe_resident()
 }
 
 template <typename T>
+size_t staged_smem(int Kp)
+{
+    return 3 * (size_t)Kp * sizeof(T);
+}
+
+// The staged forms take their three rows in dynamic shared memory (above the
+// 48 KB default): allowed once, at create time, for the largest rows.
+template <typename T>
+void staged_setup(int cfg)
+{
+    const int cap = capacity<T>(cfg);
+    const int bytes = (int)staged_smem<T>(cap);
+    if (cfg == kFirstStaged)
+        cudaFuncSetAttribute(edge_staged_kernel<T, 512, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    else
+        cudaFuncSetAttribute(edge_staged_kernel<T, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaGetLastError();
+}
+
+template <typename T>
 int edge_grid(int cfg, int64_t m, int num_sms)
 {
     const EdgeCfg& c = kCfg[cfg];
     int64_t want, cap;
+    if (c.P == 2) {
+        // one block per SM, each walking a stride of edges
+        staged_setup<T>(cfg);
+        const int64_t g = m < num_sms ? m : num_sms;
+        return (int)(g < 1 ? 1 : g);
+    }
     if (c.P) {
         // one wave of resident warps, each walking a stride of edges
         const int per_sm = c.V == 1 ? pipe_resident<T, 1>() : c.V == 2 ? pipe_resident<T, 2>() : pipe_resident<T, 4>();
@@ -1317,16 +1618,20 @@ cudaError_t launch_edge(const SweepArgs<T>& a, int cfg, cudaStream_t stream, boo
     case 4: return launch_one<T>(edge_group_kernel<T, 32, 2>, g, kThreads, stream, pdl, a);
     case 5: return launch_one<T>(edge_group_kernel<T, 32, 4>, g, kThreads, stream, pdl, a);
     case 6: return launch_one<T>(edge_group_kernel<T, 32, 8>, g, kThreads, stream, pdl, a);
-    case 7: return launch_one<T>(edge_block_kernel<T, 256, 2>, g, 256, stream, pdl, a);
-    case 8: return launch_one<T>(edge_block_kernel<T, 512, 2>, g, 512, stream, pdl, a);
-    case 9: return launch_one<T>(edge_block_kernel<T, 512, 3>, g, 512, stream, pdl, a);
-    case 10: return launch_one<T>(edge_block_kernel<T, 512, 4>, g, 512, stream, pdl, a);
-    case 11: return launch_one<T>(edge_block_kernel<T, 512, 5>, g, 512, stream, pdl, a);
-    case 12: return launch_one<T>(edge_block_kernel<T, 512, 8>, g, 512, stream, pdl, a);
-    case 13: return launch_one<T>(edge_block_kernel<T, 1024, 8>, g, 1024, stream, pdl, a);
-    case 14: return launch_one<T>(edge_pipe_kernel<T, 1>, g, kThreads, stream, pdl, a);
-    case 15: return launch_one<T>(edge_pipe_kernel<T, 2>, g, kThreads, stream, pdl, a);
-    case 16: return launch_one<T>(edge_pipe_kernel<T, 4>, g, kThreads, stream, pdl, a);
+    case 7: return launch_one<T>(edge_block_kernel<T, 128, 4>, g, 128, stream, pdl, a);
+    case 8: return launch_one<T>(edge_block_kernel<T, 256, 2>, g, 256, stream, pdl, a);
+    case 9: return launch_one<T>(edge_block_kernel<T, 512, 2>, g, 512, stream, pdl, a);
+    case 10: return launch_one<T>(edge_block_kernel<T, 512, 3>, g, 512, stream, pdl, a);
+    case 11: return launch_one<T>(edge_block_kernel<T, 512, 4>, g, 512, stream, pdl, a);
+    case 12: return launch_one<T>(edge_block_kernel<T, 512, 5>, g, 512, stream, pdl, a);
+    case 13: return launch_one<T>(edge_block_kernel<T, 256, 10>, g, 256, stream, pdl, a);
+    case 14: return launch_one<T>(edge_block_kernel<T, 512, 8>, g, 512, stream, pdl, a);
+    case 15: return launch_one<T>(edge_block_kernel<T, 1024, 8>, g, 1024, stream, pdl, a);
+    case 16: return launch_one<T>(edge_pipe_kernel<T, 1>, g, kThreads, stream, pdl, a);
+    case 17: return launch_one<T>(edge_pipe_kernel<T, 2>, g, kThreads, stream, pdl, a);
+    case 18: return launch_one<T>(edge_pipe_kernel<T, 4>, g, kThreads, stream, pdl, a);
+    case 19: return launch_one<T>(edge_staged_kernel<T, 512, 5>, g, 512, stream, pdl, a, staged_smem<T>(a.Kp));
+    case 20: return launch_one<T>(edge_staged_kernel<T, 512, 8>, g, 512, stream, pdl, a, staged_smem<T>(a.Kp));
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1362,6 +1667,66 @@ int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms)
     if (g > cap) g = cap;
     return g < 2 ? 2 : (int)g;
 }
+
+template <typename T, int G, int V>
+cudaError_t launch_batch_block_gv(const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
+                                  int psi_prologue, cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(count * csize));
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)csize;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = csize > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, batch_block_kernel<T, G, V>, args, ids, csize, sweeps, psi_prologue);
+}
+
+template <typename T>
+cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
+                               int psi_prologue, cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    if (csize < 1 || csize > 8 || (csize & (csize - 1))) return cudaErrorInvalidValue;
+    switch (edge_plain_config(cfg)) {
+    case 0: return launch_batch_block_gv<T, 4, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 1: return launch_batch_block_gv<T, 8, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 2: return launch_batch_block_gv<T, 16, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 3: return launch_batch_block_gv<T, 32, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 4: return launch_batch_block_gv<T, 32, 2>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 5: return launch_batch_block_gv<T, 32, 4>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_batch_block<float>(int, const SweepArgs<float>*, const int*, int, int, int64_t, int,
+                                               cudaStream_t);
+template cudaError_t launch_batch_block<double>(int, const SweepArgs<double>*, const int*, int, int, int64_t, int,
+                                                cudaStream_t);
+
+bool batch_block_config(int cfg)
+{
+    const int c = edge_plain_config(cfg);
+    return c >= 0 && c < kNumCfg && kCfg[c].G > 0;
+}
+
+template <typename T>
+cudaError_t launch_widen_rows(const T* src, int64_t rows, int K, int Kp, double* dst, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (rows * (int64_t)K + 255) / 256;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+    const int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+    widen_rows_kernel<T><<<grid, 256, 0, stream>>>(src, rows, K, Kp, dst);
+    return cudaGetLastError();
+}
+template cudaError_t launch_widen_rows<float>(const float*, int64_t, int, int, double*, cudaStream_t);
+template cudaError_t launch_widen_rows<double>(const double*, int64_t, int, int, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_persistent(const SweepArgs<T>& a, int cfg, int grid, int64_t sweeps, GridBarrier* bar,
@@ -1405,13 +1770,15 @@ int64_t edge_prefetch_distance(int cfg, int num_sms)
     case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 2>, kThreads, 0); break;
     case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 4>, kThreads, 0); break;
     case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_group_kernel<T, 32, 8>, kThreads, 0); break;
-    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 256, 2>, 256, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 2>, 512, 0); break;
-    case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 3>, 512, 0); break;
-    case 10: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 4>, 512, 0); break;
-    case 11: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 5>, 512, 0); break;
-    case 12: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 8>, 512, 0); break;
-    case 13: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 1024, 8>, 1024, 0); break;
+    case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 128, 4>, 128, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 256, 2>, 256, 0); break;
+    case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 2>, 512, 0); break;
+    case 10: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 3>, 512, 0); break;
+    case 11: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 4>, 512, 0); break;
+    case 12: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 5>, 512, 0); break;
+    case 13: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 256, 10>, 256, 0); break;
+    case 14: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 512, 8>, 512, 0); break;
+    case 15: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edge_block_kernel<T, 1024, 8>, 1024, 0); break;
     default: return 0;
     }
     if (e != cudaSuccess || per_sm < 1) {
@@ -1431,9 +1798,15 @@ int edge_group_lanes(int cfg)
     return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].G) ? kCfg[cfg].G : 32;
 }
 
-int edge_plain_config(int cfg) { return (cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P) ? 3 + (cfg - 14) : cfg; }
+int edge_plain_config(int cfg)
+{
+    if (cfg < 0 || cfg >= kNumCfg || !kCfg[cfg].P) return cfg;
+    if (kCfg[cfg].P == 1) return 3 + (cfg - kFirstPipelined);
+    return cfg == kFirstStaged ? 12 : 14;  // the block form of the same shape
+}
 
-bool edge_config_pipelined(int cfg) { return cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P; }
+bool edge_config_pipelined(int cfg) { return cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P == 1; }
+bool edge_config_staged(int cfg) { return cfg >= 0 && cfg < kNumCfg && kCfg[cfg].P == 2; }
 
 cudaError_t launch_convert_f32_to_f64(const float* a, double* b, int64_t count, cudaStream_t stream)
 {

@@ -148,6 +148,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// The same copy with an L2 cache-policy hint (createpolicy) for the source.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
 // Sum over the G lanes of an aligned lane group (xor offsets below G stay
 // inside the group).  Every lane of the warp must call it.  IEEE addition is
 // commutative, so every lane of the group ends with the same value.
@@ -188,6 +198,33 @@ __device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
     const int nw = blockDim.x >> 5;
     T ta = 0;
     int tb = 0;
+    for (int q = 0; q < nw; ++q) {  // same order in every thread
+        ta += sa[q];
+        tb += sb[q];
+    }
+    a = ta;
+    b = tb;
+    __syncthreads();
+}
+
+// Block-wide sums of two values, broadcast to every thread (one pair of
+// barriers for both).
+template <typename T>
+__device__ __forceinline__ void block_sum_pair(T& a, T& b, T* sa, T* sb)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    T ta = 0, tb = 0;
     for (int q = 0; q < nw; ++q) {  // same order in every thread
         ta += sa[q];
         tb += sb[q];
@@ -303,6 +340,25 @@ __device__ __forceinline__ bool sweep_stopped(const SweepArgs<T>& a)
     return stopped != 0;
 }
 
+// True in an edge kernel's update blocks during a solve's evaluation at
+// t = max_sweeps: that sweep stops by the sweep cap whatever its objective,
+// so its new flows would be discarded and the updates are skipped.  The
+// congestion partials of the returned flows f^(t), written by the previous
+// sweep's edge kernel, then stay in place.  t_sweep is the t of the sweep in
+// flight (written by the excess kernel before this launch may start), so the
+// decision block advancing t in the same launch does not affect the test.
+template <typename T>
+__device__ __forceinline__ bool final_evaluation(const SweepArgs<T>& a)
+{
+    __shared__ int fin;
+    if (threadIdx.x == 0) {
+        const volatile DevState* v = a.st;
+        fin = a.mode == MODE_SOLVE && v->t_sweep >= v->max_sweeps;
+    }
+    __syncthreads();
+    return fin != 0;
+}
+
 // Ends this instance's solve from a kernel other than the decision block
 // (a wait that ran out), exactly once.  It raises the stop flag and, in a
 // graph, ends the while loop.  A batch's loop ends with its last running
@@ -352,6 +408,25 @@ __device__ void finalize(const SweepArgs<T>& a, double zsum, double cons, double
             // so a rise means rounding now dominates the progress
             stop = 1;
             reason = STOP_STALL;
+        } else if (st->plat_window > 0) {
+            // residual plateau: the best r = max(cap_rel, cons_rel) of a window of
+            // sweeps improves on the previous window's best by less than
+            // kPlateauGain -- the FP32 rounding floor, not a slow descent (which
+            // still improves every window)
+            const double r = fmax(cap, cons);
+            if (r < st->plat_cur) st->plat_cur = r;
+            if (st->t - st->plat_t0 + 1 >= st->plat_window) {
+                // only near the target, where FP32 rounding can be the limit: a
+                // stall far above it is the method's own slow phase
+                const double ceiling = kPlateauCeiling * (st->resid_tol > 0.0 ? st->resid_tol : 1e-6);
+                if (st->plat_cur <= ceiling && st->plat_cur > (1.0 - kPlateauGain) * st->plat_prev) {
+                    stop = 1;
+                    reason = STOP_PLATEAU;
+                }
+                st->plat_prev = st->plat_cur;
+                st->plat_cur = INFINITY;
+                st->plat_t0 = st->t + 1;
+            }
         }
     }
     if (stop) {

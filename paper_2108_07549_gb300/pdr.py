@@ -26,7 +26,8 @@ ALGO_ESO, ALGO_AGD, ALGO_GDM, ALGO_CK = 0, 1, 2, 3
 VERDICT_UNKNOWN, VERDICT_FEASIBLE, VERDICT_INFEASIBLE = 0, 1, 2
 (OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_NOT_SOLVED, ERR_UNSUPPORTED,
  ERR_TIMEOUT) = range(8)  # pdr_status
-STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall"}
+STOP_NAMES = {0: "max_sweeps", 1: "objective", 2: "residual", 3: "relative", 4: "numeric", 5: "stall",
+              6: "plateau"}
 VERDICT_NAMES = {0: "unknown", 1: "feasible", 2: "infeasible"}
 
 #: every entry point declared in include/pdr.h
@@ -38,7 +39,7 @@ EXPORTS = (
     "pdr_batch_create", "pdr_batch_solve", "pdr_batch_reset", "pdr_batch_context", "pdr_batch_tuning",
     "pdr_batch_destroy", "pdr_set_data", "pdr_backward", "pdr_num_edge_variants", "pdr_edge_variant_capacity",
     "pdr_state_size", "pdr_get_state", "pdr_set_state", "pdr_debug_wait", "pdr_time_sweeps",
-    "pdr_debug_fail_alloc",
+    "pdr_debug_fail_alloc", "pdr_debug_barrier",
 )
 
 
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "pdr_get_state": ([vp, vp, i64], i32),
         "pdr_set_state": ([vp, vp, i64], i32),
         "pdr_debug_wait": ([vp, i64, i32], i32),
+        "pdr_debug_barrier": ([vp, i64, i32], i32),
         "pdr_time_sweeps": ([vp, i64, P(dbl), P(dbl)], i32),
         "pdr_debug_fail_alloc": ([i64], i32),
         "pdr_heights": ([vp, vp], i32),
@@ -169,13 +171,14 @@ def _current_stream():
 
 
 def edge_variants(precision: int = 0) -> list:
-    """The edge-kernel variant table: (index, row capacity in `precision`, pipelined) per entry."""
+    """The edge-kernel variant table: (index, row capacity in `precision`, form) per entry; form is 0 for
+    the plain forms, 1 for the pipelined warp forms, 2 for the staged block forms."""
     lib = load()
     out = []
     for v in range(lib.pdr_num_edge_variants()):
         pipe = C.c_int32(0)
         cap = lib.pdr_edge_variant_capacity(v, precision, C.byref(pipe))
-        out.append((v, cap, bool(pipe.value)))
+        out.append((v, cap, int(pipe.value)))
     return out
 
 
@@ -310,6 +313,11 @@ class Solver:
         """Test hook (pdr_debug_wait): the device wait limit and the end-marker hold."""
         self._check(self._lib.pdr_debug_wait(self._h, int(cycles), int(bool(hold_end))))
 
+    def debug_barrier(self, limit_ns: int = 2_000_000_000, withhold: bool = False):
+        """pdr_debug_barrier (test hook): time limit of the persistent engine's grid
+        barrier, and whether block 0 withholds its arrival."""
+        self._check(self._lib.pdr_debug_barrier(self._h, int(limit_ns), int(bool(withhold))))
+
     def flow_rows(self, edges, velocities: bool = False) -> np.ndarray:
         """Rows f[e, :] (or the Alg. 4 velocities v[e, :]) for the given edge ids ([len(edges), K])."""
         edges = np.ascontiguousarray(edges, dtype=np.int64)
@@ -339,6 +347,22 @@ class Solver:
         if dd is not None and dd.shape != (self.K,):
             raise ValueError("d must have shape (K,)")
         self._check(self._lib.pdr_set_data(self._h, None if uu is None else _ptr(uu), None if dd is None else _ptr(dd)))
+
+    def set_data_device(self, u_ptr: int = 0, d_ptr: int = 0):
+        """pdr_set_data from device arrays (device addresses as ints, e.g.
+        ``tensor.data_ptr()`` of contiguous float64 CUDA tensors; 0 keeps the
+        current values).  Checked and converted on the device."""
+        self._check(self._lib.pdr_set_data(self._h, C.c_void_p(u_ptr) if u_ptr else None,
+                                           C.c_void_p(d_ptr) if d_ptr else None))
+
+    def backward_into(self, T: int, ckpt_every: int, gu_ptr: int = 0, gd_ptr: int = 0) -> float:
+        """pdr_backward writing dL/du and dL/dd to device arrays (float64 [m] and
+        [K], device addresses as ints; 0 skips that gradient); returns L."""
+        L = C.c_double()
+        self._check(self._lib.pdr_backward(self._h, int(T), int(ckpt_every), C.byref(L),
+                                           C.c_void_p(gu_ptr) if gu_ptr else None,
+                                           C.c_void_p(gd_ptr) if gd_ptr else None))
+        return L.value
 
     def backward(self, T: int, ckpt_every: int = 10, grads: bool = True):
         """(L, dL/du, dL/dd) for L = z(f^(T)) after T sweeps of Alg. 1 from f = 0

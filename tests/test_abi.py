@@ -136,6 +136,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pdr_get_state(None, None, 0) == 1
     assert lib.pdr_set_state(None, None, 0) == 1
     assert lib.pdr_debug_wait(None, 10_000, 0) == 1
+    assert lib.pdr_debug_barrier(None, 1_000_000, 0) == 1
     assert lib.pdr_time_sweeps(None, 1, None, None) == 1
     assert lib.pdr_debug_fail_alloc(-1) == 1
     assert lib.pdr_debug_fail_alloc(0) == 0

@@ -128,3 +128,70 @@ def test_batch_fp64_tail_matches_single_solves(pdr):
             ref = oracle.Problem.from_instance(inst).residuals(f)
             assert ref["cap_rel"] <= 1e-6 and ref["cons_rel"] <= 1e-6
         assert r2["verdict"] == r["verdict"]
+
+
+def small_batch(seed=31, count=40):
+    """Instances small enough for the one-block-per-instance engine (m * K_p <= 2^18):
+    random out-degree-3 digraphs, n in [20, 300), K in [1, 120), every fifth at 0.6x capacity."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = int(rng.integers(20, 300))
+        K = int(rng.integers(1, 120))
+        g = I.random_digraph(n, 3, np.random.default_rng([seed, b]))
+        factor = 0.6 if b % 5 == 4 else 1.2
+        out.append(I.make_instance(f"s{b}", g, K, ("uniform_int", 1, 10), factor, np.random.default_rng([seed, b, 1])))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_engine_equals_single_solves_bit_for_bit(pdr, prec):
+    """The one-block-per-instance engine runs, per element, the standalone
+    kernels' arithmetic in their order: after a fixed number of sweeps every
+    instance's flows equal, bit for bit, a single-instance solve with the
+    variant the batch chose; the next sweep from them matches the oracle."""
+    insts = small_batch()
+    S = 137  # odd, and more than one launch's worth is not needed to cover the parity swap
+    opts = dict(precision=prec, eps_obj=0.0, resid_tol=0.0, max_sweeps=S)
+    with pdr.Batch(insts, **opts) as B:
+        res = B.solve()
+        cfg, _ = B.tuning()
+        flows = [B.solver(i).flows() for i in range(len(insts))]
+    assert all(r["sweeps"] == S and r["stop_name"] == "max_sweeps" for r in res)
+    for i, x in enumerate(insts):
+        with pdr.Solver.from_instance(x, edge_variant=int(cfg[i]), **opts) as s:
+            r1 = s.solve()
+            np.testing.assert_array_equal(s.flows(), flows[i], err_msg=x.name)
+        assert abs(r1["z"] - res[i]["z"]) <= 1e-12 * max(1.0, r1["z"])
+    x, f = insts[3], flows[3]
+    P = oracle.Problem.from_instance(x)
+    _, h = P.excess(f)
+    want, _, _ = P.qp_all(h, f)
+    with pdr.Solver.from_instance(x, precision=prec) as s:
+        s.set_flows(f)
+        s.sweeps(1)
+        got = s.flows()
+    sig = (np.abs(f) + np.abs(h[x.src]) + np.abs(h[x.col])).max(axis=1)[:, None]
+    tol = 1e-5 if prec == 0 else 1e-12
+    assert np.all(np.abs(got - want) <= tol * np.maximum(np.abs(want), sig) + 1e-36)
+
+
+def test_block_engine_verdicts_and_long_solves(pdr):
+    """Solves longer than one launch of the engine (2048 sweeps), stopped per
+    instance by their own rules, in the tail mode: verdicts as constructed and
+    as the graph-free host loop finds them, residuals <= 1e-6 per the oracle."""
+    insts = small_batch(seed=37, count=24)
+    opts = dict(precision=pdr.PREC_FP32_FP64TAIL, eps_obj=0.0, resid_tol=1e-6, eps_rel=1e-13, max_sweeps=300000)
+    with pdr.Batch(insts, **opts) as B:
+        res = B.solve()
+        flows = [B.solver(i).flows() for i in range(len(insts))]
+    with pdr.Batch(insts, use_graph=0, **opts) as B0:
+        res0 = B0.solve()
+    assert max(r["sweeps"] for r in res) > 2048
+    for x, r, r0, f in zip(insts, res, res0, flows):
+        want = x.feasible_by_construction
+        assert r["verdict"] == (pdr.VERDICT_FEASIBLE if want else pdr.VERDICT_INFEASIBLE), (x.name, r)
+        assert r["verdict"] == r0["verdict"], (x.name, r, r0)
+        if r["verdict"] == pdr.VERDICT_FEASIBLE:
+            ref = oracle.Problem.from_instance(x).residuals(f)
+            assert ref["cap_rel"] <= 1e-6 and ref["cons_rel"] <= 1e-6

@@ -113,13 +113,17 @@ def test_large_k_block_form_gradient_step(pdr, momentum):
 
 @pytest.mark.parametrize("momentum", [False, True])
 def test_fp64_gd_solve_matches_oracle(pdr, momentum):
-    """FP64 on the device: same stop sweep as the oracle and the same z trace.
+    """FP64 on the device: same stop sweep as the oracle and the same z trace,
+    and the same flows to 1e-9 relative.
 
-    An edge whose dz is zero to within FP64 rounding may be accepted by one
-    side and rejected by the other (the oracle sums sequentially, the GPU in
-    a tree); the trajectories then differ by one small step on one edge and
-    re-converge, so the trace is compared to 1e-6 relative, not bit for bit."""
+    One exception is allowed and detected: an edge whose dz is zero to within
+    FP64 rounding may be accepted by one side and rejected by the other (the
+    oracle sums sequentially, the GPU in a tree).  The trajectories then
+    differ by one small step on one edge (the trace departs by more than
+    1e-12 relative) and re-converge; the trace must still agree to 1e-6 and
+    the flows to 1e-4 of the largest demand."""
     algo = pdr.ALGO_GDM if momentum else pdr.ALGO_AGD
+    flips = []
     for inst in small_instances()[:3]:
         P = oracle.Problem.from_instance(inst)
         prm = oracle.gd_params(momentum, inst.K)
@@ -133,7 +137,13 @@ def test_fp64_gd_solve_matches_oracle(pdr, momentum):
         np.testing.assert_allclose(tr, zt, rtol=1e-6)
         if not momentum:
             assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])  # Alg. 3 never raises z
-        np.testing.assert_allclose(f, f_ref, rtol=1e-4, atol=1e-5 * inst.d.max())
+        flipped = np.max(np.abs(tr - zt) / zt) > 1e-12
+        if flipped:  # a near-tie accept/reject decision went the other way
+            np.testing.assert_allclose(f, f_ref, rtol=1e-4, atol=1e-5 * inst.d.max())
+        else:
+            np.testing.assert_allclose(f, f_ref, rtol=1e-9, atol=1e-12 * inst.d.max())
+        flips.append(flipped)
+    assert not all(flips)  # the tight comparison ran
 
 
 @pytest.mark.parametrize("momentum", [False, True])
