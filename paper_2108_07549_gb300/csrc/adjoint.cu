@@ -13,7 +13,8 @@
 //   vertex   Dbar_ik = (sum_{e out of i} cbar_e,k - sum_{e into i} cbar_e,k) / (2 delta_i)
 //            (h = Delta/delta, and c takes +h_i/2 and -h_j/2);
 //   demand   dbar_k += Dbar_{s_k,k} - Dbar_{t_k,k} (eq. (3h));
-//   flows    dL/df^(t)_e,k = cbar_e,k + Dbar_{j,k} - Dbar_{i,k} (eq. (3)).
+//   flows    dL/df^(t)_e,k = cbar_e,k + Dbar_{j,k} - Dbar_{i,k} (eq. (3)), formed
+//            on the fly by the next (earlier) sweep's edge step.
 // The seeds at T are dz/df = psi + h_j - h_i (eq. "cpgrad"), dz/du = -psi
 // and dz/dd_k = h_{s_k,k} - h_{t_k,k}.  One warp per edge row, two passes
 // over the row (the second from L1/L2), so any K works.
@@ -73,14 +74,38 @@ __global__ void demand_kernel(SweepArgs<T> a, const T* __restrict__ x, double* _
     }
 }
 
-// Warp per edge: Alg. 2's Jacobian applied to fbar (see the file comment).
-// Pass 1 decides every element's membership of the active set (c > cut)
-// from f and both height rows and records it as warp ballots in `mask`
-// (N words per 32 vectors of the row); pass 2 then re-reads only fbar.
-template <typename T>
+// Warp per edge: Alg. 2's Jacobian applied to fbar = dL/df^(t+1) (see the
+// file comment).  fbar is either read (the seed, at t + 1 = T) or formed on
+// the fly from the previous backward step's results, fbar = cbar^(t+1) +
+// Dbar^(t+1)_j - Dbar^(t+1)_i (`fused`), which saves writing and reading it.
+// cbar is updated in place: each element is read (as part of fbar) and then
+// written by the same lane.  Pass 1 decides every element's membership of the
+// active set (c > cut) from f and both height rows and records it as warp
+// ballots in `mask` (N words per 32 vectors of the row); pass 2 re-reads only
+// fbar's rows.
+template <typename T, bool FUSED>
+__device__ __forceinline__ void fbar_vec(const typename VecOf<T>::type* fb, const typename VecOf<T>::type* cb,
+                                         const typename VecOf<T>::type* di, const typename VecOf<T>::type* dj, int v,
+                                         T (&g)[VecOf<T>::N])
+{
+    constexpr int N = VecOf<T>::N;
+    if constexpr (FUSED) {
+        T c[N], x[N], y[N];
+        unpack(cb[v], c);
+        unpack(di[v], x);
+        unpack(dj[v], y);
+#pragma unroll
+        for (int j = 0; j < N; ++j) g[j] = c[j] + y[j] - x[j];
+    } else {
+        unpack(fb[v], g);
+    }
+}
+
+template <typename T, bool FUSED>
 __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a, const T* __restrict__ theta,
-                                                                 const T* __restrict__ fbar, T* __restrict__ cbar,
-                                                                 double* __restrict__ ubar, uint32_t* __restrict__ mask)
+                                                                 const T* __restrict__ fbar, T* cbar,
+                                                                 const T* __restrict__ Dbar, double* __restrict__ ubar,
+                                                                 uint32_t* __restrict__ mask)
 {
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
@@ -93,10 +118,14 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
         const T th = theta[e];
         const bool congested = th > T(0);
         const T cut = congested ? th : T(0);
+        const int32_t ti = a.src[e], tj = a.col[e];
         const VT* fr = reinterpret_cast<const VT*>(a.f + e * a.Kp);
-        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)a.src[e] * a.Kp);
-        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)a.col[e] * a.Kp);
-        const VT* fb = reinterpret_cast<const VT*>(fbar + e * a.Kp);
+        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)ti * a.Kp);
+        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)tj * a.Kp);
+        const VT* fb = FUSED ? nullptr : reinterpret_cast<const VT*>(fbar + e * a.Kp);
+        VT* cb = reinterpret_cast<VT*>(cbar + e * a.Kp);
+        const VT* di = FUSED ? reinterpret_cast<const VT*>(Dbar + (int64_t)ti * a.Kp) : nullptr;
+        const VT* dj = FUSED ? reinterpret_cast<const VT*>(Dbar + (int64_t)tj * a.Kp) : nullptr;
         uint32_t* me = mask + e * (int64_t)nq * N;
         T sb = T(0);
         int na = 0;
@@ -108,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
                 unpack(fr[v], f);
                 unpack(hi[v], x);
                 unpack(hj[v], y);
-                unpack(fb[v], g);
+                fbar_vec<T, FUSED>(fb, cb, di, dj, v, g);
             }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
@@ -127,15 +156,14 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
         // Alg. 2: theta = (S_A - u)/(2 + |A|); capacity kept: (S_A - u)/|A|.  With
         // the capacity kept and u = 0 no element is active and nothing flows back.
         const T corr = (congested && na > 0) ? sb / T((a.ck ? 0 : 2) + na) : T(0);
-        VT* out = reinterpret_cast<VT*>(cbar + e * a.Kp);
         for (int q = 0; q < nq; ++q) {
             const int v = q * 32 + lane;
             if (v >= vpr) continue;
             T g[N], o[N];
-            unpack(fb[v], g);
+            fbar_vec<T, FUSED>(fb, cb, di, dj, v, g);
 #pragma unroll
             for (int j = 0; j < N; ++j) o[j] = ((me[q * N + j] >> lane) & 1u) ? g[j] - corr : T(0);
-            out[v] = pack4(o);
+            cb[v] = pack4(o);
         }
         if (lane == 0) ubar[e] += (double)corr;
     }
@@ -192,34 +220,6 @@ __global__ void __launch_bounds__(kThreads) vertex_backward_kernel(SweepArgs<T> 
     }
 }
 
-// Warp per edge: dL/df^(t) = cbar + Dbar_j - Dbar_i.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) edge_adjoint_kernel(SweepArgs<T> a, const T* __restrict__ cbar,
-                                                                const T* __restrict__ Dbar, T* __restrict__ fbar)
-{
-    using VT = typename VecOf<T>::type;
-    constexpr int N = VecOf<T>::N;
-    const int lane = threadIdx.x & 31;
-    const int vpr = a.Kp / N;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t e = w0; e < a.m; e += nw) {
-        const VT* cb = reinterpret_cast<const VT*>(cbar + e * a.Kp);
-        const VT* di = reinterpret_cast<const VT*>(Dbar + (int64_t)a.src[e] * a.Kp);
-        const VT* dj = reinterpret_cast<const VT*>(Dbar + (int64_t)a.col[e] * a.Kp);
-        VT* out = reinterpret_cast<VT*>(fbar + e * a.Kp);
-        for (int v = lane; v < vpr; v += 32) {
-            T c[N], x[N], y[N], o[N];
-            unpack(cb[v], c);
-            unpack(di[v], x);
-            unpack(dj[v], y);
-#pragma unroll
-            for (int j = 0; j < N; ++j) o[j] = c[j] + y[j] - x[j];
-            out[v] = pack4(o);
-        }
-    }
-}
-
 int blocks(int64_t work, int per_block, int num_sms)
 {
     int64_t b = (work + per_block - 1) / per_block;
@@ -239,23 +239,23 @@ cudaError_t launch_seed(const SweepArgs<T>& a, T* fbar, double* ubar, double* db
 }
 
 template <typename T>
-cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar, T* cbar, T* Dbar, double* ubar,
-                                  double* dbar, uint32_t* mask, int num_sms, cudaStream_t s)
+cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, const T* fbar, T* cbar, T* Dbar,
+                                  double* ubar, double* dbar, uint32_t* mask, int fused, int num_sms, cudaStream_t s)
 {
-    edge_backward_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, theta, fbar, cbar, ubar,
-                                                                                       mask);
+    const int ge = blocks(a.m * 32, kThreads, num_sms);
+    if (fused) edge_backward_kernel<T, true><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
+    else edge_backward_kernel<T, false><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
     vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
         a, cbar, Dbar);
     demand_kernel<T><<<blocks(a.K, kThreads, num_sms), kThreads, 0, s>>>(a, Dbar, dbar, 1);
-    edge_adjoint_kernel<T><<<blocks(a.m * 32, kThreads, num_sms), kThreads, 0, s>>>(a, cbar, Dbar, fbar);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_seed<float>(const SweepArgs<float>&, float*, double*, double*, int, cudaStream_t);
 template cudaError_t launch_seed<double>(const SweepArgs<double>&, double*, double*, double*, int, cudaStream_t);
-template cudaError_t launch_backward_sweep<float>(const SweepArgs<float>&, const float*, float*, float*, float*,
-                                                  double*, double*, uint32_t*, int, cudaStream_t);
-template cudaError_t launch_backward_sweep<double>(const SweepArgs<double>&, const double*, double*, double*,
-                                                   double*, double*, double*, uint32_t*, int, cudaStream_t);
+template cudaError_t launch_backward_sweep<float>(const SweepArgs<float>&, const float*, const float*, float*, float*,
+                                                  double*, double*, uint32_t*, int, int, cudaStream_t);
+template cudaError_t launch_backward_sweep<double>(const SweepArgs<double>&, const double*, const double*, double*,
+                                                   double*, double*, double*, uint32_t*, int, int, cudaStream_t);
 
 }  // namespace pdr

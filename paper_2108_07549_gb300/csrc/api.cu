@@ -985,7 +985,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         }                                                \
     } while (0)
     // checkpoints of the flows and of the roots and warm starts at t = 0, C, 2C, ...
-    std::vector<T*> ck(grads ? nseg : 0), thck(grads ? nseg : 0), seg, th;
+    std::vector<T*> ck(grads ? nseg : 0), thck(grads ? nseg : 0), seg, th, hseg;
     for (auto& q : ck)
         if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
     for (auto& q : thck)
@@ -1000,6 +1000,9 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
         for (auto& q : th)
             if (!(q = (T*)grab(sizeof(T) * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
+        hseg.resize(C);  // the heights of every sweep of a segment, kept from its recomputation
+        for (auto& q : hseg)
+            if (!(q = (T*)grab(sizeof(T) * hn))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
         fbar = (T*)grab(sizeof(T) * fm);
         cbar = (T*)grab(sizeof(T) * fm);
         Dbar = (T*)grab(sizeof(T) * hn);
@@ -1036,11 +1039,12 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         const int64_t t0 = sgi * C, t1 = (t0 + C < Tn) ? t0 + C : Tn;
         CKB(cudaMemcpyAsync(seg[0], ck[sgi], sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
         CKB(cudaMemcpyAsync(ctx->theta[0], thck[sgi], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int64_t t = t0; t < t1; ++t) {  // recompute f^(t0+1..t1-1), record each sweep's roots
+        for (int64_t t = t0; t < t1; ++t) {  // recompute f^(t0+1..t1-1); keep each sweep's heights and roots
             const int rb = (int)((t - t0) & 1);
             SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
             a.f = seg[t - t0];
             a.f_out = seg[t - t0 + 1];
+            a.h = hseg[t - t0];
             a.theta_in = reinterpret_cast<const T*>(ctx->theta[rb]);
             a.theta = reinterpret_cast<T*>(ctx->theta[rb ^ 1]);
             CKB(launch_excess<T>(a, ctx->stream));
@@ -1051,8 +1055,10 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         for (int64_t t = t1 - 1; t >= t0; --t) {
             SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
             a.f = seg[t - t0];
-            CKB(launch_excess<T>(a, ctx->stream));  // h^(t)
-            CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, mask, ctx->num_sms, ctx->stream));
+            a.h = hseg[t - t0];  // h^(t), from the recomputation above
+            // the first step reads the seed; later ones form dL/df^(t+1) from cbar and Dbar
+            CKB(launch_backward_sweep<T>(a, th[t - t0], fbar, cbar, Dbar, ubar, dbar, mask, t == Tn - 1 ? 0 : 1,
+                                         ctx->num_sms, ctx->stream));
         }
     }
     // the gradients go to host or device memory alike (unified addressing)

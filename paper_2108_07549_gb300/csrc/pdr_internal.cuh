@@ -243,8 +243,8 @@ cudaError_t build_adjacency(int32_t n, int64_t m, const int64_t* row_ptr, const 
 template <typename T>
 cudaError_t launch_seed(const SweepArgs<T>& a, T* fbar, double* ubar, double* dbar, int num_sms, cudaStream_t s);
 template <typename T>
-cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, T* fbar, T* cbar, T* Dbar, double* ubar,
-                                  double* dbar, uint32_t* mask, int num_sms, cudaStream_t s);
+cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, const T* fbar, T* cbar, T* Dbar, double* ubar,
+                                  double* dbar, uint32_t* mask, int fused, int num_sms, cudaStream_t s);
 // words of the active-set ballots launch_backward_sweep keeps per edge
 inline int64_t backward_mask_words(int Kp, int vec) { return (int64_t)((Kp / vec + 31) / 32) * vec; }
 
