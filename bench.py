@@ -93,7 +93,7 @@ def parse():
                     help="time the sweep-loop engines (host loop, CUDA graph, persistent kernel) on instances "
                          "from m = 80 to the bench workload and print one JSON line")
     ap.add_argument("--excess-variant", type=int, default=-1,
-                    help="excess kernel form: -1 library default, 0 per-thread gathers, 1..3 bulk copies")
+                    help="excess kernel form: -1 library default, 0 per-thread gathers, 1..5 bulk copies")
     ap.add_argument("--compare-excess", action="store_true",
                     help="time the excess kernel forms (alone, warm and cold L2) and the sweep loop with each")
     ap.add_argument("--compare-variants", action="store_true",
@@ -405,7 +405,7 @@ def compare_excess(args, inst, pdr, torch, stream):
     out = {"kind": "excess-kernel form comparison", "workload": WORKLOAD, "sweeps": S, "dtype": "f32",
            "algorithmic_bytes": b_ex, "peak_gbs": peak, "peak_source": peak_src, "forms": {}}
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    for form in (0, 1, 2, 3):
+    for form in (0, 1, 2, 3, 4, 5):
         with torch.cuda.stream(stream):
             with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
                                           resid_tol=0.0, max_sweeps=S, excess_variant=form) as sv:

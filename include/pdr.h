@@ -129,11 +129,13 @@ typedef struct {
      * gives bit-identical heights).  -1 (default): the library's choice
      * (form 2 where it can be resident, else 0).
      * 0: one thread per (vertex, 4 values) gathers the incident flow rows.
-     * 1..3: per block, one warp brings the incident row segments (2 KB) of a
+     * 1..5: per block, one warp brings the incident row segments of a
      * contiguous range of vertices into shared memory with bulk copies
-     * (cp.async.bulk) through a ring of stages, and four warps add them:
-     * 1 = 4 stages of 8 segments, 2 = 2 stages of 8, 3 = 4 stages of 4.  A
-     * form that cannot be resident on the device gives PDR_ERR_INVALID_ARG. */
+     * (cp.async.bulk) through a ring of stages, and the other warps add them:
+     * 1 = 4 stages of 8 segments of 2 KB (four adding warps), 2 = 2 stages
+     * of 8 (2 KB), 3 = 4 stages of 4 (2 KB), 4 = 2 stages of 8 segments of
+     * 512 B (one adding warp), 5 = 4 stages of 8 (512 B).  A form that
+     * cannot be resident on the device gives PDR_ERR_INVALID_ARG. */
     int32_t excess_variant;
 } pdr_options;
 
@@ -252,7 +254,7 @@ pdr_status pdr_get_state(pdr_ctx *ctx, void *buf, int64_t bytes);
 pdr_status pdr_set_state(pdr_ctx *ctx, const void *buf, int64_t bytes);
 
 /* Test hook for the time limit of the device-side waits.
- * - Waits: the bulk-copy excess form (pdr_options.excess_variant 1..3)
+ * - Waits: the bulk-copy excess forms (pdr_options.excess_variant 1..5)
  *   waits on shared-memory barriers.
  * - Default limit: 2^32 SM clock cycles, about 2 s.
  * - cycles: sets that limit; 1000 <= cycles <= 2^32.

@@ -82,8 +82,8 @@ bool options_ok(const pdr_options* o, std::string* why)
         *why = "algo must be 0 (ESO), 1 (AGD), 2 (GDM) or 3 (capacity kept)";
         return false;
     }
-    if (o->excess_variant < -1 || o->excess_variant > 3) {
-        *why = "excess_variant must be -1 (default), 0 (gathers) or 1..3 (bulk copies)";
+    if (o->excess_variant < -1 || o->excess_variant > kExcessForms - 1) {
+        *why = "excess_variant must be -1 (default), 0 (gathers) or 1..5 (bulk copies)";
         return false;
     }
     const double g[] = {o->beta_init, o->beta_min, o->beta_max, o->alpha_inc, o->alpha_dec, o->gamma};
@@ -147,8 +147,8 @@ struct pdr_ctx {
     int grid_v[2] = {1, 1}, grid_e[2] = {1, 1}, cfg[2] = {-1, -1};
     // excess kernel form (0: gathers, 1..3: bulk copies); grid and vertex split of each bulk form
     int xform = 0;
-    int xgrid[4] = {0, 0, 0, 0};
-    int32_t* xv_start[4] = {nullptr, nullptr, nullptr, nullptr};
+    int xgrid[kExcessForms] = {};
+    int32_t* xv_start[kExcessForms] = {};
     int64_t n_psi[2] = {1, 1};
     int pgrid[2] = {0, 0};         // persistent kernel grid per precision (0: not available)
     int64_t pf[2] = {0, 0};        // edge-kernel L2 prefetch distance per precision (edges)
@@ -1099,6 +1099,7 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->trace, ctx->inv_scale_f, ctx->inv_deg_f, ctx->inv_deg_d, ctx->theta[0], ctx->theta[1],
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
                    ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3],
+                   ctx->xv_start[4], ctx->xv_start[5],
                    ctx->data_err};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -1160,7 +1161,7 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ctx->grid_v[0] = excess_grid(n, Kp, 4, ctx->num_sms, excess_resident_blocks<float>());
     ctx->grid_v[1] = excess_grid(n, Kp, 2, ctx->num_sms, excess_resident_blocks<double>());
     ctx->r_grid_v = excess_grid(n, Kp, 1, ctx->num_sms, 8);
-    for (int f = 1; f <= 3; ++f) {
+    for (int f = 1; f < kExcessForms; ++f) {
         const int r32 = excess_bulk_resident_blocks<float>(f), r64 = excess_bulk_resident_blocks<double>(f);
         const int64_t r = r32 < r64 ? r32 : r64;
         const int64_t g = r * ctx->num_sms < n ? r * ctx->num_sms : n;
@@ -1208,7 +1209,7 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     ALLOC(ctx->inv_dem_d, double, Kp);
     ALLOC(ctx->inv_dem_f, float, Kp);
     int gv = ctx->grid_v[0] > ctx->grid_v[1] ? ctx->grid_v[0] : ctx->grid_v[1];
-    for (int f = 1; f <= 3; ++f) {
+    for (int f = 1; f < kExcessForms; ++f) {
         if (ctx->xgrid[f] > gv) gv = ctx->xgrid[f];
         if (ctx->xgrid[f] > 0) ALLOC(ctx->xv_start[f], int32_t, ctx->xgrid[f] + 1);
     }
@@ -1280,7 +1281,7 @@ pdr_status pdr_create(int32_t n, int64_t m, const int64_t* row_ptr, const int32_
     CKC(cudaMemcpyAsync(ctx->inv_dem_f, idf.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, ctx->stream));
     CKC(build_adjacency(n, m, ctx->row_ptr, ctx->col, ctx->src, ctx->in_ptr, ctx->in_eid, ctx->inc_ptr, ctx->inc,
                         ctx->deg, ctx->work, ctx->stream));
-    for (int f = 1; f <= 3; ++f)
+    for (int f = 1; f < kExcessForms; ++f)
         if (ctx->xgrid[f] > 0) CKC(launch_excess_split(ctx->inc_ptr, n, ctx->xgrid[f], ctx->xv_start[f], ctx->stream));
     // degree-0 commodity endpoints make the instance infeasible outright
     {

@@ -23,6 +23,7 @@ namespace pdr {
 
 constexpr int kThreads = 256;  // block size of every sweep kernel
 constexpr int kBatchThreads = 512;  // block size of the one-block-per-instance batch kernel
+constexpr int kExcessForms = 6;     // excess kernel forms: 0 gathers, 1..5 bulk copies
 // Resident blocks per SM that the block forms of the edge kernels are
 // compiled for (the register cap that follows from it: 65,536 / (B x that)).
 constexpr int block_min_blocks(int B, int V)

@@ -194,9 +194,16 @@ __global__ void __launch_bounds__(kThreads) excess_kernel(SweepArgs<T> a)
 // a time limit; a block whose wait runs out sets DevState::fault and stop,
 // waits (with the same limit) for the copies it issued, and leaves.
 
-constexpr int kXCons = 128;                    // consumer threads: one 16-byte vector each
-constexpr int kXThreads = kXCons + 32;         // plus the producer warp
-constexpr int kXSegBytes = kXCons * 16;        // bytes of one row segment
+// C consumer threads (one 16-byte vector each) per block, plus the producer
+// warp; a row segment is C x 16 bytes (2 KB for C = 128, 512 B for C = 32).
+// Smaller segments keep every block's pass over one segment of all its rows
+// smaller, so that a row's second visit (from its other endpoint, in another
+// block) finds it in L2 when the two endpoints are far apart in vertex order.
+template <int C>
+__host__ __device__ constexpr int xseg_bytes()
+{
+    return C * 16;
+}
 constexpr int kXFirst = 1, kXLast = 2, kXEnd = 4;
 
 struct XDesc {
@@ -206,19 +213,21 @@ struct XDesc {
     double idg;     // 1/delta_i in the working precision (exact in double)
 };
 
-template <int S, int R>
+template <int S, int R, int C>
 constexpr size_t excess_bulk_smem()
 {
-    return (size_t)S * R * kXSegBytes + (size_t)S * (2 * sizeof(uint64_t) + sizeof(XDesc));
+    return (size_t)S * R * xseg_bytes<C>() + (size_t)S * (2 * sizeof(uint64_t) + sizeof(XDesc));
 }
 
-// S stages of R row segments
-template <typename T, int S, int R>
-__global__ void __launch_bounds__(kXThreads) excess_bulk_kernel(SweepArgs<T> a)
+// S stages of R row segments of C x 16 bytes
+template <typename T, int S, int R, int C>
+__global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
+    constexpr int kXCons = C;
+    constexpr int kXSegBytes = xseg_bytes<C>();
     constexpr int W = kXSegBytes / (int)sizeof(T);  // values per segment
     extern __shared__ __align__(128) unsigned char xsm[];
     unsigned char* ring = xsm;
@@ -1554,25 +1563,35 @@ cudaError_t launch_one(void (*kernel)(SweepArgs<T>), int grid, int block, cudaSt
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+template <typename T, int S, int R, int C>
+cudaError_t launch_bulk(const SweepArgs<T>& a, cudaStream_t stream, bool pdl)
+{
+    return launch_one<T>(excess_bulk_kernel<T, S, R, C>, a.grid_v, C + 32, stream, pdl, a, excess_bulk_smem<S, R, C>());
+}
+
+// Excess forms: 0 the per-thread gathers; bulk copies 1: 4 x 8 segments of
+// 2 KB, 2: 2 x 8 of 2 KB, 3: 4 x 4 of 2 KB, 4: 2 x 8 of 512 B, 5: 4 x 8 of 512 B.
 template <typename T>
 cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream, bool pdl)
 {
     switch (a.excess_form) {
-    case 1: return launch_one<T>(excess_bulk_kernel<T, 4, 8>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<4, 8>());
-    case 2: return launch_one<T>(excess_bulk_kernel<T, 2, 8>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<2, 8>());
-    case 3: return launch_one<T>(excess_bulk_kernel<T, 4, 4>, a.grid_v, kXThreads, stream, pdl, a, excess_bulk_smem<4, 4>());
+    case 1: return launch_bulk<T, 4, 8, 128>(a, stream, pdl);
+    case 2: return launch_bulk<T, 2, 8, 128>(a, stream, pdl);
+    case 3: return launch_bulk<T, 4, 4, 128>(a, stream, pdl);
+    case 4: return launch_bulk<T, 2, 8, 32>(a, stream, pdl);
+    case 5: return launch_bulk<T, 4, 8, 32>(a, stream, pdl);
     default: return launch_one<T>(excess_kernel<T>, a.grid_v, kThreads, stream, pdl, a);
     }
 }
 
-template <typename T, int S, int R>
+template <typename T, int S, int R, int C>
 int bulk_resident()
 {
-    const size_t smem = excess_bulk_smem<S, R>();
+    const size_t smem = excess_bulk_smem<S, R, C>();
     int blocks = 0;
-    if (cudaFuncSetAttribute(excess_bulk_kernel<T, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(excess_bulk_kernel<T, S, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, excess_bulk_kernel<T, S, R>, kXThreads, smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, excess_bulk_kernel<T, S, R, C>, C + 32, smem) !=
             cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -1584,9 +1603,11 @@ template <typename T>
 int excess_bulk_resident_blocks(int form)
 {
     switch (form) {
-    case 1: return bulk_resident<T, 4, 8>();
-    case 2: return bulk_resident<T, 2, 8>();
-    case 3: return bulk_resident<T, 4, 4>();
+    case 1: return bulk_resident<T, 4, 8, 128>();
+    case 2: return bulk_resident<T, 2, 8, 128>();
+    case 3: return bulk_resident<T, 4, 4, 128>();
+    case 4: return bulk_resident<T, 2, 8, 32>();
+    case 5: return bulk_resident<T, 4, 8, 32>();
     default: return 0;
     }
 }

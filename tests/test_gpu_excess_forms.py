@@ -27,7 +27,7 @@ from paper_2108_07549_gb300 import instances as I
 
 pytestmark = pytest.mark.gpu
 FP32_FLOOR = 1e-36
-FORMS = (1, 2, 3)
+FORMS = (1, 2, 3, 4, 5)
 
 
 @pytest.fixture(scope="module")
@@ -145,7 +145,7 @@ def test_switch_batch_and_rejection(pdr):
         s.set_options(excess_variant=2)
         got = s.solve()
         with pytest.raises(pdr.PdrError):
-            s.set_options(excess_variant=4)
+            s.set_options(excess_variant=6)
     # the FP32 stop rules read z, whose last bits depend on the form: compare verdicts
     assert got["verdict"] == want["verdict"] != pdr.VERDICT_UNKNOWN
     insts = cases()[:4]

@@ -43,7 +43,7 @@ def instance():
     return I.make_instance("grid6_k33", I.grid_graph(6), 33, ("lognormal", 1.0, 0.5), 1.2, rng)
 
 
-@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
 def test_wait_runs_out_and_the_context_recovers(pdr, form):
     inst = instance()
     rng = np.random.default_rng(2)
