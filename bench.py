@@ -796,7 +796,8 @@ def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
                     r = sv.solve()
             row[prec] = {"ms": r["ms_total"], "sweeps": r["sweeps"], "sweeps_fp64": r["sweeps_fp64"],
                          "cap_rel": r["cap_rel"], "cons_rel": r["cons_rel"], "margin": r["margin"],
-                         "verdict": r["verdict_name"], "stop": r["stop_name"]}
+                         "verdict": r["verdict_name"], "stop": r["stop_name"],
+                         "fp32_phase_stop": r["stop_name_fp32"]}
         P = oracle.Problem.from_instance(inst)
         t0 = time.perf_counter()
         f, rep = P.solve_eso(max_sweeps=300000, eps_obj=0.0, resid_tol=1e-6)
@@ -903,8 +904,10 @@ def batch_forms_block(pdr, torch, stream, big_batch, small_batch, flush):
     def summary(res):
         v = [r["verdict_name"] for r in res]
         feas = [r for r in res if r["verdict_name"] == "feasible"]
+        tails = [r["stop_name_fp32"] for r in res if r["sweeps_fp64"] > 0]
         return {"verdicts": {k: v.count(k) for k in sorted(set(v))},
                 "sweeps_max": max(r["sweeps"] for r in res),
+                "fp64_tail_started_by": {k: tails.count(k) for k in sorted(set(tails))},
                 "max_cap_rel_feasible": max((r["cap_rel"] for r in feas), default=None),
                 "max_cons_rel_feasible": max((r["cons_rel"] for r in feas), default=None),
                 "verdicts_as_constructed": sum(1 for r, w in zip(res, want)

@@ -154,6 +154,9 @@ typedef struct {
     double ms_total;     /* wall time of the solve in milliseconds */
     int32_t verdict;     /* pdr_verdict */
     int32_t stop_reason; /* pdr_stop_reason */
+    int32_t stop_reason_fp32; /* PDR_PREC_FP32_FP64TAIL: the pdr_stop_reason that ended the FP32
+                                 phase (it decides whether the FP64 tail ran); -1 otherwise */
+    int32_t pad;
 } pdr_result;
 
 /* Fills *opt with the defaults listed in pdr_options.  Returns PDR_OK, or

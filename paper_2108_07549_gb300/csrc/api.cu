@@ -160,6 +160,7 @@ struct pdr_ctx {
     // residuals
     double *r_h64 = nullptr, *r_part = nullptr;
     int* data_err = nullptr;  // error bits of a device-side pdr_set_data
+    int reason_fp32 = -1;     // tail mode: the stop reason of the last FP32 phase
     ResidOut* r_out = nullptr;
     ResidOut* hr_out = nullptr;  // pinned
     int r_grid_v = 1, r_grid_e = 1;
@@ -1977,6 +1978,7 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     s = ctx->cur_prec ? run_phase<double>(ctx, t_start) : run_phase<float>(ctx, t_start);
     if (s != PDR_OK) return s;
     const int r = ctx->hst->reason;
+    const int reason32 = (tail && ctx->cur_prec == 0) ? r : (tail ? ctx->reason_fp32 : -1);
     if (tail && ctx->cur_prec == 0 && needs_fp64_tail(r)) {
         ctx->t_widen = ctx->hst->t;
         s = widen_to_fp64(ctx);
@@ -1991,6 +1993,8 @@ pdr_status pdr_solve(pdr_ctx* ctx, pdr_result* out)
     res.sweeps_fp64 = ctx->cur_prec ? ctx->hst->t - (ctx->t_widen >= 0 ? ctx->t_widen : 0) : 0;
     res.dz = ctx->hst->dz;
     res.stop_reason = ctx->hst->reason;
+    res.stop_reason_fp32 = reason32;
+    ctx->reason_fp32 = reason32;
     s = residuals_into(ctx, &res);
     if (s != PDR_OK) return s;
     res.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2599,6 +2603,7 @@ pdr_status pdr_batch_solve(pdr_batch* b, pdr_result* results)
     const bool tail = b->ctx[0]->opt.precision == PDR_PREC_FP32_FP64TAIL;
     std::vector<char> run32(B, 0), run64(B, 0);
     std::vector<int64_t> t_start(B, 0), sweeps32(B, 0);
+    std::vector<int32_t> reason32(B, -1);
     pdr_status s = PDR_OK;
     // every instance starts a fresh solve from its current flows, as pdr_solve
     for (int32_t i = 0; i < B; ++i) {
@@ -2618,6 +2623,7 @@ pdr_status pdr_batch_solve(pdr_batch* b, pdr_result* results)
             s = read_state(c);
             if (s != PDR_OK) return s;
             sweeps32[i] = c->hst->t;
+            reason32[i] = c->hst->reason;
             if (needs_fp64_tail(c->hst->reason)) {
                 s = widen_to_fp64(c);
                 if (s != PDR_OK) return s;
@@ -2648,6 +2654,7 @@ pdr_status pdr_batch_solve(pdr_batch* b, pdr_result* results)
         r.sweeps_fp64 = c->cur_prec ? c->hst->t - sweeps32[i] : 0;
         r.dz = c->hst->dz;
         r.stop_reason = c->hst->reason;
+        r.stop_reason_fp32 = tail ? reason32[i] : -1;
         s = residuals_into(c, &r);
         if (s != PDR_OK) return batch_fail(s, "instance " + std::to_string(i) + ": " + c->err);
         r.ms_total = ms;

@@ -66,13 +66,14 @@ class Result(C.Structure):
         ("sweeps", C.c_int64), ("sweeps_fp64", C.c_int64), ("z", C.c_double), ("dz", C.c_double),
         ("cap_abs", C.c_double), ("cap_rel", C.c_double), ("cons_abs", C.c_double), ("cons_rel", C.c_double),
         ("f_min", C.c_double), ("margin", C.c_double), ("margin_scale", C.c_double), ("ms_total", C.c_double),
-        ("verdict", C.c_int32), ("stop_reason", C.c_int32),
+        ("verdict", C.c_int32), ("stop_reason", C.c_int32), ("stop_reason_fp32", C.c_int32), ("pad", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
         out = {k: getattr(self, k) for k, _ in self._fields_}
         out["verdict_name"] = VERDICT_NAMES.get(self.verdict, "?")
         out["stop_name"] = STOP_NAMES.get(self.stop_reason, "?")
+        out["stop_name_fp32"] = STOP_NAMES.get(self.stop_reason_fp32, "-")
         return out
 
 

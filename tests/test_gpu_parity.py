@@ -276,6 +276,11 @@ def test_verdicts_tiny(pdr, prec):
             r = s.solve()
             f = s.flows()
         assert r["verdict"] == want, (inst.name, r, rep)
+        if prec == "tail":  # the rule that ended the FP32 phase is reported
+            assert r["stop_name_fp32"] in ("stall", "plateau", "objective", "relative", "residual"), r
+            assert (r["sweeps_fp64"] > 0) == (r["stop_name_fp32"] != "residual"), r
+        else:
+            assert r["stop_name_fp32"] == "-", r
         if want == pdr.VERDICT_FEASIBLE:
             ref = P.residuals(f)
             assert ref["cap_rel"] <= 1e-6 and ref["cons_rel"] <= 1e-6
