@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(B, gd_min_blocks(B, V)) gd_block_kernel(SweepA
     using VT = typename VecOf<T>::type;
     using A = Acc<T>;
     constexpr int N = VecOf<T>::N;
-    __shared__ T sa_buf[32];
-    __shared__ int sb_buf[32];
-    __shared__ T sc_buf[32];
+    __shared__ T sa_buf[33];
+    __shared__ int sb_buf[33];
+    __shared__ T sc_buf[33];
     volatile DevState* vst = a.st;
     if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {

@@ -850,7 +850,11 @@ __global__ void __launch_bounds__(kThreads, 2) edge_pipe_kernel(SweepArgs<T> a)
 // ------------------------------------------------------------------ edge QP, block form (large K)
 
 // Block-wide S(w), n(w), m(w) of a row held by the whole block (thread l keeps
-// vectors l + q*B); the same value in every thread.
+// vectors l + q*B); the same value in every thread.  The warp partials go to
+// slots 0..31 of sa/sb/sm (33 entries each); warp 0 combines them lane-parallel
+// and leaves the totals in slot 32, which every thread reads after the second
+// barrier.  A serial walk over the partials by every thread would put one
+// dependent shared-memory load per warp on the critical path of every pass.
 template <typename T, int V, int N>
 __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& n, T& mn, T* sa, int* sb, T* sm)
 {
@@ -867,33 +871,29 @@ __device__ __forceinline__ void block_above(const T (&c)[V][N], T w, T& S, int& 
                 ml = x < ml ? x : ml;
             }
         }
-    sl = group_sum<32>(sl);
-    if constexpr (sizeof(T) == 4) {  // as in above(): ml is positive or +inf
-        nl = (int)__reduce_add_sync(kFull, (unsigned)nl);
-        ml = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(ml)));
-    } else {
-        nl = group_sum<32>(nl);
-        ml = group_min<32>(ml);
-    }
-    const int wi = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
+    warp_sum_count_min(sl, nl, ml);
+    const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
         sa[wi] = sl;
         sb[wi] = nl;
         sm[wi] = ml;
     }
     __syncthreads();
-    const int nw = blockDim.x >> 5;
-    T ts = T(0), tm = T(INFINITY);
-    int tn = 0;
-    for (int q = 0; q < nw; ++q) {  // same order in every thread
-        ts += sa[q];
-        tn += sb[q];
-        tm = sm[q] < tm ? sm[q] : tm;
+    if (wi == 0) {
+        const int nw = blockDim.x >> 5;
+        T ts = l < nw ? sa[l] : T(0), tm = l < nw ? sm[l] : T(INFINITY);
+        int tn = l < nw ? sb[l] : 0;
+        warp_sum_count_min(ts, tn, tm);
+        if (l == 0) {
+            sa[32] = ts;
+            sb[32] = tn;
+            sm[32] = tm;
+        }
     }
-    S = ts;
-    n = tn;
-    mn = tm;
     __syncthreads();
+    S = sa[32];
+    n = sb[32];
+    mn = sm[32];
 }
 
 // One block of B threads per edge; thread l keeps row vectors l + q*B.
@@ -904,9 +904,9 @@ __global__ void __launch_bounds__(B, block_min_blocks(B, V)) edge_block_kernel(S
     using VT = typename VecOf<T>::type;
     constexpr int N = VecOf<T>::N;
     using A = Acc<T>;
-    __shared__ T sa_buf[32];
-    __shared__ int sb_buf[32];
-    __shared__ T sm_buf[32];
+    __shared__ T sa_buf[33];
+    __shared__ int sb_buf[33];
+    __shared__ T sm_buf[33];
     volatile DevState* vst = a.st;
     if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {               // the decision block
@@ -1155,9 +1155,9 @@ __global__ void __launch_bounds__(B, 1) edge_staged_kernel(SweepArgs<T> a)
     using A = Acc<T>;
     extern __shared__ __align__(128) unsigned char esm[];
     __shared__ __align__(8) uint64_t full;
-    __shared__ T sa_buf[32];
-    __shared__ int sb_buf[32];
-    __shared__ T sm_buf[32];
+    __shared__ T sa_buf[33];
+    __shared__ int sb_buf[33];
+    __shared__ T sm_buf[33];
     volatile DevState* vst = a.st;
     if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
     if (blockIdx.x == gridDim.x - 1) {  // the decision block

@@ -180,7 +180,35 @@ __device__ __forceinline__ X warp_max(X x)
     return x;
 }
 
-// Block-wide sum of a value and a count, broadcast to every thread.
+// Warp-wide sum, count and minimum, in every lane.  For float the count and
+// the minimum take one redux each: the values combined are positive or +inf
+// (sums above a threshold w >= 0), so their bit patterns order as unsigned
+// integers.
+template <typename T>
+__device__ __forceinline__ void warp_sum_count_min(T& s, int& n, T& mn)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if constexpr (sizeof(T) == 4) {
+        n = (int)__reduce_add_sync(kFull, (unsigned)n);
+        mn = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n += __shfl_xor_sync(kFull, n, o);
+            const T y = __shfl_xor_sync(kFull, mn, o);
+            mn = y < mn ? y : mn;
+        }
+    }
+}
+
+// Block-wide reductions broadcast to every thread.  The warp partials go to
+// slots 0..31 of the caller's buffers (33 entries each); warp 0 combines them
+// lane-parallel and leaves the totals in slot 32, read by every thread after
+// the second barrier.  (The next call writes slots 0..31 before its first
+// barrier and slot 32 only after it, so no trailing barrier is needed.)
+
+// Sum of a value and a count.
 template <typename T>
 __device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
 {
@@ -195,20 +223,26 @@ __device__ __forceinline__ void block_sum2(T& a, int& b, T* sa, int* sb)
         sb[w] = b;
     }
     __syncthreads();
-    const int nw = blockDim.x >> 5;
-    T ta = 0;
-    int tb = 0;
-    for (int q = 0; q < nw; ++q) {  // same order in every thread
-        ta += sa[q];
-        tb += sb[q];
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        T ta = l < nw ? sa[l] : T(0);
+        int tb = l < nw ? sb[l] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_xor_sync(kFull, ta, o);
+            tb += __shfl_xor_sync(kFull, tb, o);
+        }
+        if (l == 0) {
+            sa[32] = ta;
+            sb[32] = tb;
+        }
     }
-    a = ta;
-    b = tb;
     __syncthreads();
+    a = sa[32];
+    b = sb[32];
 }
 
-// Block-wide sums of two values, broadcast to every thread (one pair of
-// barriers for both).
+// Sums of two values.
 template <typename T>
 __device__ __forceinline__ void block_sum_pair(T& a, T& b, T* sa, T* sb)
 {
@@ -223,15 +257,22 @@ __device__ __forceinline__ void block_sum_pair(T& a, T& b, T* sa, T* sb)
         sb[w] = b;
     }
     __syncthreads();
-    const int nw = blockDim.x >> 5;
-    T ta = 0, tb = 0;
-    for (int q = 0; q < nw; ++q) {  // same order in every thread
-        ta += sa[q];
-        tb += sb[q];
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        T ta = l < nw ? sa[l] : T(0), tb = l < nw ? sb[l] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_xor_sync(kFull, ta, o);
+            tb += __shfl_xor_sync(kFull, tb, o);
+        }
+        if (l == 0) {
+            sa[32] = ta;
+            sb[32] = tb;
+        }
     }
-    a = ta;
-    b = tb;
     __syncthreads();
+    a = sa[32];
+    b = sb[32];
 }
 
 // ------------------------------------------------------------------ objective accumulators
