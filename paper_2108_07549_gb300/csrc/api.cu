@@ -505,10 +505,6 @@ pdr_status select_edge_variants(pdr_ctx* ctx, const pdr_options& o)
     } else {
         c32 = edge_config<float>(Kp);
         c64 = edge_config<double>(Kp);
-        if (is_gd(o)) {
-            c32 = gd_preferred_config(c32);
-            c64 = gd_preferred_config(c64);
-        }
     }
     if (c32 < 0 || (o.precision != PDR_PREC_FP32 && c64 < 0))
         return ctx->fail(PDR_ERR_UNSUPPORTED,
@@ -1327,8 +1323,7 @@ pdr_status pdr_set_options(pdr_ctx* ctx, const pdr_options* opt)
     std::string why;
     if (!options_ok(&o, &why)) return ctx->fail(PDR_ERR_INVALID_ARG, why);
     const bool variant_changed = o.edge_variant != ctx->opt.edge_variant ||
-                                 (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0) ||
-                                 (o.edge_variant < 0 && is_gd(o) != is_gd(ctx->opt));
+                                 (o.precision != PDR_PREC_FP32 && ctx->cfg[1] < 0);
     if (variant_changed) {
         const pdr_status vs = select_edge_variants(ctx, o);  // writes nothing on failure
         if (vs != PDR_OK) return vs;

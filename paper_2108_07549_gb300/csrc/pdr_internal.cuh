@@ -207,7 +207,6 @@ template <typename T>
 cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
                                int psi_prologue, cudaStream_t stream);
 bool batch_block_config(int cfg);
-int gd_preferred_config(int cfg);
 
 // Packs and widens m padded rows into dst[rows*K] (double), dst writable by the GPU.
 template <typename T>

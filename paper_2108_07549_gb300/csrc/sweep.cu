@@ -1432,11 +1432,6 @@ int edge_config(int Kp)
     return -1;
 }
 
-// Alg. 3 / Alg. 4 take the 256 x 10 block form where Alg. 2 takes 512 x 5
-// (equal capacity; the gradient step ran faster with fewer threads per edge
-// on grid100_k10000: 0.57 against 0.51 of the HBM peak).
-int gd_preferred_config(int cfg) { return cfg == 12 ? 13 : cfg; }
-
 template <typename T, int V>
 int pipe_resident()
 {
