@@ -169,6 +169,75 @@ __global__ void __launch_bounds__(kThreads) edge_backward_kernel(SweepArgs<T> a,
     }
 }
 
+// Block of B threads per edge for long rows (thread l holds row vectors l +
+// q*B): the same step as edge_backward_kernel, but the row's cotangent and
+// its active-set bits stay in registers between the block-wide sum and the
+// write, so every input row is read once (the warp form reads fbar, or cbar
+// and both Dbar rows, a second time).
+template <typename T, int B, int V, bool FUSED>
+__global__ void __launch_bounds__(B, (1024 / B > 1 ? 1024 / B : 1))
+    edge_backward_block_kernel(SweepArgs<T> a, const T* __restrict__ theta, const T* __restrict__ fbar, T* cbar,
+                               const T* __restrict__ Dbar, double* __restrict__ ubar)
+{
+    using VT = typename VecOf<T>::type;
+    constexpr int N = VecOf<T>::N;
+    static_assert(V * N <= 32, "one bit per held value");
+    __shared__ T sa_buf[33];
+    __shared__ int sb_buf[33];
+    const int vpr = a.Kp / N;
+    for (int64_t e = blockIdx.x; e < a.m; e += gridDim.x) {
+        const T th = theta[e];
+        const bool congested = th > T(0);
+        const T cut = congested ? th : T(0);
+        const int32_t ti = a.src[e], tj = a.col[e];
+        const VT* fr = reinterpret_cast<const VT*>(a.f + e * a.Kp);
+        const VT* hi = reinterpret_cast<const VT*>(a.h + (int64_t)ti * a.Kp);
+        const VT* hj = reinterpret_cast<const VT*>(a.h + (int64_t)tj * a.Kp);
+        const VT* fb = FUSED ? nullptr : reinterpret_cast<const VT*>(fbar + e * a.Kp);
+        VT* cb = reinterpret_cast<VT*>(cbar + e * a.Kp);
+        const VT* di = FUSED ? reinterpret_cast<const VT*>(Dbar + (int64_t)ti * a.Kp) : nullptr;
+        const VT* dj = FUSED ? reinterpret_cast<const VT*>(Dbar + (int64_t)tj * a.Kp) : nullptr;
+        T g[V][N];
+        uint32_t act = 0;  // bit q*N + j: value j of vector q is in the active set
+        T sb = T(0);
+        int na = 0;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = threadIdx.x + q * B;
+            if (v < vpr) {
+                T f[N], x[N], y[N];
+                unpack(fr[v], f);
+                unpack(hi[v], x);
+                unpack(hj[v], y);
+                fbar_vec<T, FUSED>(fb, cb, di, dj, v, g[q]);
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (fma(T(0.5), x[j] - y[j], f[j]) > cut) {  // the edge-QP kernel's c
+                        act |= 1u << (q * N + j);
+                        sb += g[q][j];
+                        ++na;
+                    }
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) g[q][j] = T(0);
+            }
+        }
+        block_sum2(sb, na, sa_buf, sb_buf);
+        const T corr = (congested && na > 0) ? sb / T((a.ck ? 0 : 2) + na) : T(0);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int v = threadIdx.x + q * B;
+            if (v < vpr) {
+                T o[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) o[j] = ((act >> (q * N + j)) & 1u) ? g[q][j] - corr : T(0);
+                cb[v] = pack4(o);
+            }
+        }
+        if (threadIdx.x == 0) ubar[e] += (double)corr;
+    }
+}
+
 // Thread per (vertex, vector): Dbar = (sum_out cbar - sum_in cbar) / (2 delta),
 // the incidence list traversed in its stored order as by the excess kernel.
 template <typename T>
@@ -238,13 +307,47 @@ cudaError_t launch_seed(const SweepArgs<T>& a, T* fbar, double* ubar, double* db
     return cudaGetLastError();
 }
 
+template <typename T, int B, int V>
+void launch_backward_block(const SweepArgs<T>& a, const T* theta, const T* fbar, T* cbar, T* Dbar, double* ubar,
+                           int fused, int num_sms, cudaStream_t s)
+{
+    const int64_t per_sm = 1024 / B > 1 ? 1024 / B : 1;  // resident under the kernel's launch bounds
+    const int g = (int)(a.m < per_sm * num_sms ? a.m : per_sm * num_sms);
+    if (fused) edge_backward_block_kernel<T, B, V, true><<<g, B, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar);
+    else edge_backward_block_kernel<T, B, V, false><<<g, B, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar);
+}
+
+// The edge step's form: the block form with the smallest row capacity that
+// holds Kp, for rows longer than two vectors per lane of a warp; else (and
+// beyond the largest block capacity) the warp form.
+template <typename T>
+int backward_block_form(int Kp)
+{
+    const int vpr = Kp / VecOf<T>::N;
+    if (vpr <= 64) return -1;
+    const int cap[] = {128 * 2, 128 * 4, 256 * 4, 512 * 4, 512 * 5, 512 * 8, 1024 * 8};  // vectors, B x V
+    for (int i = 0; i < 7; ++i)
+        if (vpr <= cap[i]) return i;
+    return -1;
+}
+
 template <typename T>
 cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, const T* fbar, T* cbar, T* Dbar,
                                   double* ubar, double* dbar, uint32_t* mask, int fused, int num_sms, cudaStream_t s)
 {
     const int ge = blocks(a.m * 32, kThreads, num_sms);
-    if (fused) edge_backward_kernel<T, true><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
-    else edge_backward_kernel<T, false><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
+    switch (a.m > 0 ? backward_block_form<T>(a.Kp) : -1) {
+    case 0: launch_backward_block<T, 128, 2>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 1: launch_backward_block<T, 128, 4>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 2: launch_backward_block<T, 256, 4>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 3: launch_backward_block<T, 512, 4>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 4: launch_backward_block<T, 512, 5>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 5: launch_backward_block<T, 512, 8>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    case 6: launch_backward_block<T, 1024, 8>(a, theta, fbar, cbar, Dbar, ubar, fused, num_sms, s); break;
+    default:
+        if (fused) edge_backward_kernel<T, true><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
+        else edge_backward_kernel<T, false><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
+    }
     vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
         a, cbar, Dbar);
     demand_kernel<T><<<blocks(a.K, kThreads, num_sms), kThreads, 0, s>>>(a, Dbar, dbar, 1);
