@@ -450,7 +450,7 @@ def compare_engines(args, inst, pdr, torch, stream):
     out = {"kind": "sweep-loop engine comparison", "sweeps": S, "dtype": "f32", "us_per_sweep": {}}
     for c in cases:
         row = {"m": c.m, "K": c.K}
-        for name, eng in (("host_loop", 0), ("graph", 1), ("persistent", 2)):
+        for name, eng in (("host_loop", 0), ("graph", 1), ("persistent", 2), ("cluster", 3)):
             with torch.cuda.stream(stream):
                 with pdr.Solver.from_instance(c, stream=stream.cuda_stream, precision=pdr.PREC_FP32, eps_obj=0.0,
                                               resid_tol=0.0, max_sweeps=S, use_graph=eng) as sv:
@@ -469,51 +469,74 @@ def compare_engines(args, inst, pdr, torch, stream):
     print(json.dumps(out), flush=True)
 
 
-def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
-    """The differentiated form: L = z(f^(T)) and its gradient w.r.t. u and d
-    by reverse mode through T sweeps with checkpoints every ckpt, against the
-    T forward sweeps alone (FP32, CUDA events on the solver stream)."""
+def time_reverse_mode(pdr, torch, stream, inst, T, ckpt):
+    """The differentiated form through T sweeps: the forward sweeps alone,
+    then forward + gradient with checkpoints every ckpt sweeps and with every
+    sweep kept (ckpt_every = 1, nothing recomputed).  FP32, median of three,
+    CUDA events on the solver's stream; one untimed call of each first (it
+    also sizes the workspace the context keeps between calls)."""
     import numpy as np
 
-    out = {"kind": "differentiated form", "workload": WORKLOAD, "T": T, "ckpt_every": ckpt, "dtype": "f32"}
+    out = {"T": T, "ckpt_every": ckpt, "dtype": "f32"}
+    peak, peak_src = load_peaks()
     with torch.cuda.stream(stream):
         with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
-            sv.backward(T, ckpt)  # warm-up
-            for key, grads in (("forward_only", False), ("forward_and_gradient", True)):
+            def timed(c, grads):
+                sv.backward(T, c, grads=grads)
                 times = []
                 for _ in range(3):
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     torch.cuda.synchronize()
                     e0.record(stream)
-                    L, gu, gd = sv.backward(T, ckpt, grads=grads)
+                    res = sv.backward(T, c, grads=grads)
                     e1.record(stream)
                     torch.cuda.synchronize()
                     times.append(e0.elapsed_time(e1))
-                out[key + "_ms"] = sorted(times)[1]
-            out["L"] = L
-            out["grad_u_norm"] = float(np.linalg.norm(gu))
-            out["grad_d_norm"] = float(np.linalg.norm(gd))
-            out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
-    out["gradient_over_forward"] = out["forward_and_gradient_ms"] / out["forward_only_ms"]
+                return sorted(times)[1], res
+
+            out["forward_only_ms"], _ = timed(ckpt, False)
+            for c, key in ((ckpt, None), (1, "ckpt_every_1")):
+                ms, (L, gu, gd) = timed(c, True)
+                extra_bytes = T * gradient_sweep_bytes(inst, keep_all=(c == 1))
+                extra_ms = ms - out["forward_only_ms"]
+                rec = {"forward_and_gradient_ms": ms, "gradient_over_forward": ms / out["forward_only_ms"],
+                       "gradient_roofline": {"bound": "hbm", "algorithmic_bytes": extra_bytes, "ms": extra_ms,
+                                             "achieved": extra_bytes / (extra_ms / 1e3) / 1e9, "peak": peak,
+                                             "unit": "GB/s", "peak_source": peak_src,
+                                             "frac": extra_bytes / (extra_ms / 1e3) / 1e9 / peak}}
+                if key is None:
+                    out.update(rec)
+                    out["L"] = L
+                    out["grad_u_norm"] = float(np.linalg.norm(gu))
+                    out["grad_d_norm"] = float(np.linalg.norm(gd))
+                    out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
+                    g_ref = (L, gu, gd)
+                else:
+                    rec["same_gradients_bitwise"] = bool(L == g_ref[0] and np.array_equal(gu, g_ref[1]) and
+                                                         np.array_equal(gd, g_ref[2]))
+                    out[key] = rec
     out["forward_updates_per_s"] = inst.m * inst.K * T / (out["forward_only_ms"] / 1e3)
-    extra_bytes = T * gradient_sweep_bytes(inst)
-    extra_ms = out["forward_and_gradient_ms"] - out["forward_only_ms"]
-    peak, peak_src = load_peaks()
-    out["gradient_roofline"] = {"bound": "hbm", "algorithmic_bytes": extra_bytes, "ms": extra_ms,
-                                "achieved": extra_bytes / (extra_ms / 1e3) / 1e9,
-                                "peak": peak, "unit": "GB/s", "peak_source": peak_src,
-                                "frac": extra_bytes / (extra_ms / 1e3) / 1e9 / peak}
+    return out
+
+
+def bench_adjoint(args, inst, pdr, torch, stream, T=50, ckpt=10):
+    """The differentiated form (time_reverse_mode) on the chosen workload."""
+    out = {"kind": "differentiated form", "workload": WORKLOAD}
+    out.update(time_reverse_mode(pdr, torch, stream, inst, T, ckpt))
     out["cpu_baseline"] = adjoint_cpu_baseline(inst)
     print(json.dumps(out), flush=True)
 
 
-def gradient_sweep_bytes(inst) -> int:
+def gradient_sweep_bytes(inst, keep_all: bool = False) -> int:
     """Algorithmic bytes of the gradient's extra work per unrolled sweep (FP32),
     each array counted once: the segment's forward sweep again (excess: f in,
     h out, 4K(m+n); edge QP: f, h in, f' out, 4K(2m+n); the heights are kept
     per sweep), the Jacobian step (f, h, dL/dc' and dL/dDelta' in, dL/dc out,
     4K(3m+2n); it forms dL/df from them) and the vertex gather (dL/dc in,
-    dL/dDelta out, 4K(m+n)): 4K(7m+5n)."""
+    dL/dDelta out, 4K(m+n)): 4K(7m+5n).  With every sweep kept (keep_all) the
+    recomputation drops out: 4K(4m+3n)."""
+    if keep_all:
+        return 4 * inst.K * (4 * inst.m + 3 * inst.n)
     return 4 * inst.K * (7 * inst.m + 5 * inst.n)
 
 
@@ -777,7 +800,8 @@ def l2_resident_block(pdr, torch, stream, inst, flush, steps=5, S=2000):
 def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
     """Time to residual 1e-6 (cap_rel and cons_rel <= 1e-6, or a Farkas
     certificate) on the 5x5 grid and its infeasible twin (GPU FP64, GPU FP32
-    with the FP64 tail, and the FP64 oracle), and on the headline instance the
+    with the FP64 tail, each on the CUDA-graph engine and on the cluster
+    engine, and the FP64 oracle), and on the headline instance the
     residuals reached within a fixed budget of FP32 sweeps, with the oracle's
     residuals at the same early sweep beside the GPU's."""
     import oracle
@@ -787,10 +811,13 @@ def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
     g = I.grid5_k10(1.3, seed=0)
     for label, inst in (("grid5_k10_feasible_1.3x", g), ("grid5_k10_infeasible_0.6x", g.with_factor(0.6))):
         row = {}
-        for prec, code in (("gpu_fp64", pdr.PREC_FP64), ("gpu_fp32_fp64tail", pdr.PREC_FP32_FP64TAIL)):
+        for prec, code, engine in (("gpu_fp64", pdr.PREC_FP64, 1), ("gpu_fp32_fp64tail", pdr.PREC_FP32_FP64TAIL, 1),
+                                   ("gpu_fp64_cluster", pdr.PREC_FP64, 3),
+                                   ("gpu_fp32_fp64tail_cluster", pdr.PREC_FP32_FP64TAIL, 3)):
             with torch.cuda.stream(stream):
                 with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=code, eps_obj=0.0,
-                                              resid_tol=1e-6, eps_rel=1e-13, max_sweeps=600000) as sv:
+                                              resid_tol=1e-6, eps_rel=1e-13, max_sweeps=600000,
+                                              use_graph=engine) as sv:
                     sv.solve()  # warm-up (graph capture)
                     sv.reset()
                     r = sv.solve()
@@ -809,7 +836,7 @@ def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
         row["oracle_fp64"] = {"ms": dt * 1e3, "sweeps": rep["sweeps"], "cap_rel": res["cap_rel"],
                               "cons_rel": res["cons_rel"], "margin": res["margin"],
                               "verdict": {0: "unknown", 1: "feasible", 2: "infeasible"}[res["verdict"]]}
-        row["same_verdict"] = len({row[k]["verdict"] for k in ("gpu_fp64", "gpu_fp32_fp64tail", "oracle_fp64")}) == 1
+        row["same_verdict"] = len({v["verdict"] for v in row.values()}) == 1
         out[label] = row
     # the headline instance: residuals within a budget, and beside the oracle at sweep 3
     P = oracle.Problem.from_instance(big)
@@ -923,36 +950,9 @@ def batch_forms_block(pdr, torch, stream, big_batch, small_batch, flush):
 
 
 def adjoint_block(pdr, torch, stream, inst, T=50, ckpt=10):
-    """The differentiated form on digraph20k_k2000: L = z(f^(T)) and its gradient
-    w.r.t. u and d through T sweeps (checkpoints every ckpt) against the T
-    forward sweeps alone (FP32, CUDA events on the solver's stream)."""
-    import numpy as np
-
-    out = {"workload": WORKLOADS["digraph20k_k2000"], "T": T, "ckpt_every": ckpt, "dtype": "f32"}
-    with torch.cuda.stream(stream):
-        with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=pdr.PREC_FP32) as sv:
-            sv.backward(T, ckpt)  # warm-up
-            for key, grads in (("forward_only", False), ("forward_and_gradient", True)):
-                times = []
-                for _ in range(3):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    torch.cuda.synchronize()
-                    e0.record(stream)
-                    L, gu, gd = sv.backward(T, ckpt, grads=grads)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                out[key + "_ms"] = statistics.median(times)
-    out["gradient_over_forward"] = out["forward_and_gradient_ms"] / out["forward_only_ms"]
-    out["forward_updates_per_s"] = inst.m * inst.K * T / (out["forward_only_ms"] / 1e3)
-    out["L"] = L
-    out["euler_identity_rel"] = float(abs(np.dot(inst.u, gu) + np.dot(inst.d, gd) - 2 * L) / (2 * L))
-    extra_bytes = T * gradient_sweep_bytes(inst)
-    extra_ms = out["forward_and_gradient_ms"] - out["forward_only_ms"]
-    peak, peak_src = load_peaks()
-    out["gradient_roofline"] = {"bound": "hbm", "algorithmic_bytes": extra_bytes, "ms": extra_ms,
-                                "achieved": extra_bytes / (extra_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                                "peak_source": peak_src, "frac": extra_bytes / (extra_ms / 1e3) / 1e9 / peak}
+    """The differentiated form on digraph20k_k2000 (time_reverse_mode)."""
+    out = {"workload": WORKLOADS["digraph20k_k2000"]}
+    out.update(time_reverse_mode(pdr, torch, stream, inst, T, ckpt))
     return out
 
 

@@ -106,7 +106,13 @@ typedef struct {
                            QPs of every sweep, separated by grid barriers, for 1024 sweeps per
                            launch (PDR_ALGO_ESO with a lane-group edge variant, K <= 1024 in FP32
                            or 512 in FP64; otherwise 1 is used); a barrier that waits more than
-                           about a second ends the solve with PDR_ERR_TIMEOUT */
+                           about a second ends the solve with PDR_ERR_TIMEOUT.
+                           3: one thread-block cluster (1-8 blocks) runs the whole solve --
+                           excess pass, objective and stop test, edge QPs, separated by
+                           cluster barriers -- for 2048 sweeps per launch, as the batched
+                           form does for its small instances (PDR_ALGO_ESO or PDR_ALGO_CK,
+                           m x K <= 2^18 and a lane-group edge variant of at most 4 vectors
+                           per lane; otherwise 1 is used).  Same flows and sweeps as 1. */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */
@@ -424,8 +430,17 @@ pdr_status pdr_set_data(pdr_ctx *ctx, const double *u, const double *d);
  * (grad_d[K]) by reverse mode through the T sweeps (the derivatives of
  * eq. (3), (2), eq. "cpgrad" and of Alg. 2's active-set solution, or of the
  * capacity-kept projection for PDR_ALGO_CK; at a kink of max(0, .) or of an
- * active set, the derivative of the active set the forward took).  Flows are checkpointed every ckpt_every sweeps, so memory
- * is about (T/ckpt_every + ckpt_every) flow arrays.  Runs in the context's
+ * active set, the derivative of the active set the forward took).  Flows
+ * are checkpointed every ckpt_every sweeps and each segment's sweeps are
+ * recomputed on the way back, so the workspace is about (T/ckpt_every +
+ * ckpt_every) flow arrays plus ckpt_every height arrays.  ckpt_every = 1
+ * keeps every sweep's flows, heights and roots from the forward pass
+ * instead (T + 1 flow arrays and T height arrays) and recomputes nothing;
+ * the results are the same bit for bit.
+ * The context keeps that workspace after a call with gradients and reuses
+ * every buffer that is large enough, so later calls with the same T and
+ * ckpt_every allocate nothing; pdr_destroy frees it (and a failed call
+ * does).  Runs in the context's
  * working precision (FP32 or FP64; gradients accumulate in FP64) and leaves
  * f^(T) as the current flows.  grad_u and grad_d may be host or device
  * memory (the copy follows unified addressing); L is a host double.

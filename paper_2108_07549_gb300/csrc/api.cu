@@ -66,8 +66,8 @@ bool options_ok(const pdr_options* o, std::string* why)
         *why = "eps_obj, resid_tol and eps_rel must be finite";
         return false;
     }
-    if (o->use_graph < 0 || o->use_graph > 2) {
-        *why = "use_graph must be 0 (host loop), 1 (CUDA graph) or 2 (persistent kernel)";
+    if (o->use_graph < 0 || o->use_graph > 3) {
+        *why = "use_graph must be 0 (host loop), 1 (CUDA graph), 2 (persistent kernel) or 3 (cluster kernel)";
         return false;
     }
     if (o->max_sweeps < 0) {
@@ -186,6 +186,13 @@ struct pdr_ctx {
     long long barrier_ns = kBarrierNs;
     int hold_barrier = 0;
     int64_t t_widen = -1;  // t at which the FP64 tail of the last solve began (-1: none)
+    unsigned char* cl_args = nullptr;  // the cluster engine's arguments and instance id (device)
+    // reverse-mode workspace (pdr_backward: checkpoints, segment states,
+    // cotangents), kept for later calls: the i-th buffer a call asks for is
+    // reused when it is large enough, so calls with the same T, checkpoint
+    // interval and precision allocate nothing.  Freed by pdr_destroy, and
+    // after a failed pdr_backward.
+    std::vector<std::pair<void*, size_t>> adj_ws;
 
     pdr_status fail(pdr_status code, const std::string& msg)
     {
@@ -726,6 +733,63 @@ pdr_status widen_to_fp64(pdr_ctx* ctx)
 }
 
 constexpr int64_t kPersistChunk = 1024;  // sweeps per persistent launch (even)
+constexpr int64_t kBlockElems = int64_t(1) << 18;  // m x Kp up to which one cluster solves an instance
+constexpr int64_t kBlockChunk = 2048;              // sweeps per launch of the cluster kernel
+
+// Blocks of the thread-block cluster that runs an instance's whole solve:
+// enough that each lane group handles at most 16 edges per sweep (1..8).
+int batch_cluster_size(const pdr_ctx* c, int p);
+
+// The cluster engine (use_graph = 3, and the batched form's small
+// instances) applies to Alg. 1 and Program (6) on a small instance whose
+// edge variant is a lane-group form of at most 4 vectors per lane.
+bool cluster_eligible(const pdr_ctx* ctx, int p)
+{
+    const int cfg = ctx->cfg[p];
+    return !is_gd(ctx->opt) && ctx->m > 0 && ctx->m * (int64_t)ctx->Kp <= kBlockElems && batch_block_config(cfg) &&
+           edge_plain_config(cfg) <= 5;
+}
+
+// Alg. 1 by the cluster kernel (use_graph = 3): one thread-block cluster runs
+// the excess pass, the objective and stop test and the edge QPs of every
+// sweep, separated by cluster barriers, for kBlockChunk sweeps per launch
+// until the stop rules fire; the flows start in buffer 0.  The per-element
+// arithmetic is the standalone kernels' (the batched form's engine, with one
+// instance).
+template <typename T>
+pdr_status run_cluster(pdr_ctx* ctx, int64_t t_start)
+{
+    const int p = Prec<T>::id;
+    if (!ctx->cl_args) {
+        pdr_status st = PDR_OK;
+        ctx->cl_args = dalloc<unsigned char>(ctx, sizeof(SweepArgs<double>) + 64, &st);
+        if (!ctx->cl_args) return st;
+    }
+    SweepArgs<T>* dargs = reinterpret_cast<SweepArgs<T>*>(ctx->cl_args);
+    int* dids = reinterpret_cast<int*>(ctx->cl_args + sizeof(SweepArgs<double>) + 32);
+    CK(cudaMemsetAsync(dids, 0, sizeof(int), ctx->stream));  // the instance id: 0, its arguments at dargs[0]
+    const int csize = batch_cluster_size(ctx, p);
+    for (bool first = true;; first = false) {
+        const int par = first ? 0 : (int)((ctx->hst->t - t_start) & 1);
+        SweepArgs<T> a = make_args<T>(ctx, MODE_SOLVE, 0, 0, par, 0);
+        a.excess_form = 0;  // the gather form, run by the cluster's blocks
+        a.grid_v = csize;
+        a.grid_e = csize;
+        a.n_psi = csize * (kBatchThreads / 32);
+        a.pf_edges = 0;
+        a.l2_hints = 0;
+        a.active = nullptr;
+        CK(cudaMemcpyAsync(dargs, &a, sizeof(a), cudaMemcpyHostToDevice, ctx->stream));
+        CK(launch_batch_block<T>(edge_plain_config(ctx->cfg[p]), dargs, dids, 1, csize, kBlockChunk, first ? 1 : 0,
+                                 ctx->stream));
+        const pdr_status s = read_state(ctx);  // synchronises the stream
+        if (s != PDR_OK) return s;
+        if (ctx->hst->stop) break;
+    }
+    ctx->cur = (int)((ctx->hst->t - t_start) & 1);
+    // the current flows' congestion partials in the standalone kernels' layout
+    return refresh_psi<T>(ctx, nullptr, true);
+}
 
 // The persistent engine applies to Alg. 1 with a lane-group variant.
 bool persistent_ok(const pdr_ctx* ctx, int p)
@@ -798,6 +862,7 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     if (s != PDR_OK) return s;
     s = flows_to_buffer0<T>(ctx);
     if (s != PDR_OK) return s;
+    if (ctx->opt.use_graph == 3 && cluster_eligible(ctx, p)) return run_cluster<T>(ctx, t_start);
     if (persistent_ok(ctx, p)) {
         bool ran = false;
         s = run_persistent<T>(ctx, &ran);
@@ -950,6 +1015,13 @@ std::string validate_instance(int32_t n, int64_t m, const int64_t* row_ptr, cons
 }
 
 
+void release_adjoint_workspace(pdr_ctx* ctx)
+{
+    for (auto& w : ctx->adj_ws)
+        if (w.first) cudaFree(w.first);
+    ctx->adj_ws.clear();
+}
+
 // Reverse mode through T sweeps (pdr_backward), precision T.
 template <typename T>
 pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* grad_u, double* grad_d)
@@ -958,19 +1030,29 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     const size_t mm = (size_t)(ctx->m > 0 ? ctx->m : 1);
     const int64_t nseg = Tn > 0 ? (Tn + C - 1) / C : 0;
     const bool grads = grad_u || grad_d;
-    std::vector<void*> owned;
+    // ckpt_every = 1: the forward pass keeps every sweep's flows f^(0..T),
+    // heights h^(0..T-1) and roots (with the warm starts they leave), each
+    // sweep writing its own buffers, so the backward pass recomputes nothing
+    const bool keep_all = grads && C == 1;
     pdr_status st = PDR_OK;
-    auto cleanup = [&]() {
-        for (void* q : owned) cudaFree(q);
-    };
-    auto grab = [&](size_t bytes) -> void* {
-        void* q = nullptr;
-        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
+    auto cleanup = [&]() { release_adjoint_workspace(ctx); };  // failure paths only
+    size_t slot = 0;
+    auto grab = [&](size_t bytes) -> void* {  // the next buffer of the kept workspace
+        if (bytes == 0) bytes = 1;
+        if (slot == ctx->adj_ws.size()) ctx->adj_ws.push_back({nullptr, 0});
+        auto& w = ctx->adj_ws[slot];
+        if (w.second < bytes) {
+            if (w.first) cudaFree(w.first);
+            w = {nullptr, 0};
+            void* q = nullptr;
+            if (cudaMalloc(&q, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            w = {q, bytes};
         }
-        owned.push_back(q);
-        return q;
+        ++slot;
+        return w.first;
     };
 #define CKB(call)                                        \
     do {                                                 \
@@ -981,8 +1063,16 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             return st;                                   \
         }                                                \
     } while (0)
-    // checkpoints of the flows and of the roots and warm starts at t = 0, C, 2C, ...
-    std::vector<T*> ck(grads ? nseg : 0), thck(grads ? nseg : 0), seg, th, hseg;
+    std::vector<T*> fs(keep_all ? Tn + 1 : 0), hs(keep_all ? Tn : 0), ths(keep_all ? Tn : 0);
+    for (auto& q : fs)
+        if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "sweep-state allocation failed");
+    for (auto& q : hs)
+        if (!(q = (T*)grab(sizeof(T) * hn))) return cleanup(), ctx->fail(PDR_ERR_OOM, "sweep-state allocation failed");
+    for (auto& q : ths)
+        if (!(q = (T*)grab(sizeof(T) * 2 * mm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "sweep-state allocation failed");
+    // otherwise checkpoints of the flows and of the roots and warm starts at t = 0, C, 2C, ...
+    const bool ckpt = grads && !keep_all;
+    std::vector<T*> ck(ckpt ? nseg : 0), thck(ckpt ? nseg : 0), seg, th, hseg;
     for (auto& q : ck)
         if (!(q = (T*)grab(sizeof(T) * fm))) return cleanup(), ctx->fail(PDR_ERR_OOM, "checkpoint allocation failed");
     for (auto& q : thck)
@@ -990,7 +1080,7 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     T *fbar = nullptr, *cbar = nullptr, *Dbar = nullptr;
     double *ubar = nullptr, *dbar = nullptr;
     uint32_t* mask = nullptr;
-    if (grads) {
+    if (ckpt) {
         seg.resize(C + 1);
         th.resize(C);
         for (auto& q : seg)
@@ -1000,6 +1090,8 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
         hseg.resize(C);  // the heights of every sweep of a segment, kept from its recomputation
         for (auto& q : hseg)
             if (!(q = (T*)grab(sizeof(T) * hn))) return cleanup(), ctx->fail(PDR_ERR_OOM, "segment allocation failed");
+    }
+    if (grads) {
         fbar = (T*)grab(sizeof(T) * fm);
         cbar = (T*)grab(sizeof(T) * fm);
         Dbar = (T*)grab(sizeof(T) * hn);
@@ -1010,7 +1102,26 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
             return cleanup(), ctx->fail(PDR_ERR_OOM, "adjoint allocation failed");
     }
     // forward from f = 0 (pdr_backward reset the flows), cold roots
-    for (int64_t t = 0; t < Tn; ++t) {
+    if (keep_all) {
+        CKB(cudaMemcpyAsync(fs[0], Prec<T>::f(ctx, ctx->cur), sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int64_t t = 0; t < Tn; ++t) {
+            SweepArgs<T> a = make_args<T>(ctx, MODE_FORCED);
+            a.f = fs[t];
+            a.f_out = fs[t + 1];
+            a.h = hs[t];
+            if (t > 0) a.theta_in = ths[t - 1];
+            a.theta = ths[t];
+            CKB(launch_excess<T>(a, ctx->stream));
+            CKB(launch_edge<T>(a, ctx->cfg[Prec<T>::id], ctx->stream));
+        }
+        if (Tn > 0) {  // f^(T) and the last roots become the current state
+            CKB(cudaMemcpyAsync(Prec<T>::f(ctx, ctx->cur), fs[Tn], sizeof(T) * fm, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+            CKB(cudaMemcpyAsync(ctx->theta[ctx->cur], ths[Tn - 1], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+        }
+    }
+    for (int64_t t = 0; !keep_all && t < Tn; ++t) {
         if (grads && t % C == 0) {  // the flows and the warm starts sweep t reads
             CKB(cudaMemcpyAsync(ck[t / C], Prec<T>::f(ctx, ctx->cur), sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
             CKB(cudaMemcpyAsync(thck[t / C], ctx->theta[ctx->cur], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice,
@@ -1031,8 +1142,16 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     st = read_state(ctx);
     if (st != PDR_OK) return cleanup(), st;
     if (L) *L = ctx->hst->z;
-    // backward, segment by segment from the last
-    for (int64_t sgi = nseg - 1; grads && sgi >= 0; --sgi) {
+    // backward from the kept sweeps
+    for (int64_t t = Tn - 1; keep_all && t >= 0; --t) {
+        SweepArgs<T> a = make_args<T>(ctx, MODE_EVAL);
+        a.f = fs[t];
+        a.h = hs[t];
+        CKB(launch_backward_sweep<T>(a, ths[t], fbar, cbar, Dbar, ubar, dbar, mask, t == Tn - 1 ? 0 : 1,
+                                     ctx->num_sms, ctx->stream));
+    }
+    // or segment by segment from the last
+    for (int64_t sgi = nseg - 1; ckpt && sgi >= 0; --sgi) {
         const int64_t t0 = sgi * C, t1 = (t0 + C < Tn) ? t0 + C : Tn;
         CKB(cudaMemcpyAsync(seg[0], ck[sgi], sizeof(T) * fm, cudaMemcpyDeviceToDevice, ctx->stream));
         CKB(cudaMemcpyAsync(ctx->theta[0], thck[sgi], sizeof(T) * 2 * ctx->m, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1064,7 +1183,10 @@ pdr_status backward_T(pdr_ctx* ctx, int64_t Tn, int32_t C, double* L, double* gr
     if (grad_d) CKB(cudaMemcpyAsync(grad_d, dbar, sizeof(double) * ctx->K, cudaMemcpyDefault, ctx->stream));
     CKB(cudaStreamSynchronize(ctx->stream));
 #undef CKB
-    cleanup();
+    // a time limit that ran out in a kernel of the recomputed segments or of
+    // the backward pass
+    st = read_state(ctx);
+    if (st != PDR_OK) return cleanup(), st;
     // f^(T) stays the current flows; partials and state follow it
     st = refresh_psi<T>(ctx);
     if (st != PDR_OK) return st;
@@ -1097,9 +1219,10 @@ void pdr_destroy(pdr_ctx* ctx)
                    ctx->beta_buf[0], ctx->beta_buf[1], ctx->v32[0], ctx->v32[1], ctx->v64[0], ctx->v64[1],
                    ctx->r_h64, ctx->r_part, ctx->r_out, ctx->psi_tmp, ctx->bar, ctx->xv_start[1], ctx->xv_start[2], ctx->xv_start[3],
                    ctx->xv_start[4], ctx->xv_start[5],
-                   ctx->data_err};
+                   ctx->data_err, ctx->cl_args};
     for (void* p : dev)
         if (p) cudaFree(p);
+    release_adjoint_workspace(ctx);
     if (ctx->hst) cudaFreeHost(ctx->hst);
     if (ctx->hr_out) cudaFreeHost(ctx->hr_out);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -2138,7 +2261,6 @@ struct pdr_batch {
     std::vector<char> graph_mask[2];
     bool graph_tried[2] = {false, false}, graph_ok[2] = {false, false};
     // one-block-per-instance engine: the instances one block solves at speed
-    std::vector<char> small;              // size test passed (precision-independent part)
     void* bargs[2] = {nullptr, nullptr};  // device SweepArgs<float> / <double> [count]
     int* bids = nullptr;                  // device instance ids [count], grouped by variant
     void* hstage = nullptr;               // pinned staging of the arguments and ids
@@ -2147,8 +2269,6 @@ struct pdr_batch {
 namespace {
 
 constexpr int kBatchUnroll = 2;  // sweeps per instance per iteration of the batch's while loop
-constexpr int64_t kBlockElems = int64_t(1) << 18;  // m x Kp up to which one block solves an instance
-constexpr int64_t kBlockChunk = 2048;              // sweeps per launch of the one-block-per-instance kernel
 constexpr int kBatchPool = 32;   // capture streams
 
 pdr_status batch_fail(pdr_status code, const std::string& msg)
@@ -2325,15 +2445,11 @@ int batch_cluster_size(const pdr_ctx* c, int p)
     return cs;
 }
 
-// True if instance i runs on the one-block-per-instance engine in precision
-// p: a lane-group variant of at most 4 vectors per lane (the larger ones
-// spill at the block's register budget) and a small instance.
-bool batch_resident(const pdr_batch* b, int32_t i, int p)
-{
-    if (!b->small[i]) return false;
-    const int cfg = b->ctx[i]->cfg[p];
-    return batch_block_config(cfg) && edge_plain_config(cfg) <= 5;
-}
+// True if instance i runs on the one-cluster-per-instance engine in
+// precision p (cluster_eligible: a small instance with a lane-group variant
+// of at most 4 vectors per lane; the larger ones spill at the block's
+// register budget).
+bool batch_resident(const pdr_batch* b, int32_t i, int p) { return cluster_eligible(b->ctx[i], p); }
 
 // The instances of `blk` (set up by batch_run) on the one-block-per-instance
 // engine: launches of kBlockChunk sweeps, one per edge-kernel variant on its
@@ -2561,11 +2677,6 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance* inst, const pdr_o
     }
     b->tuned_cfg.assign(count, -1);
     b->tuned_us.assign(count, -1.0);
-    b->small.assign(count, 0);
-    for (int32_t i = 0; i < count; ++i) {
-        const pdr_ctx* c = b->ctx[i];
-        b->small[i] = !is_gd(o) && c->m > 0 && c->m * (int64_t)c->Kp <= kBlockElems;
-    }
     for (int p = 0; p < 2; ++p)
         if (cudaMalloc(&b->bargs[p], sizeof(SweepArgs<double>) * count) != cudaSuccess) {
             cudaGetLastError();

@@ -126,6 +126,96 @@ def test_capacity_kept_reverse_mode_matches_oracle(pdr, prec):
             assert worst <= 1.0, (inst.name, worst)
 
 
+def test_kept_workspace_gives_the_same_gradients(pdr):
+    """The context keeps the reverse-mode workspace between calls: a second
+    call reuses it, a call with another T and checkpoint interval reuses
+    what fits and grows the rest, and each gives the gradients of a fresh
+    context bit for bit."""
+    inst = block_cases()[0]
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32) as s:
+        first = s.backward(9, 4)
+        again = s.backward(9, 4)
+        other = s.backward(13, 3)
+    with pdr.Solver.from_instance(inst, precision=pdr.PREC_FP32) as s:
+        fresh = s.backward(13, 3)
+    for a, b in ((first, again), (other, fresh)):
+        assert a[0] == b[0]
+        np.testing.assert_array_equal(a[1], b[1])
+        np.testing.assert_array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_keep_every_sweep_equals_checkpointed(pdr, prec):
+    """ckpt_every = 1 keeps every sweep of the forward pass instead of
+    recomputing segments; the gradients are the checkpointed ones bit for
+    bit (the recomputation is deterministic), also for T = 0 and T = 1."""
+    p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
+    for inst in (cases()[2], block_cases()[1]):
+        for T, C in ((0, 3), (1, 3), (11, 4)):
+            with pdr.Solver.from_instance(inst, precision=p) as s:
+                a = s.backward(T, C)
+                fa = s.flows()
+                b = s.backward(T, 1)
+                fb = s.flows()
+            assert a[0] == b[0], (inst.name, T)
+            np.testing.assert_array_equal(a[1], b[1])
+            np.testing.assert_array_equal(a[2], b[2])
+            np.testing.assert_array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vertex_step_equal_in_every_excess_form(pdr, prec):
+    """The backward vertex step runs through the context's excess form (the
+    gather kernel for form 0, the bulk-copy forms 1..5 otherwise), in the
+    same incidence order: both gradients equal form 0's.  L is the
+    objective's cross-block reduction, whose order follows each form's grid:
+    equal to rounding."""
+    p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
+    for inst in (cases()[3], block_cases()[1]):
+        res = {}
+        for form in range(6):
+            with pdr.Solver.from_instance(inst, precision=p, excess_variant=form) as s:
+                res[form] = s.backward(9, 4)
+        for form in range(1, 6):
+            # FP32 partials are summed as compensated pairs (about 44 bits)
+            tol = 1e-14 if prec == "fp64" else 1e-11
+            assert abs(res[form][0] - res[0][0]) <= tol * res[0][0], (inst.name, form)
+            np.testing.assert_array_equal(res[form][1], res[0][1])
+            np.testing.assert_array_equal(res[form][2], res[0][2])
+
+
+def block_cases():
+    """Rows long enough for the block form of the backward edge step (more
+    than 64 vectors of the row): K = 601 (ragged: padded to 604) takes the
+    128 x 2 form in FP32 and 128 x 4 in FP64; K = 1500 takes 128 x 4 and
+    256 x 4."""
+    rng = np.random.default_rng(23)
+    return [jittered(I.make_instance("grid6_k601", I.grid_graph(6), 601, ("lognormal", 1.0, 0.5), 1.1, rng), 5),
+            jittered(I.make_instance("dg60_k1500", I.random_digraph(60, 3, rng), 1500, ("uniform_int", 1, 9), 0.9,
+                                     rng), 6)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("algo", ["eso", "ck"])
+def test_block_form_reverse_mode_matches_oracle(pdr, prec, algo):
+    """The block form against the oracle's reverse mode (Alg. 2 and Program
+    (6)): FP64 to 1e-9, FP32 to 1e-4 element by element."""
+    p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
+    for inst in block_cases():
+        ref = oracle.Problem.from_instance(inst)
+        Lr, gur, gdr = ref.adjoint_eso(12) if algo == "eso" else ref.adjoint_ck(12)
+        with pdr.Solver.from_instance(inst, precision=p, algo=pdr.ALGO_ESO if algo == "eso" else pdr.ALGO_CK) as s:
+            L, gu, gd = s.backward(12, 5)
+        if prec == "fp64":
+            assert abs(L - Lr) <= 1e-12 * Lr
+            np.testing.assert_allclose(gd, gdr, rtol=1e-9, atol=1e-12 * np.abs(gdr).max())
+            np.testing.assert_allclose(gu, gur, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(gur).max()))
+        else:
+            assert abs(L - Lr) <= 1e-5 * Lr
+            worst = elementwise_close(np.concatenate([gu, gd]), np.concatenate([gur, gdr]))
+            assert worst <= 1.0, (inst.name, worst)
+
+
 def test_torch_autograd_function(pdr):
     import torch
 
