@@ -479,11 +479,16 @@ typedef struct {
 pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_options *opt, void *stream,
                             pdr_batch **out);
 
-/* Solves every instance from its current state with one CUDA graph launch:
- * a conditional while loop whose body holds one chain of sweeps per
- * instance; the chains are independent, so the instances run concurrently.
- * Each instance stops by its own stop rules (a stopped instance's kernels
- * return at once); the loop ends when the last one stops.  With
+/* Solves every instance from its current state.  Small instances (m x K <=
+ * 2^18 on a lane-group variant of at most 4 vectors per lane, Alg. 1 or
+ * Program (6)) run their whole solve on one thread-block cluster each, in
+ * shared launches of the cluster kernel (engine 3 of pdr_options.use_graph).
+ * The others run in one CUDA graph launch: a conditional while loop whose
+ * body holds one chain of sweeps per instance; the chains are independent,
+ * so the instances run concurrently.  Each instance stops by its own stop
+ * rules (a stopped instance's kernels return at once); the loop ends when
+ * the last one stops.  The flows equal, bit for bit, single-instance solves
+ * with the same edge variant.  With
  * PDR_PREC_FP32_FP64TAIL a second launch then runs FP64 sweeps for the
  * instances whose FP32 phase stopped on the objective rules (as pdr_solve
  * does for one instance).  Then each instance's residuals and verdict are
