@@ -348,16 +348,8 @@ cudaError_t launch_backward_sweep(const SweepArgs<T>& a, const T* theta, const T
         if (fused) edge_backward_kernel<T, true><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
         else edge_backward_kernel<T, false><<<ge, kThreads, 0, s>>>(a, theta, fbar, cbar, Dbar, ubar, mask);
     }
-    if (a.excess_form >= 1) {  // the bulk-copy form of the excess pass, in incidence order as the gather below
-        SweepArgs<T> v = a;
-        v.f = cbar;
-        v.h = Dbar;
-        const cudaError_t e = launch_excess_adjoint<T>(v, s);
-        if (e != cudaSuccess) return e;
-    } else {
-        vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
-            a, cbar, Dbar);
-    }
+    vertex_backward_kernel<T><<<blocks((int64_t)a.n * (a.Kp / VecOf<T>::N), kThreads, num_sms), kThreads, 0, s>>>(
+        a, cbar, Dbar);
     demand_kernel<T><<<blocks(a.K, kThreads, num_sms), kThreads, 0, s>>>(a, Dbar, dbar, 1);
     return cudaGetLastError();
 }

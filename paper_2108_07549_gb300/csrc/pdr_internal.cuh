@@ -203,10 +203,6 @@ int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms);  // 0: 
 // instance: instances ids[0..count) of args run up to `sweeps` sweeps each
 // with the lane-group variant cfg (true for batch_block_config);
 // psi_prologue: first launch of a solve.
-// The reverse mode's vertex step (dL/dDelta from dL/dc in a.f, into a.h)
-// through the context's bulk-copy excess form a.excess_form (1..5).
-template <typename T>
-cudaError_t launch_excess_adjoint(const SweepArgs<T>& a, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
                                int psi_prologue, cudaStream_t stream);

@@ -219,11 +219,8 @@ constexpr size_t excess_bulk_smem()
     return (size_t)S * R * xseg_bytes<C>() + (size_t)S * (2 * sizeof(uint64_t) + sizeof(XDesc));
 }
 
-// S stages of R row segments of C x 16 bytes.  ADJ: the reverse mode's
-// vertex step instead, dL/dDelta_i = (sum_out - sum_in of the rows of a.f,
-// here the cotangents dL/dc) / (2 delta_i) into a.h, in the same incidence
-// order: no demand term, no objective partials, no solver state.
-template <typename T, int S, int R, int C, bool ADJ = false>
+// S stages of R row segments of C x 16 bytes
+template <typename T, int S, int R, int C>
 __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
 {
     using VT = typename VecOf<T>::type;
@@ -272,7 +269,7 @@ __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
         wb0 = __shfl_sync(kFull, ip0, 0);
         cur0 = wb0 + lane < ninc ? a.inc[wb0 + lane] : 0;
         nxt0 = wb0 + 32 + lane < ninc ? a.inc[wb0 + 32 + lane] : 0;
-    } else if (mine && !ADJ) {
+    } else if (mine) {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             sk[q] = a.s[tid * N + q];
@@ -284,11 +281,9 @@ __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
 
     pdl_wait();
     pdl_trigger();  // one wave
-    if constexpr (!ADJ) {
-        volatile DevState* vst = a.st;
-        if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
-        if (block == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
-    }
+    volatile DevState* vst = a.st;
+    if (sweep_stopped(a)) return;  // an earlier sweep of this solve stopped
+    if (block == 0 && threadIdx.x == 0) a.st->t_sweep = vst->t;
 
     typename A::V zacc = A::zero();
     T cons = T(0);
@@ -397,7 +392,7 @@ __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
                 cs = d.c;
                 const int k0 = cs * W + tid * N;
                 mine = k0 < a.Kp && tid * N < W;
-                if (mine && !ADJ) {
+                if (mine) {
 #pragma unroll
                     for (int q = 0; q < N; ++q) {
                         sk[q] = a.s[k0 + q];
@@ -423,15 +418,7 @@ __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
-            if ((d.flags & kXLast) && mine && ADJ) {
-                // acc = sum_in - sum_out, and -1/(2 delta) is exact: the
-                // values of the gather form's (sum_out - sum_in) * (1/(2 delta))
-                const T sc = T(-0.5) * (T)d.idg;
-                T hv[N];
-#pragma unroll
-                for (int q = 0; q < N; ++q) hv[q] = acc[q] * sc;
-                reinterpret_cast<VT*>(a.h + (int64_t)d.i * a.Kp + cs * W + tid * N)[0] = pack4(hv);
-            } else if ((d.flags & kXLast) && mine) {
+            if ((d.flags & kXLast) && mine) {
                 const int32_t i = d.i;
 #pragma unroll
                 for (int q = 0; q < N; ++q) {
@@ -458,10 +445,10 @@ __global__ void __launch_bounds__(C + 32) excess_bulk_kernel(SweepArgs<T> a)
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) {
             a.st->fault = 1;
-            if (!ADJ) stop_from_kernel(a);
+            stop_from_kernel(a);
         }
     }
-    if constexpr (!ADJ) excess_tail<T>(a, block, gridDim.x, zacc, cons);
+    excess_tail<T>(a, block, gridDim.x, zacc, cons);
 }
 
 // xv_start[b] = the first vertex i with inc_ptr[i] + 2 i >= b * (inc_ptr[n] + 2 n) / grid
@@ -1591,33 +1578,6 @@ cudaError_t launch_excess(const SweepArgs<T>& a, cudaStream_t stream, bool pdl)
     default: return launch_one<T>(excess_kernel<T>, a.grid_v, kThreads, stream, pdl, a);
     }
 }
-
-// The reverse mode's vertex step through the bulk-copy form `form` (1..5) of
-// the excess pass (a.f = dL/dc, a.h = dL/dDelta, the form's vertex split).
-template <typename T, int S, int R, int C>
-cudaError_t launch_bulk_adjoint(const SweepArgs<T>& a, cudaStream_t stream)
-{
-    const size_t smem = excess_bulk_smem<S, R, C>();
-    const cudaError_t e =
-        cudaFuncSetAttribute(excess_bulk_kernel<T, S, R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return launch_one<T>(excess_bulk_kernel<T, S, R, C, true>, a.grid_v, C + 32, stream, false, a, smem);
-}
-
-template <typename T>
-cudaError_t launch_excess_adjoint(const SweepArgs<T>& a, cudaStream_t stream)
-{
-    switch (a.excess_form) {
-    case 1: return launch_bulk_adjoint<T, 4, 8, 128>(a, stream);
-    case 2: return launch_bulk_adjoint<T, 2, 8, 128>(a, stream);
-    case 3: return launch_bulk_adjoint<T, 4, 4, 128>(a, stream);
-    case 4: return launch_bulk_adjoint<T, 2, 8, 32>(a, stream);
-    case 5: return launch_bulk_adjoint<T, 4, 8, 32>(a, stream);
-    default: return cudaErrorInvalidValue;
-    }
-}
-template cudaError_t launch_excess_adjoint<float>(const SweepArgs<float>&, cudaStream_t);
-template cudaError_t launch_excess_adjoint<double>(const SweepArgs<double>&, cudaStream_t);
 
 template <typename T, int S, int R, int C>
 int bulk_resident()

@@ -163,27 +163,6 @@ def test_keep_every_sweep_equals_checkpointed(pdr, prec):
             np.testing.assert_array_equal(fa, fb)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_vertex_step_equal_in_every_excess_form(pdr, prec):
-    """The backward vertex step runs through the context's excess form (the
-    gather kernel for form 0, the bulk-copy forms 1..5 otherwise), in the
-    same incidence order: both gradients equal form 0's.  L is the
-    objective's cross-block reduction, whose order follows each form's grid:
-    equal to rounding."""
-    p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
-    for inst in (cases()[3], block_cases()[1]):
-        res = {}
-        for form in range(6):
-            with pdr.Solver.from_instance(inst, precision=p, excess_variant=form) as s:
-                res[form] = s.backward(9, 4)
-        for form in range(1, 6):
-            # FP32 partials are summed as compensated pairs (about 44 bits)
-            tol = 1e-14 if prec == "fp64" else 1e-11
-            assert abs(res[form][0] - res[0][0]) <= tol * res[0][0], (inst.name, form)
-            np.testing.assert_array_equal(res[form][1], res[0][1])
-            np.testing.assert_array_equal(res[form][2], res[0][2])
-
-
 def block_cases():
     """Rows long enough for the block form of the backward edge step (more
     than 64 vectors of the row): K = 601 (ragged: padded to 604) takes the

@@ -137,4 +137,4 @@ def test_switching_engines_mid_solve(pdr):
 
 def test_option_validation(pdr):
     with pytest.raises(pdr.PdrError):
-        pdr.Solver.from_instance(small_instances()[0], use_graph=3)
+        pdr.Solver.from_instance(small_instances()[0], use_graph=4)  # engines are 0..3
