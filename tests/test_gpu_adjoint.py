@@ -145,14 +145,17 @@ def test_kept_workspace_gives_the_same_gradients(pdr):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_keep_every_sweep_equals_checkpointed(pdr, prec):
+@pytest.mark.parametrize("algo", ["eso", "ck"])
+def test_keep_every_sweep_equals_checkpointed(pdr, prec, algo):
     """ckpt_every = 1 keeps every sweep of the forward pass instead of
     recomputing segments; the gradients are the checkpointed ones bit for
-    bit (the recomputation is deterministic), also for T = 0 and T = 1."""
+    bit (the recomputation is deterministic), also for T = 0 and T = 1, for
+    Alg. 2 and for the capacity-kept step of Program (6)."""
     p = pdr.PREC_FP64 if prec == "fp64" else pdr.PREC_FP32
+    alg = pdr.ALGO_ESO if algo == "eso" else pdr.ALGO_CK
     for inst in (cases()[2], block_cases()[1]):
         for T, C in ((0, 3), (1, 3), (11, 4)):
-            with pdr.Solver.from_instance(inst, precision=p) as s:
+            with pdr.Solver.from_instance(inst, precision=p, algo=alg) as s:
                 a = s.backward(T, C)
                 fa = s.flows()
                 b = s.backward(T, 1)
