@@ -112,7 +112,11 @@ typedef struct {
                            cluster barriers -- for 2048 sweeps per launch, as the batched
                            form does for its small instances (PDR_ALGO_ESO or PDR_ALGO_CK,
                            m x K <= 2^18 and a lane-group edge variant of at most 4 vectors
-                           per lane; otherwise 1 is used).  Same flows and sweeps as 1. */
+                           per lane; otherwise 1 is used).  An instance that one block solves
+                           and whose arrays fit in 100 KB of shared memory (flows, heights,
+                           roots, partials, state and the read-only arrays of a sweep) is
+                           solved there, copied in and out once per launch.  Same flows and
+                           sweeps as 1. */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */
@@ -482,8 +486,8 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_o
 /* Solves every instance from its current state.  Small instances (m x K <=
  * 2^18 on a lane-group variant of at most 4 vectors per lane, Alg. 1 or
  * Program (6)) run their whole solve on one thread-block cluster each, in
- * shared launches of the cluster kernel (engine 3 of pdr_options.use_graph).
- * The others run in one CUDA graph launch: a conditional while loop whose
+ * shared launches of the cluster kernel (engine 3 of pdr_options.use_graph,
+ * with its shared-memory form for the instances that fit).  The others run in one CUDA graph launch: a conditional while loop whose
  * body holds one chain of sweeps per instance; the chains are independent,
  * so the instances run concurrently.  Each instance stops by its own stop
  * rules (a stopped instance's kernels return at once); the loop ends when

@@ -740,6 +740,18 @@ constexpr int64_t kBlockChunk = 2048;              // sweeps per launch of the c
 // enough that each lane group handles at most 16 edges per sweep (1..8).
 int batch_cluster_size(const pdr_ctx* c, int p);
 
+// Shared memory of the one-block engine's shared-memory form for instance c
+// in precision p, or 0 where it does not apply (a cluster of several blocks,
+// or more than kBlockSmemMax bytes).
+int64_t block_smem(const pdr_ctx* c, int p)
+{
+    if (batch_cluster_size(c, p) != 1) return 0;
+    const int64_t n_psi = kBatchThreads / 32;
+    const int64_t b = p == Prec<double>::id ? block_smem_bytes<double>(c->n, c->m, c->Kp, n_psi)
+                                         : block_smem_bytes<float>(c->n, c->m, c->Kp, n_psi);
+    return b <= kBlockSmemMax ? b : 0;
+}
+
 // The cluster engine (use_graph = 3, and the batched form's small
 // instances) applies to Alg. 1 and Program (6) on a small instance whose
 // edge variant is a lane-group form of at most 4 vectors per lane.
@@ -781,7 +793,7 @@ pdr_status run_cluster(pdr_ctx* ctx, int64_t t_start)
         a.active = nullptr;
         CK(cudaMemcpyAsync(dargs, &a, sizeof(a), cudaMemcpyHostToDevice, ctx->stream));
         CK(launch_batch_block<T>(edge_plain_config(ctx->cfg[p]), dargs, dids, 1, csize, kBlockChunk, first ? 1 : 0,
-                                 ctx->stream));
+                                 ctx->stream, block_smem(ctx, p)));
         const pdr_status s = read_state(ctx);  // synchronises the stream
         if (s != PDR_OK) return s;
         if (ctx->hst->stop) break;
@@ -2495,20 +2507,30 @@ pdr_status batch_block_run(pdr_batch* b, const std::vector<char>& blk, const std
             a.active = nullptr;
             hargs[i] = a;
         }
-        // one launch per (lane-group variant, cluster size), largest clusters first
+        // one launch per (lane-group variant, cluster size, form), largest
+        // clusters first; single blocks whose instance fits in shared memory
+        // run the shared-memory form, with the largest of their sizes
         struct Group {
             int cfg, csize, off, count;
+            int64_t smem;
         };
         std::vector<Group> groups;
         int pos = 0;
         for (int csize = 8; csize >= 1; csize >>= 1)
-            for (int cfg = 0; cfg <= 5; ++cfg) {
-                const int off = pos;
-                for (int32_t i : live)
-                    if (edge_plain_config(b->ctx[i]->cfg[p]) == cfg && batch_cluster_size(b->ctx[i], p) == csize)
+            for (int cfg = 0; cfg <= 5; ++cfg)
+                for (int sm = 0; sm < (csize == 1 ? 2 : 1); ++sm) {
+                    const int off = pos;
+                    int64_t smem = 0;
+                    for (int32_t i : live) {
+                        const pdr_ctx* c = b->ctx[i];
+                        if (edge_plain_config(c->cfg[p]) != cfg || batch_cluster_size(c, p) != csize) continue;
+                        const int64_t need = csize == 1 ? block_smem(c, p) : 0;
+                        if ((need > 0) != (sm == 1)) continue;
                         hids[pos++] = i;
-                if (pos > off) groups.push_back({cfg, csize, off, pos - off});
-            }
+                        smem = need > smem ? need : smem;
+                    }
+                    if (pos > off) groups.push_back({cfg, csize, off, pos - off, smem});
+                }
         cudaError_t e = cudaMemcpyAsync(dargs, hargs, sizeof(SweepArgs<T>) * b->count, cudaMemcpyHostToDevice,
                                         b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->bids, hids, sizeof(int) * pos, cudaMemcpyHostToDevice, b->stream);
@@ -2525,7 +2547,7 @@ pdr_status batch_block_run(pdr_batch* b, const std::vector<char>& blk, const std
             e = cudaStreamWaitEvent(sg, ev[0], 0);
             if (e == cudaSuccess)
                 e = launch_batch_block<T>(groups[g].cfg, dargs, b->bids + groups[g].off, groups[g].count, groups[g].csize,
-                                          kBlockChunk, first ? 1 : 0, sg);
+                                          kBlockChunk, first ? 1 : 0, sg, groups[g].smem);
             if (e == cudaSuccess) e = cudaEventRecord(ev[1 + g], sg);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev[1 + g], 0);
         }

@@ -202,11 +202,20 @@ int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms);  // 0: 
 // Batched form, one thread-block cluster of csize blocks (1, 2, 4 or 8) per
 // instance: instances ids[0..count) of args run up to `sweeps` sweeps each
 // with the lane-group variant cfg (true for batch_block_config);
-// psi_prologue: first launch of a solve.
+// psi_prologue: first launch of a solve.  smem > 0 (csize = 1 only, at most
+// kBlockSmemMax): the shared-memory form, each block holding its instance's
+// flows, heights, roots, partials and state in smem bytes of shared memory
+// (the largest block_smem_bytes of the instances launched).
 template <typename T>
 cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
-                               int psi_prologue, cudaStream_t stream);
+                               int psi_prologue, cudaStream_t stream, int64_t smem = 0);
 bool batch_block_config(int cfg);
+// Shared memory of the one-block form for an instance of n vertices, m edges,
+// rows of Kp values and n_psi edge partials, in bytes.
+template <typename T>
+int64_t block_smem_bytes(int64_t n, int64_t m, int64_t Kp, int64_t n_psi);
+// Largest shared-memory form: two blocks of it fit on one SM.
+constexpr int64_t kBlockSmemMax = 100 * 1024;
 
 // Packs and widens m padded rows into dst[rows*K] (double), dst writable by the GPU.
 template <typename T>

@@ -37,13 +37,14 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(SweepArgs<T> a)
 
 // ------------------------------------------------------------------ excess and heights
 
-template <typename T>
+template <typename T, bool SH = false>
 __device__ __forceinline__ void excess_tail(const SweepArgs<T>& a, int block, int nblocks,
                                             typename Acc<T>::V zacc, T cons);
 
 // Body of one excess pass run by block `block` of `nblocks` (the standalone
-// kernel passes its own grid; the persistent kernel its whole grid).
-template <typename T>
+// kernel passes its own grid; the persistent kernel its whole grid).  SH:
+// the objective partials live in shared memory (the one-block engine).
+template <typename T, bool SH = false>
 __device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, int nblocks)
 {
     using VT = typename VecOf<T>::type;
@@ -134,25 +135,26 @@ __device__ __forceinline__ void excess_body(const SweepArgs<T>& a, int block, in
         }
         zacc = A::add(zacc, zt);
     }
-    excess_tail<T>(a, block, nblocks, zacc, cons);
+    excess_tail<T, SH>(a, block, nblocks, zacc, cons);
 }
 
 // End of an excess pass in every block: add this block's fixed slice of the
 // edge kernel's psi partials and write the block's three partials.  Every
 // thread of the block calls it.
-template <typename T>
+template <typename T, bool SH>
 __device__ __forceinline__ void excess_tail(const SweepArgs<T>& a, int block, int nblocks,
                                             typename Acc<T>::V zacc, T cons)
 {
     using A = Acc<T>;
     T capb = T(0);
     {
-        const int64_t lo = (int64_t)block * a.n_psi / nblocks;
-        const int64_t hi = (int64_t)(block + 1) * a.n_psi / nblocks;
+        // the block's slice [lo, hi) of the edge partials (SH: the one block takes all)
+        const int64_t lo = SH ? 0 : (int64_t)block * a.n_psi / nblocks;
+        const int64_t hi = SH ? a.n_psi : (int64_t)(block + 1) * a.n_psi / nblocks;
         const typename A::S* pp = reinterpret_cast<const typename A::S*>(a.part_psi);
         for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-            zacc = A::add(zacc, A::load(pp + b));
-            const T c = __ldcg(a.part_cap + b);
+            zacc = A::add(zacc, A::unstore(ld_part<SH>(pp + b)));
+            const T c = ld_part<SH>(a.part_cap + b);
             capb = c > capb ? c : capb;
         }
     }
@@ -1314,15 +1316,77 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-template <typename T, int G, int V>
+// Shared-memory form (SM, one block per instance): the block copies the
+// instance's mutable arrays -- both flow buffers, the heights, both root
+// buffers, the objective partials -- and its solver state into shared
+// memory, with the read-only arrays the sweep reads (incidence lists,
+// commodities, capacities, endpoints, scales), runs its sweeps there, and
+// copies the mutable ones back before it returns.  The phases then pass
+// their data through shared memory instead of L2, whose latency is what a
+// sweep of a small instance waits on.  The arithmetic and the order of
+// every reduction are unchanged, so flows, roots, z and the stop sweep
+// equal the global-memory form's bit for bit.  Layout (each part 16-byte
+// aligned): f buffer 0 and 1 [m][Kp], h [n][Kp], roots 0 and 1 [2m], psi
+// partials [n_psi] (stored pairs) and [n_psi], excess partials (one each),
+// then inc_ptr [n+1], inc [2m], s, t, dem, 1/d [Kp], u, src, col,
+// 1/scale [m], 1/delta [n].
+template <typename T>
+struct BlockSmem {
+    int64_t f0, f1, h, th0, th1, ppsi, pcap, ph, pcons, pcapb;
+    int64_t incp, inc, s, t, dem, idem, u, src, col, isc, ideg, bytes;
+};
+
+template <typename T>
+__host__ __device__ inline BlockSmem<T> block_smem_layout(int64_t n, int64_t m, int64_t Kp, int64_t n_psi)
+{
+    auto up = [](int64_t x) { return (x + 15) & ~int64_t(15); };
+    BlockSmem<T> L{};
+    int64_t o = 0;
+    L.f0 = o;    o = up(o + m * Kp * (int64_t)sizeof(T));
+    L.f1 = o;    o = up(o + m * Kp * (int64_t)sizeof(T));
+    L.h = o;     o = up(o + n * Kp * (int64_t)sizeof(T));
+    L.th0 = o;   o = up(o + 2 * m * (int64_t)sizeof(T));
+    L.th1 = o;   o = up(o + 2 * m * (int64_t)sizeof(T));
+    L.ppsi = o;  o = up(o + n_psi * (int64_t)sizeof(typename Acc<T>::S));
+    L.pcap = o;  o = up(o + n_psi * (int64_t)sizeof(T));
+    L.ph = o;    o = up(o + (int64_t)sizeof(double));
+    L.pcons = o; o = up(o + (int64_t)sizeof(T));
+    L.pcapb = o; o = up(o + (int64_t)sizeof(T));
+    L.incp = o;  o = up(o + (n + 1) * (int64_t)sizeof(int64_t));
+    L.inc = o;   o = up(o + 2 * m * (int64_t)sizeof(int32_t));
+    L.s = o;     o = up(o + Kp * (int64_t)sizeof(int32_t));
+    L.t = o;     o = up(o + Kp * (int64_t)sizeof(int32_t));
+    L.dem = o;   o = up(o + Kp * (int64_t)sizeof(T));
+    L.idem = o;  o = up(o + Kp * (int64_t)sizeof(T));
+    L.u = o;     o = up(o + m * (int64_t)sizeof(T));
+    L.src = o;   o = up(o + m * (int64_t)sizeof(int32_t));
+    L.col = o;   o = up(o + m * (int64_t)sizeof(int32_t));
+    L.isc = o;   o = up(o + m * (int64_t)sizeof(T));
+    L.ideg = o;  o = up(o + n * (int64_t)sizeof(T));
+    L.bytes = o;
+    return L;
+}
+
+// count elements of X from src to dst by the whole block
+template <typename X>
+__device__ __forceinline__ void block_copy(X* __restrict__ dst, const X* __restrict__ src, int64_t count)
+{
+    for (int64_t q = threadIdx.x; q < count; q += blockDim.x) dst[q] = src[q];
+}
+
+template <typename T, int G, int V, bool SM>
 __global__ void __launch_bounds__(kBatchThreads, 2)
     batch_block_kernel(const SweepArgs<T>* __restrict__ args, const int* __restrict__ ids, int csize,
                        int64_t sweeps, int psi_prologue)
 {
+    using VT = typename VecOf<T>::type;
+    using S = typename Acc<T>::S;
     // the instance's arguments live in shared memory (not in every thread's
     // registers); thread 0 of every block swaps its buffers between sweeps
     __shared__ SweepArgs<T> sa;
     __shared__ int stop;
+    __shared__ DevState sst;  // SM: the solver state while the block runs
+    extern __shared__ __align__(16) unsigned char smem[];
     const int rank = (int)(blockIdx.x % (unsigned)csize);
     auto sync = [csize]() {
         if (csize > 1) cluster_sync_all();
@@ -1335,6 +1399,65 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     }
     __syncthreads();
     if (stop) return;  // the same value in every block of the cluster (no block of it has run yet)
+    // SM: the global buffers, to which the shared copies return at the end
+    T* const gf0 = sa.f;
+    T* const gf1 = sa.f_out;
+    T* const gh = sa.h;
+    T* const gth0 = const_cast<T*>(sa.theta_in);
+    T* const gth1 = sa.theta;
+    S* const gpsi = reinterpret_cast<S*>(sa.part_psi);
+    T* const gcap = sa.part_cap;
+    DevState* const gst = sa.st;
+    const BlockSmem<T> L = block_smem_layout<T>(sa.n, sa.m, sa.Kp, sa.n_psi);
+    if constexpr (SM) {
+        const int64_t rowv = sa.m * sa.Kp / VecOf<T>::N;
+        block_copy(reinterpret_cast<VT*>(smem + L.f0), reinterpret_cast<const VT*>(gf0), rowv);
+        block_copy(reinterpret_cast<VT*>(smem + L.f1), reinterpret_cast<const VT*>(gf1), rowv);
+        block_copy(reinterpret_cast<VT*>(smem + L.h), reinterpret_cast<const VT*>(gh),
+                   (int64_t)sa.n * sa.Kp / VecOf<T>::N);
+        block_copy(reinterpret_cast<T*>(smem + L.th0), gth0, 2 * sa.m);
+        block_copy(reinterpret_cast<T*>(smem + L.th1), gth1, 2 * sa.m);
+        block_copy(reinterpret_cast<S*>(smem + L.ppsi), gpsi, sa.n_psi);
+        block_copy(reinterpret_cast<T*>(smem + L.pcap), gcap, sa.n_psi);
+        block_copy(reinterpret_cast<int64_t*>(smem + L.incp), sa.inc_ptr, (int64_t)sa.n + 1);
+        block_copy(reinterpret_cast<int32_t*>(smem + L.inc), sa.inc, 2 * sa.m);
+        block_copy(reinterpret_cast<int32_t*>(smem + L.s), sa.s, (int64_t)sa.Kp);
+        block_copy(reinterpret_cast<int32_t*>(smem + L.t), sa.t, (int64_t)sa.Kp);
+        block_copy(reinterpret_cast<T*>(smem + L.dem), sa.dem, (int64_t)sa.Kp);
+        block_copy(reinterpret_cast<T*>(smem + L.idem), sa.inv_dem, (int64_t)sa.Kp);
+        block_copy(reinterpret_cast<T*>(smem + L.u), sa.u, sa.m);
+        block_copy(reinterpret_cast<int32_t*>(smem + L.src), sa.src, sa.m);
+        block_copy(reinterpret_cast<int32_t*>(smem + L.col), sa.col, sa.m);
+        block_copy(reinterpret_cast<T*>(smem + L.isc), sa.inv_scale_t, sa.m);
+        block_copy(reinterpret_cast<T*>(smem + L.ideg), sa.inv_deg, (int64_t)sa.n);
+        __syncthreads();  // every thread has read sa's global pointers
+        if (threadIdx.x == 0) {
+            sst = *gst;
+            sa.f = reinterpret_cast<T*>(smem + L.f0);
+            sa.f_out = reinterpret_cast<T*>(smem + L.f1);
+            sa.h = reinterpret_cast<T*>(smem + L.h);
+            sa.theta_in = reinterpret_cast<const T*>(smem + L.th0);
+            sa.theta = reinterpret_cast<T*>(smem + L.th1);
+            sa.part_psi = smem + L.ppsi;
+            sa.part_cap = reinterpret_cast<T*>(smem + L.pcap);
+            sa.part_h = reinterpret_cast<double*>(smem + L.ph);
+            sa.part_cons = reinterpret_cast<T*>(smem + L.pcons);
+            sa.part_capb = reinterpret_cast<T*>(smem + L.pcapb);
+            sa.inc_ptr = reinterpret_cast<const int64_t*>(smem + L.incp);
+            sa.inc = reinterpret_cast<const int32_t*>(smem + L.inc);
+            sa.s = reinterpret_cast<const int32_t*>(smem + L.s);
+            sa.t = reinterpret_cast<const int32_t*>(smem + L.t);
+            sa.dem = reinterpret_cast<const T*>(smem + L.dem);
+            sa.inv_dem = reinterpret_cast<const T*>(smem + L.idem);
+            sa.u = reinterpret_cast<const T*>(smem + L.u);
+            sa.src = reinterpret_cast<const int32_t*>(smem + L.src);
+            sa.col = reinterpret_cast<const int32_t*>(smem + L.col);
+            sa.inv_scale_t = reinterpret_cast<const T*>(smem + L.isc);
+            sa.inv_deg = reinterpret_cast<const T*>(smem + L.ideg);
+            sa.st = &sst;
+        }
+        __syncthreads();
+    }
     if (psi_prologue) {  // congestion partials of the starting flows, in this kernel's layout
         edge_group_body<T, G, V, true>(sa, rank, csize);
         sync();
@@ -1342,13 +1465,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
         __syncthreads();
     }
     for (int64_t q = 0; q < sweeps; ++q) {
-        excess_body<T>(sa, rank, csize);
+        excess_body<T, SM>(sa, rank, csize);
         sync();
-        if (rank == 0) reduce_and_finalize(sa);
+        if (rank == 0) reduce_and_finalize<T, SM>(sa);
         sync();
         if (threadIdx.x == 0) stop = reinterpret_cast<volatile DevState*>(sa.st)->stop;
         __syncthreads();
-        if (stop) return;  // f^(t) stays in sa.f
+        if (stop) break;  // f^(t) stays in sa.f
         edge_group_body<T, G, V, true>(sa, rank, csize);
         sync();
         if (threadIdx.x == 0) {  // f^(t+1) becomes the current flows
@@ -1360,6 +1483,18 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
             sa.theta = const_cast<T*>(th);
         }
         __syncthreads();
+    }
+    if constexpr (SM) {  // every buffer back to its global counterpart
+        const int64_t rowv = sa.m * sa.Kp / VecOf<T>::N;
+        block_copy(reinterpret_cast<VT*>(gf0), reinterpret_cast<const VT*>(smem + L.f0), rowv);
+        block_copy(reinterpret_cast<VT*>(gf1), reinterpret_cast<const VT*>(smem + L.f1), rowv);
+        block_copy(reinterpret_cast<VT*>(gh), reinterpret_cast<const VT*>(smem + L.h),
+                   (int64_t)sa.n * sa.Kp / VecOf<T>::N);
+        block_copy(gth0, reinterpret_cast<const T*>(smem + L.th0), 2 * sa.m);
+        block_copy(gth1, reinterpret_cast<const T*>(smem + L.th1), 2 * sa.m);
+        block_copy(gpsi, reinterpret_cast<const S*>(smem + L.ppsi), sa.n_psi);
+        block_copy(gcap, reinterpret_cast<const T*>(smem + L.pcap), sa.n_psi);
+        if (threadIdx.x == 0) *gst = sst;
     }
 }
 
@@ -1686,7 +1821,7 @@ int persistent_grid(int cfg, int64_t m, int32_t n, int Kp, int num_sms)
 
 template <typename T, int G, int V>
 cudaError_t launch_batch_block_gv(const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
-                                  int psi_prologue, cudaStream_t stream)
+                                  int psi_prologue, cudaStream_t stream, int64_t smem)
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(count * csize));
@@ -1699,29 +1834,45 @@ cudaError_t launch_batch_block_gv(const SweepArgs<T>* args, const int* ids, int 
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = csize > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, batch_block_kernel<T, G, V>, args, ids, csize, sweeps, psi_prologue);
+    if (smem > 0) {
+        const cudaError_t e = cudaFuncSetAttribute(batch_block_kernel<T, G, V, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cfg.dynamicSmemBytes = (size_t)smem;
+        return cudaLaunchKernelEx(&cfg, batch_block_kernel<T, G, V, true>, args, ids, csize, sweeps, psi_prologue);
+    }
+    return cudaLaunchKernelEx(&cfg, batch_block_kernel<T, G, V, false>, args, ids, csize, sweeps, psi_prologue);
 }
 
 template <typename T>
 cudaError_t launch_batch_block(int cfg, const SweepArgs<T>* args, const int* ids, int count, int csize, int64_t sweeps,
-                               int psi_prologue, cudaStream_t stream)
+                               int psi_prologue, cudaStream_t stream, int64_t smem)
 {
     if (count <= 0) return cudaSuccess;
     if (csize < 1 || csize > 8 || (csize & (csize - 1))) return cudaErrorInvalidValue;
+    if (smem < 0 || smem > kBlockSmemMax || (smem > 0 && csize != 1)) return cudaErrorInvalidValue;
     switch (edge_plain_config(cfg)) {
-    case 0: return launch_batch_block_gv<T, 4, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
-    case 1: return launch_batch_block_gv<T, 8, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
-    case 2: return launch_batch_block_gv<T, 16, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
-    case 3: return launch_batch_block_gv<T, 32, 1>(args, ids, count, csize, sweeps, psi_prologue, stream);
-    case 4: return launch_batch_block_gv<T, 32, 2>(args, ids, count, csize, sweeps, psi_prologue, stream);
-    case 5: return launch_batch_block_gv<T, 32, 4>(args, ids, count, csize, sweeps, psi_prologue, stream);
+    case 0: return launch_batch_block_gv<T, 4, 1>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
+    case 1: return launch_batch_block_gv<T, 8, 1>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
+    case 2: return launch_batch_block_gv<T, 16, 1>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
+    case 3: return launch_batch_block_gv<T, 32, 1>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
+    case 4: return launch_batch_block_gv<T, 32, 2>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
+    case 5: return launch_batch_block_gv<T, 32, 4>(args, ids, count, csize, sweeps, psi_prologue, stream, smem);
     default: return cudaErrorInvalidValue;
     }
 }
 template cudaError_t launch_batch_block<float>(int, const SweepArgs<float>*, const int*, int, int, int64_t, int,
-                                               cudaStream_t);
+                                               cudaStream_t, int64_t);
 template cudaError_t launch_batch_block<double>(int, const SweepArgs<double>*, const int*, int, int, int64_t, int,
-                                                cudaStream_t);
+                                                cudaStream_t, int64_t);
+
+template <typename T>
+int64_t block_smem_bytes(int64_t n, int64_t m, int64_t Kp, int64_t n_psi)
+{
+    return block_smem_layout<T>(n, m, Kp, n_psi).bytes;
+}
+template int64_t block_smem_bytes<float>(int64_t, int64_t, int64_t, int64_t);
+template int64_t block_smem_bytes<double>(int64_t, int64_t, int64_t, int64_t);
 
 bool batch_block_config(int cfg)
 {

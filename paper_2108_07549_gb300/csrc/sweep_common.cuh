@@ -308,6 +308,7 @@ struct Acc<float> {
     }
     static __device__ __forceinline__ S store(V a) { return make_float2(a.hi, a.lo); }
     static __device__ __forceinline__ V load(const S* p) { const float2 x = __ldcg(p); return {x.x, x.y}; }
+    static __device__ __forceinline__ V unstore(S x) { return {x.x, x.y}; }
     static __device__ __forceinline__ double to_double(V a) { return (double)a.hi + (double)a.lo; }
 };
 
@@ -320,6 +321,7 @@ struct Acc<double> {
     static __device__ __forceinline__ V shfl(V a, int o) { return __shfl_xor_sync(kFull, a, o); }
     static __device__ __forceinline__ S store(V a) { return a; }
     static __device__ __forceinline__ V load(const S* p) { return __ldcg(p); }
+    static __device__ __forceinline__ V unstore(S x) { return x; }
     static __device__ __forceinline__ double to_double(V a) { return a; }
 };
 
@@ -482,19 +484,41 @@ __device__ void finalize(const SweepArgs<T>& a, double zsum, double cons, double
     }
 }
 
+// Load of an objective partial that another block of the same launch may
+// have written: at L2 (coherent) from global memory; SH = true when the
+// partials live in the block's shared memory (the one-block engine), where
+// a plain load is the coherent one.
+template <bool SH, typename X>
+__device__ __forceinline__ X ld_part(const X* p)
+{
+    if constexpr (SH) return *p;
+    else return __ldcg(p);
+}
+
 // FP64 reduction of the excess blocks' partials in a fixed order, then the
 // objective and the stop test.  Run by one whole block.
-template <typename T>
+template <typename T, bool SH = false>
 __device__ void reduce_and_finalize(const SweepArgs<T>& a)
 {
+    if (SH && a.grid_v == 1) {
+        // one partial of each kind: the block reduction below would add and
+        // compare only zeros to thread 0's values, so thread 0 forms the
+        // same result directly
+        if (threadIdx.x == 0) {
+            const double zs = 0.0 + ld_part<SH>(a.part_h);
+            const T c1 = ld_part<SH>(a.part_cons), c2 = ld_part<SH>(a.part_capb);
+            finalize(a, zs, (double)(c1 > T(0) ? c1 : T(0)), (double)(c2 > T(0) ? c2 : T(0)));
+        }
+        return;
+    }
     __shared__ double sz[32];
     __shared__ T sm1[32], sm2[32];
     double zs = 0.0;
     T cm = T(0), cp = T(0);
     for (int b = threadIdx.x; b < a.grid_v; b += blockDim.x) {
-        zs += __ldcg(a.part_h + b);
-        const T c1 = __ldcg(a.part_cons + b);
-        const T c2 = __ldcg(a.part_capb + b);
+        zs += ld_part<SH>(a.part_h + b);
+        const T c1 = ld_part<SH>(a.part_cons + b);
+        const T c2 = ld_part<SH>(a.part_capb + b);
         cm = c1 > cm ? c1 : cm;
         cp = c2 > cp ? c2 : cp;
     }
