@@ -309,6 +309,7 @@ struct Acc<float> {
     static __device__ __forceinline__ S store(V a) { return make_float2(a.hi, a.lo); }
     static __device__ __forceinline__ V load(const S* p) { const float2 x = __ldcg(p); return {x.x, x.y}; }
     static __device__ __forceinline__ V unstore(S x) { return {x.x, x.y}; }
+    static __device__ __forceinline__ bool nonzero(V a) { return a.hi != 0.f || a.lo != 0.f; }
     static __device__ __forceinline__ double to_double(V a) { return (double)a.hi + (double)a.lo; }
 };
 
@@ -322,30 +323,48 @@ struct Acc<double> {
     static __device__ __forceinline__ S store(V a) { return a; }
     static __device__ __forceinline__ V load(const S* p) { return __ldcg(p); }
     static __device__ __forceinline__ V unstore(S x) { return x; }
+    static __device__ __forceinline__ bool nonzero(V a) { return a != 0.0; }
     static __device__ __forceinline__ double to_double(V a) { return a; }
 };
+
+// Zero sums and maxima.  The terms reduced below are sums of squares and
+// maxima of non-negative values, and an accumulator pair is normalised
+// (hi = hi + lo rounded), so adding a zero pair, or taking the maximum with
+// zero, returns the other operand unchanged: a warp whose values are all
+// zero skips its reduction, and the block reduction skips such warps,
+// without changing any finite result.  (NaN counts as nonzero; an
+// accumulator that overflowed stops the solve as non-finite either way.)
+template <typename T>
+__device__ __forceinline__ bool acc_max_nonzero(typename Acc<T>::V z, T m)
+{
+    return Acc<T>::nonzero(z) || m != T(0);
+}
 
 // Warp reduction of (sum, max): the result is valid in lane 0 (lane 0 always
 // combines in the same order, so it is deterministic).
 template <typename T>
 __device__ __forceinline__ void warp_acc_max(typename Acc<T>::V& z, T& mx)
 {
+    if (!__any_sync(kFull, acc_max_nonzero<T>(z, mx))) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
     mx = warp_max(mx);
 }
 
-// Block reduction of (sum, max, max); the result is valid in thread 0.
+// Block reduction of (sum, max, max); the result is valid in thread 0, which
+// adds the warps' results in warp order (the all-zero warps left out).
 template <typename T>
 __device__ void block_acc_max2(typename Acc<T>::V& z, T& m1, T& m2)
 {
     using V = typename Acc<T>::V;
     __shared__ V sz[32];
     __shared__ T s1[32], s2[32];
+    if (__any_sync(kFull, acc_max_nonzero<T>(z, m1) || m2 != T(0))) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
-    m1 = warp_max(m1);
-    m2 = warp_max(m2);
+        for (int o = 16; o > 0; o >>= 1) z = Acc<T>::add(z, Acc<T>::shfl(z, o));
+        m1 = warp_max(m1);
+        m2 = warp_max(m2);
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
         sz[w] = z;
@@ -353,13 +372,17 @@ __device__ void block_acc_max2(typename Acc<T>::V& z, T& m1, T& m2)
         s2[w] = m2;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
         const int nw = blockDim.x >> 5;
-        for (int q = 1; q < nw; ++q) {
-            z = Acc<T>::add(z, sz[q]);
-            m1 = s1[q] > m1 ? s1[q] : m1;
-            m2 = s2[q] > m2 ? s2[q] : m2;
-        }
+        const bool nz = l < nw && (acc_max_nonzero<T>(sz[l], s1[l]) || s2[l] != T(0));
+        const unsigned live = __ballot_sync(kFull, nz);
+        if (l == 0)
+            for (unsigned b = live & ~1u; b; b &= b - 1) {
+                const int q = __ffs(b) - 1;
+                z = Acc<T>::add(z, sz[q]);
+                m1 = s1[q] > m1 ? s1[q] : m1;
+                m2 = s2[q] > m2 ? s2[q] : m2;
+            }
     }
 }
 
