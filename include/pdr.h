@@ -115,8 +115,9 @@ typedef struct {
                            per lane; otherwise 1 is used).  An instance that one block solves
                            and whose arrays fit in 100 KB of shared memory (flows, heights,
                            roots, partials, state and the read-only arrays of a sweep) is
-                           solved there, copied in and out once per launch.  Same flows and
-                           sweeps as 1. */
+                           solved there, copied in and out once per launch.  FP64 sweeps
+                           (PDR_PREC_FP64 and the FP64 tail) run on engine 1: one block has
+                           one SM's FP64 rate.  Same flows and sweeps as 1. */
     double eps_obj;     /* Alg. 1 stop rule, absolute; <= 0 disables (default 1e-6, Section 7) */
     double resid_tol;   /* residual stop and feasibility tolerance; <= 0 disables the stop (default 1e-6) */
     double eps_rel;     /* relative objective-change stop; <= 0 disables (default 0) */

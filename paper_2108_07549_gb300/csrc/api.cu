@@ -874,7 +874,10 @@ pdr_status run_phase(pdr_ctx* ctx, int64_t t_start)
     if (s != PDR_OK) return s;
     s = flows_to_buffer0<T>(ctx);
     if (s != PDR_OK) return s;
-    if (ctx->opt.use_graph == 3 && cluster_eligible(ctx, p)) return run_cluster<T>(ctx, t_start);
+    // one instance's FP64 sweeps stay on the graph engine: one block is held
+    // to one SM's FP64 rate, a small fraction of its FP32 rate on this GPU,
+    // and loses to the kernels that spread a sweep over several SMs
+    if (ctx->opt.use_graph == 3 && p == Prec<float>::id && cluster_eligible(ctx, p)) return run_cluster<T>(ctx, t_start);
     if (persistent_ok(ctx, p)) {
         bool ran = false;
         s = run_persistent<T>(ctx, &ran);

@@ -1,8 +1,12 @@
 """The cluster engine (pdr_options.use_graph = 3): one thread-block cluster
 runs a small instance's whole solve (the batched form's engine, with one
 instance).  Its sweeps, objective and flows equal the CUDA-graph engine's
-bit for bit, across launches of 2048 sweeps and in every precision mode;
-an instance it does not take runs on the graph engine."""
+bit for bit, across launches of 2048 sweeps and in every precision mode
+(the FP64 sweeps of one instance run on the graph engine; the batched form
+runs them on the cluster kernel, tested in test_gpu_batch.py); an instance
+it does not take runs on the graph engine.  Small instances run the
+kernel's shared-memory form, larger single-block ones its global-memory
+form (dg60_k40 in FP32 is the former, dg80_k200 the latter)."""
 
 import numpy as np
 import pytest
@@ -38,7 +42,8 @@ def test_cluster_engine_equals_graph_engine(pdr, prec, algo):
     a = pdr.ALGO_ESO if algo == "eso" else pdr.ALGO_CK
     rng = np.random.default_rng(5)
     insts = [I.grid5_k10(1.3), I.grid5_k10(0.6),
-             I.make_instance("dg60_k40", I.random_digraph(60, 3, rng), 40, ("uniform_int", 1, 9), 1.0, rng)]
+             I.make_instance("dg60_k40", I.random_digraph(60, 3, rng), 40, ("uniform_int", 1, 9), 1.0, rng),
+             I.make_instance("dg80_k200", I.random_digraph(80, 3, rng), 200, ("uniform_int", 1, 9), 1.0, rng)]
     for inst in insts:
         opts = dict(precision=p, algo=a, eps_obj=0.0, resid_tol=1e-6, max_sweeps=5000)
         r1, f1 = solve(pdr, inst, 1, **opts)
@@ -53,7 +58,7 @@ def test_cluster_engine_runs_several_launches_and_resumes(pdr):
     """A solve longer than one launch (2048 sweeps), then a second solve call
     that continues from the returned flows: both as the graph engine's."""
     inst = I.grid5_k10(1.3)
-    opts = dict(precision=pdr.PREC_FP64, eps_obj=0.0, resid_tol=0.0, max_sweeps=4500)
+    opts = dict(precision=pdr.PREC_FP32, eps_obj=0.0, resid_tol=0.0, max_sweeps=4500)
     out = {}
     for engine in (1, 3):
         with pdr.Solver.from_instance(inst, use_graph=engine, **opts) as s:
