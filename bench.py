@@ -800,9 +800,9 @@ def l2_resident_block(pdr, torch, stream, inst, flush, steps=5, S=2000):
 def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
     """Time to residual 1e-6 (cap_rel and cons_rel <= 1e-6, or a Farkas
     certificate) on the 5x5 grid and its infeasible twin (GPU FP64, GPU FP32
-    with the FP64 tail, each on the CUDA-graph engine and on the cluster
-    engine -- one block holding the instance in shared memory -- and the FP64
-    oracle), and on the headline instance the
+    with the FP64 tail on the CUDA-graph engine, the same with its FP32
+    sweeps on the cluster engine -- one block holding the instance in shared
+    memory -- and the FP64 oracle), and on the headline instance the
     residuals reached within a fixed budget of FP32 sweeps, with the oracle's
     residuals at the same early sweep beside the GPU's."""
     import oracle
@@ -813,7 +813,6 @@ def residual_block(pdr, torch, stream, big, budget_sweeps=2000):
     for label, inst in (("grid5_k10_feasible_1.3x", g), ("grid5_k10_infeasible_0.6x", g.with_factor(0.6))):
         row = {}
         for prec, code, eng in (("gpu_fp64", pdr.PREC_FP64, 1), ("gpu_fp32_fp64tail", pdr.PREC_FP32_FP64TAIL, 1),
-                                ("gpu_fp64_cluster_engine", pdr.PREC_FP64, 3),
                                 ("gpu_fp32_fp64tail_cluster_engine", pdr.PREC_FP32_FP64TAIL, 3)):
             with torch.cuda.stream(stream):
                 with pdr.Solver.from_instance(inst, stream=stream.cuda_stream, precision=code, eps_obj=0.0,
