@@ -486,11 +486,13 @@ pdr_status pdr_batch_create(int32_t count, const pdr_instance *inst, const pdr_o
 
 /* Solves every instance from its current state.  Small instances (m x K <=
  * 2^18 on a lane-group variant of at most 4 vectors per lane, Alg. 1 or
- * Program (6)) run their whole solve on one thread-block cluster each, in
+ * Program (6)) run their FP32 sweeps on one thread-block cluster each, in
  * shared launches of the cluster kernel (engine 3 of pdr_options.use_graph,
- * with its shared-memory form for the instances that fit).  The others run in one CUDA graph launch: a conditional while loop whose
- * body holds one chain of sweeps per instance; the chains are independent,
- * so the instances run concurrently.  Each instance stops by its own stop
+ * with its shared-memory form for the instances that fit).  The others, and
+ * every FP64 sweep (one block has only one SM's FP64 rate), run in one CUDA
+ * graph launch: a conditional while loop whose body holds one chain of
+ * sweeps per instance; the chains are independent, so the instances run
+ * concurrently.  Each instance stops by its own stop
  * rules (a stopped instance's kernels return at once); the loop ends when
  * the last one stops.  The flows equal, bit for bit, single-instance solves
  * with the same edge variant.  With

@@ -2463,8 +2463,12 @@ int batch_cluster_size(const pdr_ctx* c, int p)
 // True if instance i runs on the one-cluster-per-instance engine in
 // precision p (cluster_eligible: a small instance with a lane-group variant
 // of at most 4 vectors per lane; the larger ones spill at the block's
-// register budget).
-bool batch_resident(const pdr_batch* b, int32_t i, int p) { return cluster_eligible(b->ctx[i], p); }
+// register budget).  FP64 sweeps run on the graph: one block has one SM's
+// FP64 rate, and the graph's kernels spread each instance over several SMs.
+bool batch_resident(const pdr_batch* b, int32_t i, int p)
+{
+    return p == Prec<float>::id && cluster_eligible(b->ctx[i], p);
+}
 
 // The instances of `blk` (set up by batch_run) on the one-block-per-instance
 // engine: launches of kBlockChunk sweeps, one per edge-kernel variant on its

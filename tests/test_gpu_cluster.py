@@ -2,9 +2,8 @@
 runs a small instance's whole solve (the batched form's engine, with one
 instance).  Its sweeps, objective and flows equal the CUDA-graph engine's
 bit for bit, across launches of 2048 sweeps and in every precision mode
-(the FP64 sweeps of one instance run on the graph engine; the batched form
-runs them on the cluster kernel, tested in test_gpu_batch.py); an instance
-it does not take runs on the graph engine.  Small instances run the
+(FP64 sweeps run on the graph engine, here and in the batched form); an
+instance it does not take runs on the graph engine.  Small instances run the
 kernel's shared-memory form, larger single-block ones its global-memory
 form (dg60_k40 in FP32 is the former, dg80_k200 the latter)."""
 
